@@ -1,0 +1,162 @@
+/*
+ * prop.h -- C ABI of the GB300 one-way vector Helmholtz propagator.
+ *
+ * The library advances the transverse envelope w = (w1[, w2]) of the electric
+ * field by steps of dz with the exponential one-way propagator of Keefe et al.
+ * (arXiv 2410.17446), Sec. 2:
+ *
+ *   w(z+dz) = r0 w(z) + sum_k r_k (Z - p_k I)^-1 w(z)          Eqs. (approx_prop), (W_k_def)
+ *
+ * where r(zeta) = r0 + sum_k r_k/(zeta - p_k) approximates
+ * exp(iK(-1 + sqrt(1 + zeta))), K = k0 n0 dz (Eq. expop_prop; partial
+ * fractions of Eq. pf_expan_eq with the factor e^{-iK} of Eq. Wk_define
+ * folded into r0 and r_k), and Z is the operator matrix of Eq. (Z_bar_eq).
+ * Each shifted system is solved by restarted GMRES, right-preconditioned by the
+ * free-space solve (Z_fs - p_k I)^-1 of Sec. 4.2 (Eqs. Z_bar_fs_def,
+ * fs_sylvester), which on the periodic pseudo-spectral grid used here is
+ * diagonal in Fourier space.
+ *
+ * Discretisation: nx x ny periodic grid, x fastest, spectral derivatives; the
+ * absorbing border is part of the caller's complex n^2 (Im n^2 > 0 absorbs).
+ * Supported sizes: nx, ny in {16, 32, 64, 128, 256, 384, 512, 768, 1024}.
+ *
+ * Memory and ownership.  The caller owns all device memory: it passes one
+ * device workspace of at least prop_workspace_size() bytes to prop_create and
+ * keeps it alive until prop_destroy.  The library itself allocates no device
+ * memory.  The handle (host memory) is allocated by prop_create.  Field and
+ * medium buffers passed to set/get calls may be host or device pointers
+ * (unified addressing); the data is copied, so the caller may reuse its buffer
+ * once the call returns.  All calls are asynchronous on the handle's stream
+ * except where stated.
+ *
+ * Errors.  Every call returns a status (PROP_OK = 0).  Argument errors leave
+ * the handle unchanged.  PROP_E_NOCONV leaves the field at the last completed
+ * step.  No C++ exception crosses this interface.  A handle is not thread-safe.
+ */
+#ifndef PROP_H
+#define PROP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum prop_status {
+  PROP_OK = 0,
+  PROP_E_ARG = 1,          /* invalid argument (size, pointer, option)           */
+  PROP_E_WORKSPACE = 2,    /* workspace missing, misaligned or too small          */
+  PROP_E_CUDA = 3,         /* a CUDA runtime call failed                          */
+  PROP_E_NOCONV = 4,       /* GMRES hit max_restarts without reaching tol         */
+  PROP_E_NAN = 5,          /* a residual norm became NaN or Inf                   */
+  PROP_E_UNSUPPORTED = 6   /* grid size / mode not compiled into this library     */
+};
+
+enum prop_precision {
+  PROP_FP64 = 0,           /* all arithmetic in complex FP64                      */
+  PROP_FP32 = 1            /* transforms and Krylov basis in complex FP32; Givens,
+                              least squares, residual norms, the solution and the
+                              field accumulated in FP64                           */
+};
+
+typedef struct prop_grid {
+  int32_t nx, ny;          /* cells, border included                              */
+  double dx, dy;           /* cell size, same length unit as 2 pi / k0            */
+} prop_grid;
+
+typedef struct prop_opts {
+  int32_t ncomp;           /* 1: scalar (psi terms dropped, Sec. 2); 2: (w1, w2)  */
+  int32_t precision;       /* enum prop_precision                                 */
+  int32_t restart;         /* GMRES restart length m, 1..64 (default 20)          */
+  int32_t max_restarts;    /* cycles per solve before PROP_E_NOCONV (default 50)  */
+  double tol;              /* stop when ||w - (Z - p_k) x_k|| <= tol ||w||         */
+} prop_opts;
+
+typedef struct prop_stats {
+  int64_t steps;           /* steps completed since prop_create / prop_set_field  */
+  int32_t npoles, nbeams;
+  int32_t last_iters_max;  /* max over (beam, pole) of Arnoldi steps, last step   */
+  int32_t last_cycles_max; /* max over (beam, pole) of restart cycles, last step  */
+  int64_t last_iters_sum;  /* sum over (beam, pole) of Arnoldi steps, last step   */
+  double last_resid_max;   /* max relative true residual, last step               */
+  int64_t total_iters;     /* Arnoldi steps summed over all steps                 */
+} prop_stats;
+
+typedef struct prop prop; /* opaque handle */
+
+/* Fill *o with the defaults for `precision` (tol 1e-12 FP64, 1e-7 FP32). */
+int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision);
+
+/* Bytes of device workspace prop_create needs for these beams and options.
+ * grids[nbeams]: one grid per independent beam. */
+int prop_workspace_size(int32_t nbeams, const prop_grid* grids, int32_t npoles,
+                        const prop_opts* opts, size_t* bytes);
+
+/* Create a propagator for nbeams independent beams sharing (k0, n0, dz) and one
+ * pole table.  poles[2*npoles], residues[2*npoles]: (re, im) pairs, host
+ * memory; r0[2]: the constant term.  d_workspace: 256-byte aligned device
+ * memory of ws_bytes >= prop_workspace_size().  stream: a cudaStream_t (NULL =
+ * legacy default stream).  On success *out holds the handle; the medium of
+ * every beam starts as n^2 = n0^2 (homogeneous) and every field as zero. */
+int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, double dz,
+                int32_t npoles, const double* poles, const double* residues, const double r0[2],
+                const prop_opts* opts, void* d_workspace, size_t ws_bytes, void* stream,
+                prop** out);
+
+/* Set the medium of one beam from complex128 n^2[ny][nx] (host or device).
+ * Z is rebuilt from it (Sec. 2: n and psi are updated between steps):
+ * delta = (n^2 - n0^2)/n0^2 and, for ncomp = 2, psi = Log n^2 with its
+ * spectral derivatives psi_x, psi_y, psi_xx, psi_yy, psi_xy scaled by (k0 n0)^-2. */
+int prop_set_medium(prop* h, int32_t beam, const void* n2);
+
+/* Set / get the field of one beam: complex128 [ncomp][ny][nx], host or device.
+ * prop_get_field synchronises the stream when dst is host memory. */
+int prop_set_field(prop* h, int32_t beam, const void* w);
+int prop_get_field(prop* h, int32_t beam, void* w);
+
+/* Advance every beam by dz (one z-step, Eq. approx_prop). */
+int prop_step(prop* h);
+
+/* Callback run before step s (0-based within this call); it may call
+ * prop_set_medium.  Returning non-zero stops the run with that status. */
+typedef int (*prop_medium_fn)(prop* h, int32_t step, void* user);
+
+/* nsteps calls of (cb, prop_step). cb may be NULL. */
+int prop_run(prop* h, int32_t nsteps, prop_medium_fn cb, void* user);
+
+/* Statistics of the last step (synchronises the stream). */
+int prop_get_stats(prop* h, prop_stats* out);
+
+/* Per-(beam, pole) Arnoldi step counts of the last step, iters[nbeams*npoles]
+ * (host memory; synchronises the stream). */
+int prop_get_iterations(prop* h, int32_t* iters);
+
+const char* prop_error_string(int status);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+void prop_destroy(prop* h);
+
+/* ---- building blocks, exposed for tests and tools ---------------------- */
+
+/* In-place batched 2-D DFT of `batch` complex [ny][nx] arrays on the device:
+ * forward X[ky,kx] = sum w[y,x] e^{-2 pi i (kx x/nx + ky y/ny)}, inverse with
+ * e^{+...} and a 1/(nx ny) factor.  precision selects complex64/complex128
+ * data.  d_work: device scratch of prop_fft2_workspace_size() bytes. */
+int prop_fft2_workspace_size(int32_t nx, int32_t ny, int32_t precision, size_t* bytes);
+int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse,
+              void* d_data, void* d_work, size_t work_bytes, void* stream);
+
+/* out = (Z_fs - p_k I)^-1 v for beam `beam`, pole k (Sec. 4.2.1): the free-space
+ * preconditioner.  v, out: device complex128 [ncomp][ny][nx]. */
+int prop_apply_freespace_inverse(prop* h, int32_t beam, int32_t pole, const void* d_v, void* d_out);
+
+/* out = Z v for beam `beam` with its current medium (Eq. Z_bar_eq).
+ * v, out: device complex128 [ncomp][ny][nx]. */
+int prop_apply_operator(prop* h, int32_t beam, const void* d_v, void* d_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROP_H */

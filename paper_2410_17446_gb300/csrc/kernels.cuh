@@ -1,0 +1,614 @@
+// Device kernels of one propagation step (scalar operator).
+//
+// Data live in a caller-provided workspace, grouped by grid: a group is the
+// set of beams that share (nx, ny, dx, dy); a "system" is one (beam, pole)
+// shifted solve of Eq. (W_k_def).  Every launch covers all units of a group at
+// once (grid.y = unit x component), so poles, components and beams share one
+// launch.  Masked launches skip, per CTA, the systems whose GMRES state does
+// not match.
+//
+// The three FFT passes of a 2-D transform round trip are
+//   rows  (forward row DFTs, coalesced along x),
+//   cols  (a tile of NV columns: column DFT, Fourier-diagonal multiply,
+//          inverse column DFT, in shared memory),
+//   rows  (inverse row DFTs followed by a pointwise epilogue),
+// so the free-space solve (Z_fs - p I)^-1 of Sec. 4.2 -- diagonal in Fourier
+// space on the periodic grid -- and the operator Z of Eq. (Z_bar_eq) share them.
+#pragma once
+#include "fft.cuh"
+
+namespace prop_dev {
+
+constexpr int MMAX = 64;   // largest GMRES restart length
+
+enum SysStateCode { ST_DONE = 0, ST_ITER = 1, ST_CYCLE_END = 2 };
+
+// GMRES state of one (beam, pole) system.  Complex numbers are double2.
+struct SysState {
+  int state, j, jend, iters, cycles, flags;   // flags: 1 = NaN seen, 2 = hit max cycles
+  double beta, resid, scale, nrm_a, nrm_b, pad;
+  double2 g[MMAX + 1];
+  double2 sn[MMAX];
+  double cs[MMAX];
+  double2 H[(MMAX + 1) * MMAX];   // H[i + j*(MMAX+1)]
+  double2 y[MMAX];
+  double2 dots1[MMAX + 1];
+  double2 dots2[MMAX + 1];
+  double2 coef[MMAX + 1];
+};
+
+template <typename T> struct GV {
+  using C = typename Cx<T>::t;
+  int nx, ny, ncomp, P, m, nb, nsys;
+  long npts;
+  C* V;          // [nsys][m+1][ncomp][npts]  Krylov basis
+  C* Zb;         // [nsys][m][ncomp][npts]    preconditioned basis z_j = M^-1 v_j
+  C* R0;         // [nsys][ncomp][npts]       right-hand side of the correction system
+  double2* E;    // [nsys][ncomp][npts]       correction e_k, FP64
+  C* Tmp;        // [nsys][ncomp][npts]       FFT intermediate
+  double2* W64;  // [nb][ncomp][npts]         master field
+  C* What;       // [nb][ncomp][npts]         2-D spectrum of the field (rounded to T)
+  C* Btmp;       // [nb][ncomp][npts]         beam-level FFT intermediate
+  C* delta;      // [nb][npts]                (n^2 - n0^2)/n0^2
+  C* basemul;    // [npts]                    (r(zeta_fs) - 1)/(nx ny)
+  const T* ax;   // [(P+1)][nx][2]            -kx^2/(k0n0)^2 - Re p/2 as (hi, lo)
+  const T* ay;   // [(P+1)][ny][2]            -ky^2/(k0n0)^2 - Re p/2 as (hi, lo)
+  const T* pim;  // [P+1]                     -Im p (pole P is p = 0: the plain Z_fs)
+  const C* twx;  // [nx] twiddles
+  const C* twy;  // [ny]
+  SysState* st;  // [nsys]
+  double* bnorm2;       // [nb] ||w||^2 of the step's right-hand side
+  int* nonhomog;        // [nb] 1 if delta != 0 somewhere
+  const double2* rk;    // [P] residues r_k
+};
+
+// Which buffer a pass reads or writes: item (unit u, component c) lives at
+// base + (u / div) * ustride + c * npts.
+template <typename C> struct Buf {
+  C* base;
+  long ustride;
+  int div;
+  __device__ __forceinline__ C* at(int u, int c, long npts) const {
+    return base + (long)(u / div) * ustride + (long)c * npts;
+  }
+};
+
+enum MulMode { MUL_NONE = 0, MUL_TABLE = 1, MUL_POLE_INV = 2, MUL_POLE_FWD = 3, MUL_SCALE = 4 };
+enum EpiMode { EPI_STORE = 0, EPI_STORE64 = 1, EPI_ACCUM64 = 2, EPI_R0 = 3, EPI_ARNOLDI = 4,
+               EPI_TRUERES = 5, EPI_OPERATOR = 6 };
+
+__device__ __forceinline__ float2 to_c(double2 a, float) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_c(double2 a, double) { return a; }
+__device__ __forceinline__ float2 to_c(float2 a, float) { return a; }
+__device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_d(double2 a) { return a; }
+
+// block-wide sum of a double (blockDim.x threads, multiple of 32); result valid in thread 0
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+  }
+  return r;
+}
+
+__device__ __forceinline__ bool unit_active(const SysState* st, int mask, int u) {
+  return mask < 0 || st[u].state == mask;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: forward row DFTs.  grid = (ny/NR, units*ncomp).
+// ---------------------------------------------------------------------------
+template <typename T, int N, int NR, int NT, typename SRC>
+__global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
+                                                 int mask, double* norm_acc) {
+  using C = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[32];
+  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  if (!unit_active(g.st, mask, u)) return;
+  const int row0 = blockIdx.x * NR;
+  const SRC* in = src.at(u, c, g.npts) + (long)row0 * N;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < NR * N; e += NT) {
+    const int r = e / N, n = e % N;
+    SRC v = in[e];
+    if (norm_acc) acc += (double)v.x * v.x + (double)v.y * v.y;
+    s[sidx<N, NR, false>(r, n)] = to_c(v, T());
+  }
+  __syncthreads();
+  fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
+  C* out = dst.at(u, c, g.npts) + (long)row0 * N;
+  for (int e = threadIdx.x; e < NR * N; e += NT) out[e] = s[sidx<N, NR, false>(e / N, e % N)];
+  if (norm_acc) {
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&norm_acc[u], t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: column tile of NV columns: [column DFT] -> multiply -> [inverse column DFT].
+// grid = (nx/NV, units*ncomp).  The multiplier sees kx index i = x0 + v and ky
+// index n; pole k = unit % P for system units.
+// ---------------------------------------------------------------------------
+template <typename T, int NY, int NV, int NT>
+__global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
+                                             int mask, int fwd, int mul, int inv, int skip_homog, int pole,
+                                             T scale) {
+  using C = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  if (!unit_active(g.st, mask, u)) return;
+  if (skip_homog && !g.nonhomog[u / g.P]) return;
+  const int x0 = blockIdx.x * NV;
+  const C* in = src.at(u, c, g.npts);
+  for (int e = threadIdx.x; e < NY * NV; e += NT) {
+    const int n = e / NV, v = e % NV;
+    s[n * NV + v] = in[(long)n * g.nx + x0 + v];
+  }
+  __syncthreads();
+  if (fwd) fft_smem<C, NY, false, NV, NT, true>(s, g.twy, threadIdx.x);
+  if (mul != MUL_NONE) {
+    const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD);
+    const int k = pm ? (pole >= 0 ? pole : u % g.P) : 0;
+    const T* ax = pm ? g.ax + (long)k * g.nx * 2 : nullptr;
+    const T* ay = pm ? g.ay + (long)k * g.ny * 2 : nullptr;
+    const T pim = pm ? g.pim[k] : (T)0;
+    for (int e = threadIdx.x; e < NY * NV; e += NT) {
+      const int n = e / NV, v = e % NV, i = x0 + v;
+      C a = s[e];
+      if (mul == MUL_TABLE) {
+        a = cmul(a, g.basemul[(long)n * g.nx + i]);
+      } else if (mul == MUL_SCALE) {
+        a.x *= scale; a.y *= scale;
+      } else {
+        // Re(zeta_fs - p) = ax + ay from (hi, lo) pairs: the hi parts cancel
+        // exactly near the pole (Sterbenz), the lo parts restore the rest.
+        const T re = (ax[2 * i] + ay[2 * n]) + (ax[2 * i + 1] + ay[2 * n + 1]);
+        C f;
+        if (mul == MUL_POLE_INV) {
+          const T d = scale / (re * re + pim * pim);
+          f.x = re * d; f.y = -pim * d;
+        } else {
+          f.x = re * scale; f.y = pim * scale;
+        }
+        a = cmul(a, f);
+      }
+      s[e] = a;
+    }
+    __syncthreads();
+  }
+  if (inv) fft_smem<C, NY, true, NV, NT, true>(s, g.twy, threadIdx.x);
+  C* out = dst.at(u, c, g.npts);
+  for (int e = threadIdx.x; e < NY * NV; e += NT) {
+    const int n = e / NV, v = e % NV;
+    out[(long)n * g.nx + x0 + v] = s[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3: inverse row DFTs and the pointwise epilogue.  grid = (ny/NR, units*ncomp).
+// ---------------------------------------------------------------------------
+struct EpiArgs {
+  int mode;
+  int jj;              // Arnoldi column (EPI_ARNOLDI)
+  const double2* in64; // EPI_OPERATOR input
+  double2* out64;      // EPI_STORE64 / EPI_OPERATOR output
+};
+
+template <typename T, int N, int NR, int NT>
+__global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
+                                                 int mask, int skip_homog, EpiArgs ep) {
+  using C = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[32];
+  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  if (!unit_active(g.st, mask, u)) return;
+  const bool sys = (ep.mode == EPI_R0 || ep.mode == EPI_ARNOLDI || ep.mode == EPI_TRUERES);
+  const int beam = sys ? u / g.P : u;
+  if (skip_homog && !g.nonhomog[beam]) return;
+  const int row0 = blockIdx.x * NR;
+  const long off = (long)row0 * N;
+  const C* in = src.at(u, c, g.npts) + off;
+  for (int e = threadIdx.x; e < NR * N; e += NT) s[sidx<N, NR, false>(e / N, e % N)] = in[e];
+  __syncthreads();
+  fft_smem<C, N, true, NR, NT, false>(s, g.twx, threadIdx.x);
+  const C* dl = g.delta + (long)beam * g.npts + off;
+  const long unit_off = ((long)u * g.ncomp + c) * g.npts + off;   // [unit][c][pt] arrays
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < NR * N; e += NT) {
+    const C val = s[sidx<N, NR, false>(e / N, e % N)];
+    switch (ep.mode) {
+      case EPI_STORE: dst.at(u, c, g.npts)[off + e] = val; break;
+      case EPI_STORE64: ep.out64[unit_off + e] = to_d(val); break;
+      case EPI_ACCUM64: {   // out64 = W64 + val (the new field, written beside the old one)
+        double2 t = g.W64[unit_off + e];
+        t.x += (double)val.x; t.y += (double)val.y;
+        ep.out64[unit_off + e] = t;
+      } break;
+      case EPI_OPERATOR: {
+        const double2 v = ep.in64[unit_off + e];
+        const double2 d = to_d(dl[e]);
+        double2 o;
+        o.x = (double)val.x + d.x * v.x - d.y * v.y;
+        o.y = (double)val.y + d.x * v.y + d.y * v.x;
+        ep.out64[unit_off + e] = o;
+      } break;
+      case EPI_R0: {
+        const C r = cmul(dl[e], val);
+        C m; m.x = -r.x; m.y = -r.y;
+        g.R0[unit_off + e] = m;
+        acc += (double)m.x * m.x + (double)m.y * m.y;
+      } break;
+      case EPI_ARNOLDI: {
+        const long vb = (((long)u * (g.m + 1) + ep.jj) * g.ncomp + c) * g.npts + off + e;
+        const long zb = (((long)u * g.m + ep.jj) * g.ncomp + c) * g.npts + off + e;
+        g.Zb[zb] = val;
+        const C v = g.V[vb];
+        const C dz = cmul(dl[e], val);
+        C w; w.x = v.x + dz.x; w.y = v.y + dz.y;
+        g.V[vb + (long)g.ncomp * g.npts] = w;
+      } break;
+      case EPI_TRUERES: {
+        const double2 r0 = to_d(g.R0[unit_off + e]);
+        const double2 ee = g.E[unit_off + e];
+        const double2 d = to_d(dl[e]);
+        double2 r;
+        r.x = r0.x - (double)val.x - (d.x * ee.x - d.y * ee.y);
+        r.y = r0.y - (double)val.y - (d.x * ee.y + d.y * ee.x);
+        const long vb = (((long)u * (g.m + 1)) * g.ncomp + c) * g.npts + off + e;
+        g.V[vb] = to_c(r, T());
+        acc += r.x * r.x + r.y * r.y;
+      } break;
+    }
+  }
+  if (ep.mode == EPI_R0 || ep.mode == EPI_TRUERES) {
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&g.st[u].nrm_a, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched Krylov vector kernels.  grid = (chunks, nsys); each CTA owns a
+// contiguous chunk of the system's ncomp*npts points.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ typename Cx<T>::t* vslot(const GV<T>& g, int s, int jj) {
+  return g.V + ((long)s * (g.m + 1) + jj) * g.ncomp * g.npts;
+}
+
+// dots1[i] += <v_i, w>, i <= jj, with w = v_{jj+1}; nrm_b unused here.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_dots(GV<T> g, int jj) {
+  using C = typename Cx<T>::t;
+  __shared__ double red[32];
+  const int s = blockIdx.y;
+  if (g.st[s].state != ST_ITER) return;
+  const long L = (long)g.ncomp * g.npts;
+  const long chunk = (L + gridDim.x - 1) / gridDim.x;
+  const long b0 = blockIdx.x * chunk, b1 = min(L, b0 + chunk);
+  const C* w = vslot(g, s, jj + 1);
+  for (int i = 0; i <= jj; ++i) {
+    const C* v = vslot(g, s, i);
+    double ar = 0.0, ai = 0.0;
+    for (long p = b0 + threadIdx.x; p < b1; p += NT) {
+      const double2 a = to_d(v[p]), b = to_d(w[p]);
+      ar += a.x * b.x + a.y * b.y;
+      ai += a.x * b.y - a.y * b.x;
+    }
+    const double tr = block_sum(ar, red);
+    const double ti = block_sum(ai, red);
+    if (threadIdx.x == 0) {
+      atomicAdd(&g.st[s].dots1[i].x, tr);
+      atomicAdd(&g.st[s].dots1[i].y, ti);
+    }
+  }
+}
+
+// Classical Gram-Schmidt, first subtraction and the re-orthogonalisation dots:
+// w <- w - sum_i dots1[i] v_i; dots2[i] += <v_i, w>; nrm_b += ||w||^2.
+template <typename T, int NT, int EPT>
+__global__ void __launch_bounds__(NT) k_cgs(GV<T> g, int jj) {
+  using C = typename Cx<T>::t;
+  __shared__ double red[32];
+  __shared__ C h[MMAX + 1];
+  const int s = blockIdx.y;
+  if (g.st[s].state != ST_ITER) return;
+  for (int i = threadIdx.x; i <= jj; i += NT) {
+    const double2 d = g.st[s].dots1[i];
+    h[i].x = (T)d.x; h[i].y = (T)d.y;
+  }
+  __syncthreads();
+  const long L = (long)g.ncomp * g.npts;
+  C* w = vslot(g, s, jj + 1);
+  const long per = (long)NT * EPT;
+  for (long b0 = (long)blockIdx.x * per; b0 < L; b0 += (long)gridDim.x * per) {
+    C x[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const long p = b0 + threadIdx.x + (long)q * NT;
+      x[q] = p < L ? w[p] : C{};
+    }
+    for (int i = 0; i <= jj; ++i) {
+      const C* v = vslot(g, s, i);
+      const C hi = h[i];
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const long p = b0 + threadIdx.x + (long)q * NT;
+        if (p < L) { const C t = cmul(hi, v[p]); x[q].x -= t.x; x[q].y -= t.y; }
+      }
+    }
+    double nr = 0.0;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const long p = b0 + threadIdx.x + (long)q * NT;
+      if (p < L) { w[p] = x[q]; nr += (double)x[q].x * x[q].x + (double)x[q].y * x[q].y; }
+    }
+    const double tn = block_sum(nr, red);
+    if (threadIdx.x == 0) atomicAdd(&g.st[s].nrm_b, tn);
+    for (int i = 0; i <= jj; ++i) {
+      const C* v = vslot(g, s, i);
+      double ar = 0.0, ai = 0.0;
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const long p = b0 + threadIdx.x + (long)q * NT;
+        if (p < L) {
+          const double2 a = to_d(v[p]), b = to_d(x[q]);
+          ar += a.x * b.x + a.y * b.y;
+          ai += a.x * b.y - a.y * b.x;
+        }
+      }
+      const double tr = block_sum(ar, red);
+      const double ti = block_sum(ai, red);
+      if (threadIdx.x == 0) {
+        atomicAdd(&g.st[s].dots2[i].x, tr);
+        atomicAdd(&g.st[s].dots2[i].y, ti);
+      }
+    }
+  }
+}
+
+// v_{jj+1} = (w - sum_i coef[i] v_i) * scale  for systems still iterating.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_normalize(GV<T> g, int jj) {
+  using C = typename Cx<T>::t;
+  __shared__ C h[MMAX + 1];
+  const int s = blockIdx.y;
+  if (g.st[s].state != ST_ITER) return;
+  for (int i = threadIdx.x; i <= jj; i += NT) {
+    const double2 d = g.st[s].coef[i];
+    h[i].x = (T)d.x; h[i].y = (T)d.y;
+  }
+  __syncthreads();
+  const T sc = (T)g.st[s].scale;
+  const long L = (long)g.ncomp * g.npts;
+  C* w = vslot(g, s, jj + 1);
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
+    C x = w[p];
+    for (int i = 0; i <= jj; ++i) {
+      const C t = cmul(h[i], vslot(g, s, i)[p]);
+      x.x -= t.x; x.y -= t.y;
+    }
+    x.x *= sc; x.y *= sc;
+    w[p] = x;
+  }
+}
+
+// v_0 *= scale (start of a cycle)
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_scale_v0(GV<T> g) {
+  using C = typename Cx<T>::t;
+  const int s = blockIdx.y;
+  if (g.st[s].state != ST_ITER || g.st[s].j != 0) return;
+  const T sc = (T)g.st[s].scale;
+  const long L = (long)g.ncomp * g.npts;
+  C* w = vslot(g, s, 0);
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
+    C x = w[p]; x.x *= sc; x.y *= sc; w[p] = x;
+  }
+}
+
+// v_0 = R0 (copy, first cycle) and E = 0 for every system.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_init_systems(GV<T> g) {
+  const int s = blockIdx.y;
+  const long L = (long)g.ncomp * g.npts;
+  const bool it = g.st[s].state == ST_ITER;
+  auto* v = vslot(g, s, 0);
+  const auto* r = g.R0 + (long)s * L;
+  double2* e = g.E + (long)s * L;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
+    if (it) v[p] = r[p];
+    e[p] = make_double2(0.0, 0.0);
+  }
+}
+
+// E += sum_{i < jend} y_i z_i  (FP64 accumulation) for systems at a cycle end.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_update_e(GV<T> g) {
+  const int s = blockIdx.y;
+  const SysState& st = g.st[s];
+  if (st.state != ST_CYCLE_END) return;
+  const int J = st.jend;
+  const long L = (long)g.ncomp * g.npts;
+  double2* e = g.E + (long)s * L;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
+    double2 a = e[p];
+    for (int i = 0; i < J; ++i) {
+      const double2 z = to_d(g.Zb[((long)s * g.m + i) * L + p]);
+      const double2 y = st.y[i];
+      a.x += y.x * z.x - y.y * z.y;
+      a.y += y.x * z.y + y.y * z.x;
+    }
+    e[p] = a;
+  }
+}
+
+// Wn[b] += sum_k r_k E[b, k]  (the residue sum of Eq. approx_prop, correction part).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_residue_sum(GV<T> g, double2* Wn) {
+  const int b = blockIdx.y;
+  const long L = (long)g.ncomp * g.npts;
+  double2* w = Wn + (long)b * L;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
+    double2 a = w[p];
+    for (int k = 0; k < g.P; ++k) {
+      const double2 e = g.E[((long)b * g.P + k) * L + p];
+      const double2 r = g.rk[k];
+      a.x += r.x * e.x - r.y * e.y;
+      a.y += r.x * e.y + r.y * e.x;
+    }
+    w[p] = a;
+  }
+}
+
+// delta = (n^2 - n0^2)/n0^2 from a complex128 slab; flags a non-zero delta.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2* n2, double n0sq) {
+  using C = typename Cx<T>::t;
+  C* d = g.delta + (long)beam * g.npts;
+  int nz = 0;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < g.npts; p += (long)gridDim.x * NT) {
+    const double2 a = n2[p];
+    double2 v; v.x = (a.x - n0sq) / n0sq; v.y = a.y / n0sq;
+    const C t = to_c(v, T());
+    d[p] = t;
+    nz |= (t.x != (T)0 || t.y != (T)0);
+  }
+  if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&g.nonhomog[beam], 1);
+}
+
+// ---------------------------------------------------------------------------
+// GMRES control (one thread per system; tiny).
+// ---------------------------------------------------------------------------
+
+// Begin a cycle for systems in state `from` (ST_DONE-initialised systems at a
+// step start use from = -1): beta = ||r||; converged if beta <= tol ||w||.
+__global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm2, double tol,
+                              int from, int max_cycles, int first) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    SysState& q = st[s];
+    if (!first && q.state != from) continue;
+    if (first) { q.iters = 0; q.cycles = 0; q.flags = 0; }
+    const double beta = sqrt(q.nrm_a);
+    const double wn = sqrt(bnorm2[s / P]);
+    q.nrm_a = 0.0;
+    q.beta = beta;
+    q.resid = wn > 0 ? beta / wn : 0.0;
+    if (!isfinite(beta)) { q.flags |= 1; q.state = ST_DONE; continue; }
+    if (beta <= tol * wn) { q.state = ST_DONE; continue; }
+    if (q.cycles >= max_cycles) { q.flags |= 2; q.state = ST_DONE; continue; }
+    q.cycles += 1;
+    q.state = ST_ITER;
+    q.j = 0;
+    q.scale = 1.0 / beta;
+    for (int i = 0; i <= MMAX; ++i) { q.g[i] = make_double2(0.0, 0.0); q.dots1[i] = q.g[i]; q.dots2[i] = q.g[i]; }
+    q.g[0] = make_double2(beta, 0.0);
+    q.nrm_b = 0.0;
+  }
+}
+
+__device__ __forceinline__ double2 dmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double dabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// After the dots of Arnoldi column jj: form h, rotate with the previous Givens
+// rotations, make the new one, update g and the residual estimate |g[jj+1]|;
+// end the cycle on convergence, breakdown or jj+1 == m (solving R y = g).
+__global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bnorm2, double tol,
+                                 int m, int jj, double breakdown) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    SysState& q = st[s];
+    if (q.state != ST_ITER) continue;
+    const int L = MMAX + 1;
+    double2* col = &q.H[jj * L];
+    double d2 = 0.0;
+    for (int i = 0; i <= jj; ++i) {
+      col[i] = make_double2(q.dots1[i].x + q.dots2[i].x, q.dots1[i].y + q.dots2[i].y);
+      d2 += dabs2(q.dots2[i]);
+      q.coef[i] = q.dots2[i];
+    }
+    const double hn = sqrt(fmax(q.nrm_b - d2, 0.0));
+    col[jj + 1] = make_double2(hn, 0.0);
+    // previous rotations
+    for (int i = 0; i < jj; ++i) {
+      const double2 a = col[i], b = col[i + 1];
+      const double c = q.cs[i];
+      const double2 sn = q.sn[i];
+      col[i] = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
+      const double2 t = dmul(dconj(sn), a);
+      col[i + 1] = make_double2(c * b.x - t.x, c * b.y - t.y);
+    }
+    // new rotation zeroing col[jj+1]
+    const double2 a = col[jj];
+    const double an = sqrt(dabs2(a));
+    const double r = sqrt(an * an + hn * hn);
+    double c; double2 sn;
+    if (hn == 0.0) { c = 1.0; sn = make_double2(0.0, 0.0); }
+    else if (an == 0.0) { c = 0.0; sn = make_double2(1.0, 0.0); }
+    else { c = an / r; sn = make_double2(a.x / an * hn / r, a.y / an * hn / r); }
+    q.cs[jj] = c; q.sn[jj] = sn;
+    col[jj] = (an == 0.0) ? make_double2(hn, 0.0) : make_double2(a.x / an * r, a.y / an * r);
+    col[jj + 1] = make_double2(0.0, 0.0);
+    const double2 gj = q.g[jj];
+    q.g[jj] = make_double2(c * gj.x, c * gj.y);
+    const double2 t = dmul(dconj(sn), gj);
+    q.g[jj + 1] = make_double2(-t.x, -t.y);
+    q.iters += 1;
+    q.j = jj + 1;
+    const double est = sqrt(dabs2(q.g[jj + 1]));
+    const double wn = sqrt(bnorm2[s / P]);
+    for (int i = 0; i <= jj + 1; ++i) { q.dots1[i] = make_double2(0.0, 0.0); q.dots2[i] = q.dots1[i]; }
+    const double nb = q.nrm_b;
+    q.nrm_b = 0.0;
+    if (!isfinite(est) || !isfinite(hn)) { q.flags |= 1; q.state = ST_DONE; continue; }
+    if (est <= tol * wn || jj + 1 == m || hn <= breakdown * sqrt(fmax(nb, 0.0)) || hn == 0.0) {
+      const int J = jj + 1;
+      for (int i = J - 1; i >= 0; --i) {
+        double2 acc = q.g[i];
+        for (int k2 = i + 1; k2 < J; ++k2) {
+          const double2 t2 = dmul(q.H[k2 * L + i], q.y[k2]);
+          acc.x -= t2.x; acc.y -= t2.y;
+        }
+        const double2 d = q.H[i * L + i];
+        const double dd = dabs2(d);
+        q.y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+      }
+      q.jend = J;
+      q.state = ST_CYCLE_END;
+    } else {
+      q.scale = 1.0 / hn;
+    }
+  }
+}
+
+// compact per-system statistics for the host
+__global__ void k_collect(const SysState* st, int nsys, int* iters, int* cycles, double* resid, int* flags) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    iters[s] = st[s].iters; cycles[s] = st[s].cycles; resid[s] = st[s].resid; flags[s] = st[s].flags;
+  }
+}
+
+// counts[0] = systems iterating, counts[1] = at a cycle end, counts[2] = flags
+__global__ void k_count(const SysState* st, int nsys, int* counts) {
+  __shared__ int c0, c1, c2;
+  if (threadIdx.x == 0) { c0 = 0; c1 = 0; c2 = 0; }
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+    if (st[s].state == ST_ITER) atomicAdd(&c0, 1);
+    if (st[s].state == ST_CYCLE_END) atomicAdd(&c1, 1);
+    if (st[s].flags) atomicOr(&c2, st[s].flags);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) { counts[0] = c0; counts[1] = c1; counts[2] = c2; }
+}
+
+}  // namespace prop_dev

@@ -1,0 +1,727 @@
+// C ABI of the propagator (include/prop.h): handle, workspace carve-up, launch
+// dispatch and the z-step driver.
+//
+// One step, per group of equal-grid beams (Eqs. approx_prop, W_k_def):
+//   w_hat = FFT2(w)                                   (shared by every pole)
+//   w_new = w + IFFT2[(r(zeta_fs) - 1) w_hat]          (free-space part, Eq. approx_fs_prop)
+//   for each pole k:  z_k = IFFT2[w_hat/(zeta_fs - p_k)] (the preconditioner of Sec. 4.2)
+//                     solve (Z - p_k) e_k = -delta z_k by GMRES right-preconditioned
+//                     with (Z_fs - p_k)^-1, x0 = 0
+//   w_new += sum_k r_k e_k
+// Since x_k = z_k + e_k solves (Z - p_k) x_k = w, this is r0 w + sum_k r_k x_k
+// written so that rounding errors scale with the increment, not with w; the
+// field itself is accumulated in FP64.
+#include "../../include/prop.h"
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace prop_dev;
+using cplx = std::complex<double>;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool supported_n(int n) {
+  switch (n) {
+    case 16: case 32: case 64: case 128: case 256: case 384: case 512: case 768: case 1024: return true;
+    default: return false;
+  }
+}
+
+template <typename T> constexpr int cols_per_cta() { return sizeof(T) == 4 ? 8 : 4; }
+constexpr int NT_PASS = 256;
+constexpr int NT_VEC = 256;
+constexpr int EPT_CGS = 4;
+
+struct Layout {
+  size_t V, Zb, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
+      rk, stage, iters, cycles, resid, flags, end;
+};
+
+struct Group {
+  int nx, ny;
+  double dx, dy;
+  std::vector<int> beams;  // global beam ids in slot order
+  long npts;
+  Layout off;
+  int cur;                 // which of W64a / W64b holds the field
+};
+
+}  // namespace
+
+struct prop {
+  int nbeams, P, C, prec, m, max_restarts;
+  double tol, k0, n0, dz;
+  std::vector<cplx> poles, res;
+  cplx r0;
+  std::vector<prop_grid> grids;
+  std::vector<int> beam_group, beam_slot;
+  std::vector<Group> groups;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  size_t counts_off;
+  int64_t steps, total_iters;
+  int last_status;
+};
+
+namespace {
+
+size_t elem_size(int prec) { return prec == PROP_FP64 ? sizeof(double) : sizeof(float); }
+
+// Carve one group's buffers starting at `base`; returns the end offset.
+size_t carve(Group& G, size_t base, int P, int C, int m, int prec) {
+  const size_t es = elem_size(prec), cs = 2 * es;
+  const size_t nb = G.beams.size(), nsys = nb * P, npts = G.npts;
+  Layout& L = G.off;
+  size_t o = align_up(base);
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
+  L.V = take(nsys * (m + 1) * C * npts * cs);
+  L.Zb = take(nsys * m * C * npts * cs);
+  L.R0 = take(nsys * C * npts * cs);
+  L.E = take(nsys * C * npts * 16);
+  L.Tmp = take(nsys * C * npts * cs);
+  L.W64a = take(nb * C * npts * 16);
+  L.W64b = take(nb * C * npts * 16);
+  L.What = take(nb * C * npts * cs);
+  L.Btmp = take(nb * C * npts * cs);
+  L.delta = take(nb * npts * cs);
+  L.basemul = take(npts * cs);
+  L.ax = take((P + 1) * G.nx * 2 * es);
+  L.ay = take((P + 1) * G.ny * 2 * es);
+  L.pim = take((P + 1) * es);
+  L.twx = take(G.nx * cs);
+  L.twy = take(G.ny * cs);
+  L.st = take(nsys * sizeof(SysState));
+  L.bnorm2 = take(nb * sizeof(double));
+  L.nonhomog = take(nb * sizeof(int));
+  L.rk = take(P * 16);
+  L.stage = take(npts * 16);
+  L.iters = take(nsys * sizeof(int));
+  L.cycles = take(nsys * sizeof(int));
+  L.resid = take(nsys * sizeof(double));
+  L.flags = take(nsys * sizeof(int));
+  L.end = o;
+  return o;
+}
+
+template <typename T> GV<T> view(const prop* h, const Group& G) {
+  using C = typename Cx<T>::t;
+  char* b = h->ws;
+  const Layout& L = G.off;
+  GV<T> g;
+  g.nx = G.nx; g.ny = G.ny; g.ncomp = h->C; g.P = h->P; g.m = h->m;
+  g.nb = (int)G.beams.size(); g.nsys = g.nb * h->P; g.npts = G.npts;
+  g.V = (C*)(b + L.V); g.Zb = (C*)(b + L.Zb); g.R0 = (C*)(b + L.R0); g.E = (double2*)(b + L.E);
+  g.Tmp = (C*)(b + L.Tmp);
+  g.W64 = (double2*)(b + (G.cur == 0 ? L.W64a : L.W64b));
+  g.What = (C*)(b + L.What); g.Btmp = (C*)(b + L.Btmp); g.delta = (C*)(b + L.delta);
+  g.basemul = (C*)(b + L.basemul);
+  g.ax = (const T*)(b + L.ax); g.ay = (const T*)(b + L.ay); g.pim = (const T*)(b + L.pim);
+  g.twx = (const C*)(b + L.twx); g.twy = (const C*)(b + L.twy);
+  g.st = (SysState*)(b + L.st); g.bnorm2 = (double*)(b + L.bnorm2); g.nonhomog = (int*)(b + L.nonhomog);
+  g.rk = (const double2*)(b + L.rk);
+  return g;
+}
+
+template <typename C> Buf<C> buf(C* base, long ustride, int div = 1) { Buf<C> b; b.base = base; b.ustride = ustride; b.div = div; return b; }
+
+// ---------------------------------------------------------------------------
+// Launch dispatch over the compiled sizes
+// ---------------------------------------------------------------------------
+template <typename T, int N> constexpr int NRC() { return N <= 256 ? 16 : (N <= 512 ? 8 : 4); }
+
+template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int N, typename SRC>
+cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst, int mask, double* nacc,
+                       int units, cudaStream_t st) {
+  using C = typename Cx<T>::t;
+  constexpr int NR = NRC<T, N>();
+  const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
+  auto k = k_rows_fwd<T, N, NR, NT_PASS, SRC>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(g.ny / NR, units * g.ncomp);
+  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, nacc);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask,
+                       int skip, EpiArgs ep, int units, cudaStream_t st) {
+  using C = typename Cx<T>::t;
+  constexpr int NR = NRC<T, N>();
+  const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
+  auto k = k_rows_inv<T, N, NR, NT_PASS>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(g.ny / NR, units * g.ncomp);
+  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, skip, ep);
+  return cudaGetLastError();
+}
+
+template <typename T, int NY>
+cudaError_t cols_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
+                   int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st) {
+  using C = typename Cx<T>::t;
+  constexpr int NV = cols_per_cta<T>();
+  const size_t sm = smem_elems<NY, NV, true>() * sizeof(C);
+  auto k = k_cols<T, NY, NV, NT_PASS>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid(g.nx / NV, units * g.ncomp);
+  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale);
+  return cudaGetLastError();
+}
+
+#define PROP_SIZE_SWITCH(n, CALL)                      \
+  switch (n) {                                         \
+    case 16: return CALL(16);                          \
+    case 32: return CALL(32);                          \
+    case 64: return CALL(64);                          \
+    case 128: return CALL(128);                        \
+    case 256: return CALL(256);                        \
+    case 384: return CALL(384);                        \
+    case 512: return CALL(512);                        \
+    case 768: return CALL(768);                        \
+    case 1024: return CALL(1024);                      \
+    default: return cudaErrorInvalidValue;             \
+  }
+
+template <typename T, typename SRC>
+cudaError_t rows_fwd(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst, int mask, double* nacc, int units,
+                     cudaStream_t st) {
+#define CALL(N) rows_fwd_n<T, N, SRC>(g, src, dst, mask, nacc, units, st)
+  PROP_SIZE_SWITCH(g.nx, CALL)
+#undef CALL
+}
+template <typename T>
+cudaError_t rows_inv(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int skip,
+                     EpiArgs ep, int units, cudaStream_t st) {
+#define CALL(N) rows_inv_n<T, N>(g, src, dst, mask, skip, ep, units, st)
+  PROP_SIZE_SWITCH(g.nx, CALL)
+#undef CALL
+}
+template <typename T>
+cudaError_t cols(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd, int mul,
+                 int inv, int skip, int pole, T scale, int units, cudaStream_t st) {
+#define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st)
+  PROP_SIZE_SWITCH(g.ny, CALL)
+#undef CALL
+}
+
+EpiArgs epi(int mode, int jj = 0, const double2* in64 = nullptr, double2* out64 = nullptr) {
+  EpiArgs e; e.mode = mode; e.jj = jj; e.in64 = in64; e.out64 = out64; return e;
+}
+
+int vec_blocks(long L) { return (int)std::max<long>(1, std::min<long>(1024, (L + NT_VEC * 16 - 1) / (NT_VEC * 16))); }
+
+#define CK(...)                                      \
+  do {                                               \
+    cudaError_t e_ = (__VA_ARGS__);                  \
+    if (e_ != cudaSuccess) return PROP_E_CUDA;       \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Host-side tables
+// ---------------------------------------------------------------------------
+template <typename T> void twiddles(int n, std::vector<T>& out) {
+  out.resize(2 * n);
+  for (int m = 0; m < n; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)n;
+    out[2 * m] = (T)std::cos(a);
+    out[2 * m + 1] = (T)std::sin(a);
+  }
+}
+
+double kfreq(int i, int n, double d) {   // angular wavenumber of FFT index i
+  const int f = (i < (n + 1) / 2) ? i : i - n;
+  return 2.0 * M_PI * (double)f / ((double)n * d);
+}
+
+// -k^2/(k0n0)^2 - Re p/2 as (hi, lo) pairs for each pole and the zero pole
+template <typename T> void axis_table(int n, double d, double k0n0, const std::vector<cplx>& poles, std::vector<T>& out) {
+  const int P = (int)poles.size();
+  out.resize((size_t)(P + 1) * n * 2);
+  for (int k = 0; k <= P; ++k) {
+    const double pre = k < P ? poles[k].real() : 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double kk = kfreq(i, n, d);
+      const double v = -(kk * kk) / (k0n0 * k0n0) - 0.5 * pre;
+      const T hi = (T)v;
+      const T lo = (T)(v - (double)hi);
+      out[((size_t)k * n + i) * 2] = hi;
+      out[((size_t)k * n + i) * 2 + 1] = lo;
+    }
+  }
+}
+
+template <typename T> int upload_group_tables(prop* h, Group& G) {
+  const double k0n0 = h->k0 * h->n0;
+  std::vector<T> tw;
+  char* b = h->ws;
+  twiddles<T>(G.nx, tw);
+  CK(cudaMemcpyAsync(b + G.off.twx, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  std::vector<T> twy;
+  twiddles<T>(G.ny, twy);
+  CK(cudaMemcpyAsync(b + G.off.twy, twy.data(), twy.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  std::vector<T> ax, ay;
+  axis_table<T>(G.nx, G.dx, k0n0, h->poles, ax);
+  axis_table<T>(G.ny, G.dy, k0n0, h->poles, ay);
+  CK(cudaMemcpyAsync(b + G.off.ax, ax.data(), ax.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(b + G.off.ay, ay.data(), ay.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  std::vector<T> pim(h->P + 1);
+  for (int k = 0; k < h->P; ++k) pim[k] = (T)(-h->poles[k].imag());
+  pim[h->P] = (T)0;
+  CK(cudaMemcpyAsync(b + G.off.pim, pim.data(), pim.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  // (r(zeta_fs) - 1)/(nx ny), r evaluated in FP64 and rounded once
+  std::vector<T> bm((size_t)G.npts * 2);
+  const double sc = 1.0 / (double)G.npts;
+  std::vector<double> kx2(G.nx), ky2(G.ny);
+  for (int i = 0; i < G.nx; ++i) { const double k = kfreq(i, G.nx, G.dx); kx2[i] = k * k / (k0n0 * k0n0); }
+  for (int j = 0; j < G.ny; ++j) { const double k = kfreq(j, G.ny, G.dy); ky2[j] = k * k / (k0n0 * k0n0); }
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i) {
+      const cplx z(-(kx2[i] + ky2[j]), 0.0);
+      cplx r = h->r0 - 1.0;
+      for (int k = 0; k < h->P; ++k) r += h->res[k] / (z - h->poles[k]);
+      r *= sc;
+      bm[((size_t)j * G.nx + i) * 2] = (T)r.real();
+      bm[((size_t)j * G.nx + i) * 2 + 1] = (T)r.imag();
+    }
+  CK(cudaMemcpyAsync(b + G.off.basemul, bm.data(), bm.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  std::vector<double> rk(2 * h->P);
+  for (int k = 0; k < h->P; ++k) { rk[2 * k] = h->res[k].real(); rk[2 * k + 1] = h->res[k].imag(); }
+  CK(cudaMemcpyAsync(b + G.off.rk, rk.data(), rk.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  // the host vectors must outlive the async copies
+  CK(cudaStreamSynchronize(h->stream));
+  return PROP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The step
+// ---------------------------------------------------------------------------
+int read_counts(prop* h, int* c3) {
+  if (cudaMemcpyAsync(c3, h->ws + h->counts_off, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return PROP_E_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PROP_E_CUDA;
+  return PROP_OK;
+}
+
+template <typename T> int step_group(prop* h, Group& G) {
+  using C = typename Cx<T>::t;
+  GV<T> g = view<T>(h, G);
+  cudaStream_t st = h->stream;
+  const int Cn = h->C, P = h->P, nb = g.nb, nsys = g.nsys, m = h->m;
+  const long F = (long)Cn * g.npts;                       // one field
+  const T scale = (T)(1.0 / (double)g.npts);
+  int* counts = (int*)(h->ws + h->counts_off);
+  double2* Wn = (double2*)(h->ws + (G.cur == 0 ? G.off.W64b : G.off.W64a));
+
+  // w_hat = FFT2(w); ||w||^2 per beam
+  CK(cudaMemsetAsync(g.bnorm2, 0, nb * sizeof(double), st));
+  CK(rows_fwd<T, double2>(g, buf(g.W64, F), buf(g.Btmp, F), -1, g.bnorm2, nb, st));
+  CK(cols<T>(g, buf(g.Btmp, F), buf(g.What, F), -1, 1, MUL_NONE, 0, 0, -1, (T)1, nb, st));
+  // free-space part: Wn = w + IFFT2[(r - 1) w_hat]
+  CK(cols<T>(g, buf(g.What, F), buf(g.Btmp, F), -1, 0, MUL_TABLE, 1, 0, -1, (T)1, nb, st));
+  CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0, epi(EPI_ACCUM64, 0, nullptr, Wn), nb, st));
+  // correction systems: R0_k = -delta * IFFT2[w_hat/(zeta - p_k)]
+  CK(cols<T>(g, buf(g.What, F, P), buf(g.Tmp, F), -1, 0, MUL_POLE_INV, 1, 1, -1, scale, nsys, st));
+  CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), -1, 1, epi(EPI_R0), nsys, st));
+  const int tb = 128, tg = (nsys + tb - 1) / tb;
+  k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1);
+  const int vb = vec_blocks(F);
+  k_init_systems<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
+  k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
+  CK(cudaGetLastError());
+
+  const double breakdown = sizeof(T) == 4 ? 1e-6 : 1e-14;
+  int c3[3];
+  k_count<<<1, 256, 0, st>>>(g.st, nsys, counts);
+  int rc = read_counts(h, c3);
+  if (rc) return rc;
+  while (c3[0] > 0) {
+    for (int jj = 0; jj < m; ++jj) {
+      C* Vj = g.V + (long)jj * F;
+      const long vs = (long)(m + 1) * F;
+      CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st));
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st));
+      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st));
+      k_dots<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj);
+      k_cgs<T, NT_VEC, EPT_CGS><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj);
+      k_arnoldi_finish<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown);
+      k_normalize<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj);
+      k_count<<<1, 256, 0, st>>>(g.st, nsys, counts);
+      CK(cudaGetLastError());
+      rc = read_counts(h, c3);
+      if (rc) return rc;
+      if (c3[0] == 0) break;
+    }
+    if (c3[1] == 0) break;
+    // cycle end: e += M^-1 V y (stored z_j), true residual r = R0 - (Z - p) e
+    k_update_e<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
+    CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st));
+    CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st));
+    CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st));
+    k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0);
+    k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
+    k_count<<<1, 256, 0, st>>>(g.st, nsys, counts);
+    CK(cudaGetLastError());
+    rc = read_counts(h, c3);
+    if (rc) return rc;
+  }
+  if (c3[2] & 1) return PROP_E_NAN;
+  if (c3[2] & 2) return PROP_E_NOCONV;
+  k_residue_sum<T, NT_VEC><<<dim3(vb, nb), NT_VEC, 0, st>>>(g, Wn);
+  CK(cudaGetLastError());
+  G.cur ^= 1;   // commit: the new field becomes current
+  return PROP_OK;
+}
+
+int validate_opts(const prop_opts* o) {
+  if (!o) return PROP_E_ARG;
+  if (o->ncomp != 1) return PROP_E_UNSUPPORTED;
+  if (o->precision != PROP_FP32 && o->precision != PROP_FP64) return PROP_E_ARG;
+  if (o->restart < 1 || o->restart > MMAX) return PROP_E_ARG;
+  if (o->max_restarts < 1) return PROP_E_ARG;
+  if (!(o->tol > 0.0)) return PROP_E_ARG;
+  return PROP_OK;
+}
+
+int build_groups(int nbeams, const prop_grid* grids, std::vector<Group>& groups, std::vector<int>& bg,
+                 std::vector<int>& bs) {
+  groups.clear();
+  bg.assign(nbeams, -1);
+  bs.assign(nbeams, -1);
+  for (int b = 0; b < nbeams; ++b) {
+    const prop_grid& gr = grids[b];
+    if (!supported_n(gr.nx) || !supported_n(gr.ny)) return PROP_E_UNSUPPORTED;
+    if (!(gr.dx > 0) || !(gr.dy > 0)) return PROP_E_ARG;
+    int gi = -1;
+    for (size_t i = 0; i < groups.size(); ++i)
+      if (groups[i].nx == gr.nx && groups[i].ny == gr.ny && groups[i].dx == gr.dx && groups[i].dy == gr.dy) gi = (int)i;
+    if (gi < 0) {
+      Group G;
+      G.nx = gr.nx; G.ny = gr.ny; G.dx = gr.dx; G.dy = gr.dy; G.npts = (long)gr.nx * gr.ny; G.cur = 0;
+      groups.push_back(G);
+      gi = (int)groups.size() - 1;
+    }
+    bg[b] = gi;
+    bs[b] = (int)groups[gi].beams.size();
+    groups[gi].beams.push_back(b);
+  }
+  return PROP_OK;
+}
+
+size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, size_t* counts_off) {
+  size_t o = 0;
+  for (Group& G : groups) o = carve(G, o, P, C, m, prec);
+  *counts_off = align_up(o);
+  return *counts_off + ALIGN;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision) {
+  if (!o) return PROP_E_ARG;
+  o->ncomp = ncomp;
+  o->precision = precision;
+  o->restart = 20;
+  o->max_restarts = 50;
+  o->tol = precision == PROP_FP64 ? 1e-12 : 1e-7;
+  return PROP_OK;
+}
+
+int prop_workspace_size(int32_t nbeams, const prop_grid* grids, int32_t npoles, const prop_opts* opts, size_t* bytes) {
+  if (nbeams < 1 || !grids || npoles < 1 || !bytes) return PROP_E_ARG;
+  int rc = validate_opts(opts);
+  if (rc) return rc;
+  std::vector<Group> groups;
+  std::vector<int> bg, bs;
+  rc = build_groups(nbeams, grids, groups, bg, bs);
+  if (rc) return rc;
+  size_t co;
+  *bytes = total_layout(groups, npoles, opts->ncomp, opts->restart, opts->precision, &co);
+  return PROP_OK;
+}
+
+int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, double dz, int32_t npoles,
+                const double* poles, const double* residues, const double r0[2], const prop_opts* opts,
+                void* d_workspace, size_t ws_bytes, void* stream, prop** out) {
+  if (!out) return PROP_E_ARG;
+  *out = nullptr;
+  if (nbeams < 1 || !grids || npoles < 1 || !poles || !residues || !r0) return PROP_E_ARG;
+  if (!(k0 > 0) || !(n0 > 0) || !(dz > 0)) return PROP_E_ARG;
+  int rc = validate_opts(opts);
+  if (rc) return rc;
+  if (!d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return PROP_E_WORKSPACE;
+  prop* h = new (std::nothrow) prop();
+  if (!h) return PROP_E_ARG;
+  h->nbeams = nbeams; h->P = npoles; h->C = opts->ncomp; h->prec = opts->precision; h->m = opts->restart;
+  h->max_restarts = opts->max_restarts; h->tol = opts->tol; h->k0 = k0; h->n0 = n0; h->dz = dz;
+  h->poles.resize(npoles); h->res.resize(npoles);
+  for (int k = 0; k < npoles; ++k) {
+    h->poles[k] = cplx(poles[2 * k], poles[2 * k + 1]);
+    h->res[k] = cplx(residues[2 * k], residues[2 * k + 1]);
+  }
+  h->r0 = cplx(r0[0], r0[1]);
+  h->grids.assign(grids, grids + nbeams);
+  rc = build_groups(nbeams, grids, h->groups, h->beam_group, h->beam_slot);
+  if (rc) { delete h; return rc; }
+  const size_t need = total_layout(h->groups, h->P, h->C, h->m, h->prec, &h->counts_off);
+  if (ws_bytes < need) { delete h; return PROP_E_WORKSPACE; }
+  h->ws = (char*)d_workspace; h->ws_bytes = ws_bytes;
+  h->stream = (cudaStream_t)stream;
+  h->steps = 0; h->total_iters = 0; h->last_status = 0;
+  if (cudaMemsetAsync(h->ws, 0, need, h->stream) != cudaSuccess) { delete h; return PROP_E_CUDA; }
+  for (Group& G : h->groups) {
+    rc = h->prec == PROP_FP64 ? upload_group_tables<double>(h, G) : upload_group_tables<float>(h, G);
+    if (rc) { delete h; return rc; }
+  }
+  *out = h;
+  return PROP_OK;
+}
+
+int prop_set_medium(prop* h, int32_t beam, const void* n2) {
+  if (!h || !n2 || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
+  Group& G = h->groups[h->beam_group[beam]];
+  const int slot = h->beam_slot[beam];
+  void* stage = h->ws + G.off.stage;
+  CK(cudaMemcpyAsync(stage, n2, G.npts * 16, cudaMemcpyDefault, h->stream));
+  int* nh = (int*)(h->ws + G.off.nonhomog) + slot;
+  CK(cudaMemsetAsync(nh, 0, sizeof(int), h->stream));
+  const int blocks = (int)std::min<long>(1024, (G.npts + 255) / 256);
+  const double n0sq = h->n0 * h->n0;
+  if (h->prec == PROP_FP64) k_medium<double, 256><<<blocks, 256, 0, h->stream>>>(view<double>(h, G), slot, (const double2*)stage, n0sq);
+  else k_medium<float, 256><<<blocks, 256, 0, h->stream>>>(view<float>(h, G), slot, (const double2*)stage, n0sq);
+  CK(cudaGetLastError());
+  return PROP_OK;
+}
+
+int prop_set_field(prop* h, int32_t beam, const void* w) {
+  if (!h || !w || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
+  Group& G = h->groups[h->beam_group[beam]];
+  const long F = (long)h->C * G.npts;
+  char* dst = h->ws + (G.cur == 0 ? G.off.W64a : G.off.W64b) + (size_t)h->beam_slot[beam] * F * 16;
+  CK(cudaMemcpyAsync(dst, w, F * 16, cudaMemcpyDefault, h->stream));
+  h->steps = 0;
+  return PROP_OK;
+}
+
+int prop_get_field(prop* h, int32_t beam, void* w) {
+  if (!h || !w || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
+  Group& G = h->groups[h->beam_group[beam]];
+  const long F = (long)h->C * G.npts;
+  const char* src = h->ws + (G.cur == 0 ? G.off.W64a : G.off.W64b) + (size_t)h->beam_slot[beam] * F * 16;
+  CK(cudaMemcpyAsync(w, src, F * 16, cudaMemcpyDefault, h->stream));
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, w) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return PROP_OK;
+}
+
+int prop_step(prop* h) {
+  if (!h) return PROP_E_ARG;
+  for (Group& G : h->groups) {
+    const int rc = h->prec == PROP_FP64 ? step_group<double>(h, G) : step_group<float>(h, G);
+    if (rc) { h->last_status = rc; return rc; }
+  }
+  h->steps += 1;
+  return PROP_OK;
+}
+
+int prop_run(prop* h, int32_t nsteps, prop_medium_fn cb, void* user) {
+  if (!h || nsteps < 0) return PROP_E_ARG;
+  for (int s = 0; s < nsteps; ++s) {
+    if (cb) {
+      const int rc = cb(h, s, user);
+      if (rc) return rc;
+    }
+    const int rc = prop_step(h);
+    if (rc) return rc;
+  }
+  return PROP_OK;
+}
+
+static int collect(prop* h, std::vector<int>& iters, std::vector<int>& cyc, std::vector<double>& resid) {
+  iters.assign((size_t)h->nbeams * h->P, 0);
+  cyc.assign((size_t)h->nbeams * h->P, 0);
+  resid.assign((size_t)h->nbeams * h->P, 0.0);
+  for (Group& G : h->groups) {
+    const int nsys = (int)G.beams.size() * h->P;
+    int* di = (int*)(h->ws + G.off.iters);
+    int* dc = (int*)(h->ws + G.off.cycles);
+    double* dr = (double*)(h->ws + G.off.resid);
+    int* df = (int*)(h->ws + G.off.flags);
+    k_collect<<<(nsys + 127) / 128, 128, 0, h->stream>>>((SysState*)(h->ws + G.off.st), nsys, di, dc, dr, df);
+    std::vector<int> ti(nsys), tc(nsys);
+    std::vector<double> tr(nsys);
+    CK(cudaMemcpyAsync(ti.data(), di, nsys * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(tc.data(), dc, nsys * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(tr.data(), dr, nsys * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int s = 0; s < nsys; ++s) {
+      const int b = G.beams[s / h->P], k = s % h->P;
+      iters[(size_t)b * h->P + k] = ti[s];
+      cyc[(size_t)b * h->P + k] = tc[s];
+      resid[(size_t)b * h->P + k] = tr[s];
+    }
+  }
+  return PROP_OK;
+}
+
+int prop_get_stats(prop* h, prop_stats* out) {
+  if (!h || !out) return PROP_E_ARG;
+  std::vector<int> it, cy;
+  std::vector<double> rs;
+  const int rc = collect(h, it, cy, rs);
+  if (rc) return rc;
+  out->steps = h->steps;
+  out->npoles = h->P;
+  out->nbeams = h->nbeams;
+  out->last_iters_max = 0; out->last_cycles_max = 0; out->last_iters_sum = 0; out->last_resid_max = 0.0;
+  for (size_t i = 0; i < it.size(); ++i) {
+    out->last_iters_max = std::max(out->last_iters_max, it[i]);
+    out->last_cycles_max = std::max(out->last_cycles_max, cy[i]);
+    out->last_iters_sum += it[i];
+    out->last_resid_max = std::max(out->last_resid_max, rs[i]);
+  }
+  out->total_iters = h->total_iters;
+  return PROP_OK;
+}
+
+int prop_get_iterations(prop* h, int32_t* iters) {
+  if (!h || !iters) return PROP_E_ARG;
+  std::vector<int> it, cy;
+  std::vector<double> rs;
+  const int rc = collect(h, it, cy, rs);
+  if (rc) return rc;
+  std::memcpy(iters, it.data(), it.size() * sizeof(int));
+  return PROP_OK;
+}
+
+const char* prop_error_string(int status) {
+  switch (status) {
+    case PROP_OK: return "ok";
+    case PROP_E_ARG: return "invalid argument";
+    case PROP_E_WORKSPACE: return "workspace missing, misaligned or too small";
+    case PROP_E_CUDA: return "CUDA runtime error";
+    case PROP_E_NOCONV: return "GMRES did not converge within max_restarts";
+    case PROP_E_NAN: return "NaN or Inf in a residual";
+    case PROP_E_UNSUPPORTED: return "unsupported grid size or mode";
+    default: return "unknown status";
+  }
+}
+
+void prop_destroy(prop* h) { delete h; }
+
+// ---- building blocks --------------------------------------------------------
+
+int prop_fft2_workspace_size(int32_t nx, int32_t ny, int32_t precision, size_t* bytes) {
+  if (!bytes) return PROP_E_ARG;
+  if (!supported_n(nx) || !supported_n(ny)) return PROP_E_UNSUPPORTED;
+  const size_t cs = 2 * elem_size(precision);
+  *bytes = align_up(nx * cs) + align_up(ny * cs);
+  return PROP_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int fft2_impl(int nx, int ny, int batch, int inverse, void* data, void* work, cudaStream_t st) {
+  using C = typename Cx<T>::t;
+  std::vector<T> tx, ty;
+  twiddles<T>(nx, tx);
+  twiddles<T>(ny, ty);
+  char* w = (char*)work;
+  const size_t ox = 0, oy = align_up(nx * sizeof(C));
+  CK(cudaMemcpyAsync(w + ox, tx.data(), tx.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(w + oy, ty.data(), ty.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  GV<T> g;
+  std::memset(&g, 0, sizeof(g));
+  g.nx = nx; g.ny = ny; g.ncomp = 1; g.P = 1; g.m = 1; g.nb = batch; g.nsys = batch; g.npts = (long)nx * ny;
+  g.twx = (const C*)(w + ox); g.twy = (const C*)(w + oy);
+  C* d = (C*)data;
+  const long F = g.npts;
+  if (!inverse) {
+    CK(rows_fwd<T, C>(g, buf(d, F), buf(d, F), -1, nullptr, batch, st));
+    CK(cols<T>(g, buf(d, F), buf(d, F), -1, 1, MUL_NONE, 0, 0, -1, (T)1, batch, st));
+  } else {
+    CK(cols<T>(g, buf(d, F), buf(d, F), -1, 0, MUL_SCALE, 1, 0, -1, (T)(1.0 / (double)F), batch, st));
+    CK(rows_inv<T>(g, buf(d, F), buf(d, F), -1, 0, epi(EPI_STORE), batch, st));
+  }
+  CK(cudaStreamSynchronize(st));   // the host twiddle vectors must outlive the copies
+  return PROP_OK;
+}
+
+extern "C" {
+
+int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse, void* d_data, void* d_work,
+              size_t work_bytes, void* stream) {
+  size_t need;
+  int rc = prop_fft2_workspace_size(nx, ny, precision, &need);
+  if (rc) return rc;
+  if (batch < 0 || !d_data || !d_work) return PROP_E_ARG;
+  if (work_bytes < need) return PROP_E_WORKSPACE;
+  if (batch == 0) return PROP_OK;
+  if (precision == PROP_FP64) return fft2_impl<double>(nx, ny, batch, inverse, d_data, d_work, (cudaStream_t)stream);
+  if (precision == PROP_FP32) return fft2_impl<float>(nx, ny, batch, inverse, d_data, d_work, (cudaStream_t)stream);
+  return PROP_E_ARG;
+}
+
+}  // extern "C"
+
+template <typename T> static int apply_impl(prop* h, int beam, int pole, const void* v, void* out, bool op) {
+  using C = typename Cx<T>::t;
+  Group& G = h->groups[h->beam_group[beam]];
+  const int slot = h->beam_slot[beam];
+  GV<T> g = view<T>(h, G);
+  const long F = (long)h->C * g.npts;
+  g.delta += (long)slot * g.npts;
+  C* scratch = g.Btmp + (long)slot * F;
+  const T scale = (T)(1.0 / (double)g.npts);
+  cudaStream_t st = h->stream;
+  CK(rows_fwd<T, double2>(g, buf((double2*)v, F), buf(scratch, F), -1, nullptr, 1, st));
+  CK(cols<T>(g, buf(scratch, F), buf(scratch, F), -1, 1, op ? MUL_POLE_FWD : MUL_POLE_INV, 1, 0,
+             op ? h->P : pole, scale, 1, st));
+  CK(rows_inv<T>(g, buf(scratch, F), buf(scratch, F), -1, 0,
+                 op ? epi(EPI_OPERATOR, 0, (const double2*)v, (double2*)out) : epi(EPI_STORE64, 0, nullptr, (double2*)out),
+                 1, st));
+  return PROP_OK;
+}
+
+extern "C" {
+
+int prop_apply_freespace_inverse(prop* h, int32_t beam, int32_t pole, const void* d_v, void* d_out) {
+  if (!h || !d_v || !d_out || beam < 0 || beam >= h->nbeams || pole < 0 || pole >= h->P) return PROP_E_ARG;
+  return h->prec == PROP_FP64 ? apply_impl<double>(h, beam, pole, d_v, d_out, false)
+                              : apply_impl<float>(h, beam, pole, d_v, d_out, false);
+}
+
+int prop_apply_operator(prop* h, int32_t beam, const void* d_v, void* d_out) {
+  if (!h || !d_v || !d_out || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
+  return h->prec == PROP_FP64 ? apply_impl<double>(h, beam, 0, d_v, d_out, true)
+                              : apply_impl<float>(h, beam, 0, d_v, d_out, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+"""Parity of the CUDA z-step (Eq. approx_prop) with the CPU oracle, through the C ABI.
+
+Bars: relative L2 field error <= 1e-10 where FP64 runs, <= 1e-5 for the FP32
+path (the accuracy bars of the method's configurations)."""
+import math
+
+import numpy as np
+import pytest
+
+from util import gpu_propagator, gpu_run, oracle_table, rel_l2, table_json
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    from paper_2410_17446_gb300 import build, prop
+    build.build()
+    return prop
+
+
+def oracle_run(W, table, nsteps, beam=0, tol=1e-12):
+    from oracle import propagator as pr
+    b = W.beams[beam]
+    return pr.run(b, W.k0, W.n0, table, W.ncomp, nsteps, tol=tol)
+
+
+def test_plain_scalar_64_fp64_full_run(P):
+    """64^2, 12 poles, static sine-product medium with an absorbing border, 16 steps, FP64."""
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.plain_scalar_64()
+    pr = gpu_propagator(W, "plain_scalar_64", P.PROP_FP64, tol=1e-12)
+    got = gpu_run(pr, W, W.nsteps)[0]
+    ref = oracle_run(W, oracle_table("plain_scalar_64"), W.nsteps)
+    assert rel_l2(got, ref) < FP64_TOL
+    it = pr.iterations()
+    assert it.min() >= 1
+
+
+@pytest.mark.parametrize("n,steps", [(128, 3), (256, 1)])
+def test_batched_scalar_fp32_reduced(P, n, steps):
+    """z-varying sine-product medium with border, 16 poles, complex FP32 path."""
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.batched_scalar_1024(steps, n=n)
+    pr = gpu_propagator(W, "batched_scalar_1024", P.PROP_FP32)
+    got = gpu_run(pr, W, steps)[0]
+    ref = oracle_run(W, oracle_table("batched_scalar_1024"), steps, tol=1e-12)
+    assert rel_l2(got, ref) < FP32_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", FP32_TOL), ("fp64", FP64_TOL)])
+def test_homogeneous_aperture_against_closed_form(P, prec, tol):
+    """Homogeneous medium: the step is IFFT[r(zeta_fs) FFT w] (Eq. approx_fs_prop)
+    and no GMRES iteration is needed."""
+    from oracle import propagator as orp
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.homogeneous_aperture_1024(20, n=256)
+    pr = gpu_propagator(W, "homogeneous_aperture_1024", P.PROP_FP64 if prec == "fp64" else P.PROP_FP32)
+    got = gpu_run(pr, W, 20)[0]
+    g = W.beams[0].grid
+    ref = orp.homogeneous_rational_step(W.beams[0].w0, g.dx, g.dy, W.k0, oracle_table("homogeneous_aperture_1024"), 20)
+    assert rel_l2(got, ref) < tol
+    assert pr.iterations().max() == 0
+
+
+def test_uneven_beams_in_one_handle(P):
+    """Beams of different grid sizes (and one repeated size) share one handle."""
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.uneven_batch(nbeams=3, nsteps=2, sizes=(64, 128))
+    pr = gpu_propagator(W, "uneven_batch", P.PROP_FP32)
+    got = gpu_run(pr, W, 2)
+    T = oracle_table("uneven_batch")
+    for i in range(3):
+        assert rel_l2(got[i], oracle_run(W, T, 2, beam=i)) < FP32_TOL
+
+
+def test_zero_field_stays_zero(P):
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.plain_scalar_64(2)
+    pr = gpu_propagator(W, "plain_scalar_64", P.PROP_FP32)
+    pr.set_field(0, np.zeros((1, 64, 64), np.complex128))
+    out = gpu_run(pr, W, 2)[0]
+    assert np.all(out == 0)
+
+
+def test_noconv_leaves_field_unchanged(P):
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.plain_scalar_64(1)
+    pr = gpu_propagator(W, "plain_scalar_64", P.PROP_FP64, tol=1e-15, max_restarts=1, restart=2)
+    pr.set_medium(0, W.beams[0].medium(0))
+    with pytest.raises(P.PropError) as e:
+        pr.step()
+    assert e.value.status == P.PROP_E_NOCONV
+    np.testing.assert_array_equal(pr.get_field(0), W.beams[0].w0)
