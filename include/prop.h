@@ -81,7 +81,20 @@ typedef struct prop_stats {
   int64_t last_iters_sum;  /* sum over (beam, pole) of Arnoldi steps, last step   */
   double last_resid_max;   /* max relative true residual, last step               */
   int64_t total_iters;     /* Arnoldi steps summed over all steps                 */
+  int64_t kernel_launches; /* kernels this handle has launched since prop_create  */
 } prop_stats;
+
+/* Per kernel kind: launches, device time (CUDA events recorded on the handle's
+ * stream around each launch while profiling is on) and the algorithmic bytes
+ * those launches had to move (each input read once, each output written once). */
+typedef struct prop_kernel_profile {
+  char name[24];
+  int64_t launches;
+  double total_ms;
+  double alg_bytes;
+} prop_kernel_profile;
+
+#define PROP_NKINDS 12
 
 typedef struct prop prop; /* opaque handle */
 
@@ -132,6 +145,12 @@ int prop_get_stats(prop* h, prop_stats* out);
  * (host memory; synchronises the stream). */
 int prop_get_iterations(prop* h, int32_t* iters);
 
+/* Turn per-launch event timing on (1) or off (0); turning it on clears the totals. */
+int prop_set_profiling(prop* h, int32_t on);
+
+/* Copy the PROP_NKINDS per-kind totals into out[PROP_NKINDS] (synchronises). */
+int prop_get_profile(prop* h, prop_kernel_profile* out);
+
 const char* prop_error_string(int status);
 
 /* Release the handle (host memory only; the workspace stays the caller's). */
@@ -150,6 +169,13 @@ int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t 
 /* out = (Z_fs - p_k I)^-1 v for beam `beam`, pole k (Sec. 4.2.1): the free-space
  * preconditioner.  v, out: device complex128 [ncomp][ny][nx]. */
 int prop_apply_freespace_inverse(prop* h, int32_t beam, int32_t pole, const void* d_v, void* d_out);
+
+/* Copy the correction e_k of the last step for (beam, pole k): the solution of
+ * (Z - p_k I) x_k = w of Eq. (W_k_def) is x_k = (Z_fs - p_k I)^-1 w + e_k, with
+ * w the field before that step.  out: complex128 [ncomp][ny][nx], host or
+ * device (synchronises for host memory).  e_k is zero when the solve needed
+ * no correction (e.g. a homogeneous medium). */
+int prop_get_correction(prop* h, int32_t beam, int32_t pole, void* out);
 
 /* out = Z v for beam `beam` with its current medium (Eq. Z_bar_eq).
  * v, out: device complex128 [ncomp][ny][nx]. */

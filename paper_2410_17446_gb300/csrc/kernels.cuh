@@ -26,7 +26,9 @@ enum SysStateCode { ST_DONE = 0, ST_ITER = 1, ST_CYCLE_END = 2 };
 // GMRES state of one (beam, pole) system.  Complex numbers are double2.
 struct SysState {
   int state, j, jend, iters, cycles, flags;   // flags: 1 = NaN seen, 2 = hit max cycles
+  int used, pad_i;                            // used: iterated this step (E is meaningful)
   double beta, resid, scale, nrm_a, nrm_b, pad;
+  double z0norm2, enorm2;                     // ||z_k||^2 (free-space solve), ||e_k||^2
   double2 g[MMAX + 1];
   double2 sn[MMAX];
   double cs[MMAX];
@@ -60,6 +62,7 @@ template <typename T> struct GV {
   double* bnorm2;       // [nb] ||w||^2 of the step's right-hand side
   int* nonhomog;        // [nb] 1 if delta != 0 somewhere
   const double2* rk;    // [P] residues r_k
+  const double* anorm;  // [P] bound on ||Z - p_k I|| over this grid (backward-error test)
 };
 
 // Which buffer a pass reads or writes: item (unit u, component c) lives at
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
   const int row0 = blockIdx.x * NR;
   const SRC* in = src.at(u, c, g.npts) + (long)row0 * N;
   double acc = 0.0;
+#pragma unroll
   for (int e = threadIdx.x; e < NR * N; e += NT) {
     const int r = e / N, n = e % N;
     SRC v = in[e];
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
   __syncthreads();
   fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
   C* out = dst.at(u, c, g.npts) + (long)row0 * N;
+#pragma unroll
   for (int e = threadIdx.x; e < NR * N; e += NT) out[e] = s[sidx<N, NR, false>(e / N, e % N)];
   if (norm_acc) {
     const double t = block_sum(acc, red);
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
 template <typename T, int NY, int NV, int NT>
 __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                              int mask, int fwd, int mul, int inv, int skip_homog, int pole,
-                                             T scale) {
+                                             T scale, Buf<typename Cx<T>::t> spec) {
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -150,12 +155,18 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   const int x0 = blockIdx.x * NV;
   const C* in = src.at(u, c, g.npts);
+#pragma unroll 8
   for (int e = threadIdx.x; e < NY * NV; e += NT) {
     const int n = e / NV, v = e % NV;
     s[n * NV + v] = in[(long)n * g.nx + x0 + v];
   }
   __syncthreads();
   if (fwd) fft_smem<C, NY, false, NV, NT, true>(s, g.twy, threadIdx.x);
+  if (spec.base) {   // keep the 2-D spectrum as well (read again by the pole solves)
+    C* sp = spec.at(u, c, g.npts);
+#pragma unroll 8
+    for (int e = threadIdx.x; e < NY * NV; e += NT) sp[(long)(e / NV) * g.nx + x0 + e % NV] = s[e];
+  }
   if (mul != MUL_NONE) {
     const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD);
     const int k = pm ? (pole >= 0 ? pole : u % g.P) : 0;
@@ -188,6 +199,7 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
   }
   if (inv) fft_smem<C, NY, true, NV, NT, true>(s, g.twy, threadIdx.x);
   C* out = dst.at(u, c, g.npts);
+#pragma unroll 8
   for (int e = threadIdx.x; e < NY * NV; e += NT) {
     const int n = e / NV, v = e % NV;
     out[(long)n * g.nx + x0 + v] = s[e];
@@ -219,12 +231,13 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   const int row0 = blockIdx.x * NR;
   const long off = (long)row0 * N;
   const C* in = src.at(u, c, g.npts) + off;
+#pragma unroll
   for (int e = threadIdx.x; e < NR * N; e += NT) s[sidx<N, NR, false>(e / N, e % N)] = in[e];
   __syncthreads();
   fft_smem<C, N, true, NR, NT, false>(s, g.twx, threadIdx.x);
   const C* dl = g.delta + (long)beam * g.npts + off;
   const long unit_off = ((long)u * g.ncomp + c) * g.npts + off;   // [unit][c][pt] arrays
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   for (int e = threadIdx.x; e < NR * N; e += NT) {
     const C val = s[sidx<N, NR, false>(e / N, e % N)];
     switch (ep.mode) {
@@ -248,6 +261,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
         C m; m.x = -r.x; m.y = -r.y;
         g.R0[unit_off + e] = m;
         acc += (double)m.x * m.x + (double)m.y * m.y;
+        acc2 += (double)val.x * val.x + (double)val.y * val.y;
       } break;
       case EPI_ARNOLDI: {
         const long vb = (((long)u * (g.m + 1) + ep.jj) * g.ncomp + c) * g.npts + off + e;
@@ -274,6 +288,10 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   if (ep.mode == EPI_R0 || ep.mode == EPI_TRUERES) {
     const double t = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].nrm_a, t);
+  }
+  if (ep.mode == EPI_R0) {
+    const double t = block_sum(acc2, red);
+    if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t);
   }
 }
 
@@ -416,17 +434,17 @@ __global__ void __launch_bounds__(NT) k_scale_v0(GV<T> g) {
   }
 }
 
-// v_0 = R0 (copy, first cycle) and E = 0 for every system.
+// v_0 = R0 and E = 0 for the systems that start iterating (the others keep E unused).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_init_systems(GV<T> g) {
   const int s = blockIdx.y;
+  if (g.st[s].state != ST_ITER) return;
   const long L = (long)g.ncomp * g.npts;
-  const bool it = g.st[s].state == ST_ITER;
   auto* v = vslot(g, s, 0);
   const auto* r = g.R0 + (long)s * L;
   double2* e = g.E + (long)s * L;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
-    if (it) v[p] = r[p];
+    v[p] = r[p];
     e[p] = make_double2(0.0, 0.0);
   }
 }
@@ -434,12 +452,14 @@ __global__ void __launch_bounds__(NT) k_init_systems(GV<T> g) {
 // E += sum_{i < jend} y_i z_i  (FP64 accumulation) for systems at a cycle end.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_update_e(GV<T> g) {
+  __shared__ double red[32];
   const int s = blockIdx.y;
   const SysState& st = g.st[s];
   if (st.state != ST_CYCLE_END) return;
   const int J = st.jend;
   const long L = (long)g.ncomp * g.npts;
   double2* e = g.E + (long)s * L;
+  double nr = 0.0;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
     double2 a = e[p];
     for (int i = 0; i < J; ++i) {
@@ -449,7 +469,10 @@ __global__ void __launch_bounds__(NT) k_update_e(GV<T> g) {
       a.y += y.x * z.y + y.y * z.x;
     }
     e[p] = a;
+    nr += a.x * a.x + a.y * a.y;
   }
+  const double t = block_sum(nr, red);
+  if (threadIdx.x == 0) atomicAdd(&g.st[s].enorm2, t);
 }
 
 // Wn[b] += sum_k r_k E[b, k]  (the residue sum of Eq. approx_prop, correction part).
@@ -461,6 +484,7 @@ __global__ void __launch_bounds__(NT) k_residue_sum(GV<T> g, double2* Wn) {
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
     double2 a = w[p];
     for (int k = 0; k < g.P; ++k) {
+      if (!g.st[b * g.P + k].used) continue;
       const double2 e = g.E[((long)b * g.P + k) * L + p];
       const double2 r = g.rk[k];
       a.x += r.x * e.x - r.y * e.y;
@@ -492,21 +516,31 @@ __global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2*
 
 // Begin a cycle for systems in state `from` (ST_DONE-initialised systems at a
 // step start use from = -1): beta = ||r||; converged if beta <= tol ||w||.
+// Convergence threshold: tol ||w|| (plain relative residual), or with
+// backward = 1 the normwise backward-error bound tol (||w|| + ||A|| ||x_k||),
+// x_k = z_k + e_k, for arithmetic whose transforms cannot resolve residuals
+// below eps ||A|| ||x||.
+__device__ __forceinline__ double conv_threshold(const SysState& q, double tol, double wn, double anorm, int backward) {
+  if (!backward) return tol * wn;
+  return tol * (wn + anorm * (sqrt(q.z0norm2) + sqrt(q.enorm2)));
+}
+
 __global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm2, double tol,
-                              int from, int max_cycles, int first) {
+                              int from, int max_cycles, int first, const double* anorm, int backward) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     SysState& q = st[s];
     if (!first && q.state != from) continue;
-    if (first) { q.iters = 0; q.cycles = 0; q.flags = 0; }
+    if (first) { q.iters = 0; q.cycles = 0; q.flags = 0; q.used = 0; q.enorm2 = 0.0; }
     const double beta = sqrt(q.nrm_a);
     const double wn = sqrt(bnorm2[s / P]);
     q.nrm_a = 0.0;
     q.beta = beta;
     q.resid = wn > 0 ? beta / wn : 0.0;
     if (!isfinite(beta)) { q.flags |= 1; q.state = ST_DONE; continue; }
-    if (beta <= tol * wn) { q.state = ST_DONE; continue; }
+    if (beta <= conv_threshold(q, tol, wn, anorm[s % P], backward)) { q.state = ST_DONE; continue; }
     if (q.cycles >= max_cycles) { q.flags |= 2; q.state = ST_DONE; continue; }
     q.cycles += 1;
+    q.used = 1;
     q.state = ST_ITER;
     q.j = 0;
     q.scale = 1.0 / beta;
@@ -524,7 +558,7 @@ __device__ __forceinline__ double dabs2(double2 a) { return a.x * a.x + a.y * a.
 // rotations, make the new one, update g and the residual estimate |g[jj+1]|;
 // end the cycle on convergence, breakdown or jj+1 == m (solving R y = g).
 __global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bnorm2, double tol,
-                                 int m, int jj, double breakdown) {
+                                 int m, int jj, double breakdown, const double* anorm, int backward) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     SysState& q = st[s];
     if (q.state != ST_ITER) continue;
@@ -570,7 +604,8 @@ __global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bn
     const double nb = q.nrm_b;
     q.nrm_b = 0.0;
     if (!isfinite(est) || !isfinite(hn)) { q.flags |= 1; q.state = ST_DONE; continue; }
-    if (est <= tol * wn || jj + 1 == m || hn <= breakdown * sqrt(fmax(nb, 0.0)) || hn == 0.0) {
+    if (est <= conv_threshold(q, tol, wn, anorm[s % P], backward) || jj + 1 == m ||
+        hn <= breakdown * sqrt(fmax(nb, 0.0)) || hn == 0.0) {
       const int J = jj + 1;
       for (int i = J - 1; i >= 0; --i) {
         double2 acc = q.g[i];
@@ -583,10 +618,18 @@ __global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bn
         q.y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
       }
       q.jend = J;
+      q.enorm2 = 0.0;          // recomputed by the correction update
       q.state = ST_CYCLE_END;
     } else {
       q.scale = 1.0 / hn;
     }
+  }
+}
+
+// zero the per-step accumulators of every system
+__global__ void k_step_reset(SysState* st, int nsys) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    st[s].z0norm2 = 0.0; st[s].nrm_a = 0.0; st[s].enorm2 = 0.0;
   }
 }
 

@@ -44,7 +44,7 @@ constexpr int EPT_CGS = 4;
 
 struct Layout {
   size_t V, Zb, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
-      rk, stage, iters, cycles, resid, flags, end;
+      rk, anorm, stage, iters, cycles, resid, flags, end;
 };
 
 struct Group {
@@ -54,6 +54,9 @@ struct Group {
   long npts;
   Layout off;
   int cur;                 // which of W64a / W64b holds the field
+  bool medium_dirty;       // a medium was set since the homogeneity flags were read
+  bool stats_zero;         // per-system statistics already record a homogeneous step
+  std::vector<int> nonhomog_host;
 };
 
 }  // namespace
@@ -72,6 +75,14 @@ struct prop {
   size_t counts_off;
   int64_t steps, total_iters;
   int last_status;
+  // launch accounting and optional per-launch event timing
+  int64_t launches;
+  int profiling;
+  struct Pending { int kind; double bytes; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t k_launches[PROP_NKINDS];
+  double k_ms[PROP_NKINDS], k_bytes[PROP_NKINDS];
 };
 
 namespace {
@@ -105,6 +116,7 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec) {
   L.bnorm2 = take(nb * sizeof(double));
   L.nonhomog = take(nb * sizeof(int));
   L.rk = take(P * 16);
+  L.anorm = take(P * sizeof(double));
   L.stage = take(npts * 16);
   L.iters = take(nsys * sizeof(int));
   L.cycles = take(nsys * sizeof(int));
@@ -130,6 +142,7 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   g.twx = (const C*)(b + L.twx); g.twy = (const C*)(b + L.twy);
   g.st = (SysState*)(b + L.st); g.bnorm2 = (double*)(b + L.bnorm2); g.nonhomog = (int*)(b + L.nonhomog);
   g.rk = (const double2*)(b + L.rk);
+  g.anorm = (const double*)(b + L.anorm);
   return g;
 }
 
@@ -140,9 +153,12 @@ template <typename C> Buf<C> buf(C* base, long ustride, int div = 1) { Buf<C> b;
 // ---------------------------------------------------------------------------
 template <typename T, int N> constexpr int NRC() { return N <= 256 ? 16 : (N <= 512 ? 8 : 4); }
 
-template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// Raise the dynamic shared-memory limit of one kernel instantiation (once per process).
+template <typename K> cudaError_t set_smem_once(K kernel, size_t bytes, bool& done) {
+  if (done || bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
 }
 
 template <typename T, int N, typename SRC>
@@ -152,7 +168,8 @@ cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
   constexpr int NR = NRC<T, N>();
   const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
   auto k = k_rows_fwd<T, N, NR, NT_PASS, SRC>;
-  cudaError_t e = set_smem(k, sm);
+  static bool attr = false;
+  cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units * g.ncomp);
   k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, nacc);
@@ -166,7 +183,8 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
   constexpr int NR = NRC<T, N>();
   const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
   auto k = k_rows_inv<T, N, NR, NT_PASS>;
-  cudaError_t e = set_smem(k, sm);
+  static bool attr = false;
+  cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units * g.ncomp);
   k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, skip, ep);
@@ -175,15 +193,17 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
 
 template <typename T, int NY>
 cudaError_t cols_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
-                   int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st) {
+                   int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
+                   Buf<typename Cx<T>::t> spec) {
   using C = typename Cx<T>::t;
   constexpr int NV = cols_per_cta<T>();
   const size_t sm = smem_elems<NY, NV, true>() * sizeof(C);
   auto k = k_cols<T, NY, NV, NT_PASS>;
-  cudaError_t e = set_smem(k, sm);
+  static bool attr = false;
+  cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.nx / NV, units * g.ncomp);
-  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale);
+  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, spec);
   return cudaGetLastError();
 }
 
@@ -217,8 +237,9 @@ cudaError_t rows_inv(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx
 }
 template <typename T>
 cudaError_t cols(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd, int mul,
-                 int inv, int skip, int pole, T scale, int units, cudaStream_t st) {
-#define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st)
+                 int inv, int skip, int pole, T scale, int units, cudaStream_t st,
+                 Buf<typename Cx<T>::t> spec = Buf<typename Cx<T>::t>{nullptr, 0, 1}) {
+#define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec)
   PROP_SIZE_SWITCH(g.ny, CALL)
 #undef CALL
 }
@@ -303,6 +324,15 @@ template <typename T> int upload_group_tables(prop* h, Group& G) {
       bm[((size_t)j * G.nx + i) * 2 + 1] = (T)r.imag();
     }
   CK(cudaMemcpyAsync(b + G.off.basemul, bm.data(), bm.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  // ||Z - p_k I|| <= max over the grid's free-space spectrum of |zeta - p_k| + 0.5 (|delta| <= 0.5)
+  {
+    const double kxm = M_PI / G.dx, kym = M_PI / G.dy;
+    const double zmin = -(kxm * kxm + kym * kym) / (k0n0 * k0n0);
+    std::vector<double> an(h->P);
+    for (int k = 0; k < h->P; ++k) an[k] = std::max(std::abs(cplx(zmin, 0.0) - h->poles[k]), std::abs(h->poles[k])) + 0.5;
+    CK(cudaMemcpyAsync(b + G.off.anorm, an.data(), an.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   std::vector<double> rk(2 * h->P);
   for (int k = 0; k < h->P; ++k) { rk[2 * k] = h->res[k].real(); rk[2 * k + 1] = h->res[k].imag(); }
   CK(cudaMemcpyAsync(b + G.off.rk, rk.data(), rk.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -312,12 +342,63 @@ template <typename T> int upload_group_tables(prop* h, Group& G) {
 }
 
 // ---------------------------------------------------------------------------
+// Launch accounting
+// ---------------------------------------------------------------------------
+enum Kind { K_ROWS_FWD, K_COLS, K_ROWS_INV, K_DOTS, K_CGS, K_NORMALIZE, K_UPDATE_E, K_RESIDUE, K_MEDIUM,
+            K_CONTROL, K_INIT, K_SCALE };
+const char* kind_name(int k) {
+  static const char* n[PROP_NKINDS] = {"rows_fwd", "cols", "rows_inv", "dots", "cgs", "normalize",
+                                       "update_e", "residue_sum", "medium", "control", "init_systems",
+                                       "scale_v0"};
+  return n[k];
+}
+
+cudaEvent_t take_event(prop* h) {
+  if (!h->pool.empty()) { cudaEvent_t e = h->pool.back(); h->pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Resolve recorded event pairs; call only after the stream has been synchronised.
+void resolve_pending(prop* h) {
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->k_ms[p.kind] += ms;
+    h->pool.push_back(p.a);
+    h->pool.push_back(p.b);
+  }
+  h->pending.clear();
+  cudaGetLastError();
+}
+
+// Counts one launch of `kind` moving `bytes` algorithmic bytes; with profiling
+// on, brackets it with events on the handle's stream.
+struct Prof {
+  prop* h; int kind; double bytes; cudaEvent_t a;
+  Prof(prop* h_, int kind_, double bytes_) : h(h_), kind(kind_), bytes(bytes_), a(nullptr) {
+    h->launches += 1;
+    h->k_launches[kind] += 1;
+    h->k_bytes[kind] += bytes;
+    if (h->profiling) { a = take_event(h); cudaEventRecord(a, h->stream); }
+  }
+  ~Prof() {
+    if (a) {
+      cudaEvent_t b = take_event(h);
+      cudaEventRecord(b, h->stream);
+      h->pending.push_back({kind, bytes, a, b});
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
 // The step
 // ---------------------------------------------------------------------------
 int read_counts(prop* h, int* c3) {
   if (cudaMemcpyAsync(c3, h->ws + h->counts_off, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return PROP_E_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PROP_E_CUDA;
+  if (!h->pending.empty()) resolve_pending(h);
   return PROP_OK;
 }
 
@@ -326,66 +407,127 @@ template <typename T> int step_group(prop* h, Group& G) {
   GV<T> g = view<T>(h, G);
   cudaStream_t st = h->stream;
   const int Cn = h->C, P = h->P, nb = g.nb, nsys = g.nsys, m = h->m;
-  const long F = (long)Cn * g.npts;                       // one field
+  const long F = (long)Cn * g.npts;                       // points of one field
+  const double cs = (double)sizeof(C), pts = (double)g.npts;
   const T scale = (T)(1.0 / (double)g.npts);
   int* counts = (int*)(h->ws + h->counts_off);
   double2* Wn = (double2*)(h->ws + (G.cur == 0 ? G.off.W64b : G.off.W64a));
+  const int tb = 128, tg = (nsys + tb - 1) / tb;
+  const int vb = vec_blocks(F);
+
+  // which beams carry a non-zero delta (read back once per medium change)
+  if (G.medium_dirty) {
+    G.nonhomog_host.assign(nb, 0);
+    CK(cudaMemcpyAsync(G.nonhomog_host.data(), g.nonhomog, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    G.medium_dirty = false;
+  }
+  int n_inh = 0;
+  for (int b = 0; b < nb; ++b) n_inh += G.nonhomog_host[b] ? 1 : 0;
 
   // w_hat = FFT2(w); ||w||^2 per beam
   CK(cudaMemsetAsync(g.bnorm2, 0, nb * sizeof(double), st));
-  CK(rows_fwd<T, double2>(g, buf(g.W64, F), buf(g.Btmp, F), -1, g.bnorm2, nb, st));
-  CK(cols<T>(g, buf(g.Btmp, F), buf(g.What, F), -1, 1, MUL_NONE, 0, 0, -1, (T)1, nb, st));
-  // free-space part: Wn = w + IFFT2[(r - 1) w_hat]
-  CK(cols<T>(g, buf(g.What, F), buf(g.Btmp, F), -1, 0, MUL_TABLE, 1, 0, -1, (T)1, nb, st));
-  CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0, epi(EPI_ACCUM64, 0, nullptr, Wn), nb, st));
-  // correction systems: R0_k = -delta * IFFT2[w_hat/(zeta - p_k)]
-  CK(cols<T>(g, buf(g.What, F, P), buf(g.Tmp, F), -1, 0, MUL_POLE_INV, 1, 1, -1, scale, nsys, st));
-  CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), -1, 1, epi(EPI_R0), nsys, st));
-  const int tb = 128, tg = (nsys + tb - 1) / tb;
-  k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1);
-  const int vb = vec_blocks(F);
-  k_init_systems<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
-  k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
+  { Prof p_(h, K_ROWS_FWD, (16 + cs) * pts * nb * Cn);
+    CK(rows_fwd<T, double2>(g, buf(g.W64, F), buf(g.Btmp, F), -1, g.bnorm2, nb, st)); }
+  // column DFT (spectrum kept when poles will need it), then the free-space part
+  // Wn = w + IFFT2[(r - 1) w_hat] (Eq. approx_fs_prop), in one column pass
+  { Prof p_(h, K_COLS, (n_inh ? 4 : 3) * cs * pts * nb * Cn);
+    CK(cols<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 1, MUL_TABLE, 1, 0, -1, (T)1, nb, st,
+               n_inh ? buf(g.What, F) : Buf<C>{nullptr, 0, 1})); }
+  { Prof p_(h, K_ROWS_INV, (cs + 32) * pts * nb * Cn);
+    CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0, epi(EPI_ACCUM64, 0, nullptr, Wn), nb, st)); }
+  const int bw = h->prec == PROP_FP32 ? 1 : 0;
+  if (n_inh == 0) {           // homogeneous medium: the free-space step is exact, no correction
+    if (!G.stats_zero) {      // record zero iterations for every system (once)
+      Prof p_(h, K_CONTROL, 0);
+      k_step_reset<<<tg, tb, 0, st>>>(g.st, nsys);
+      k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw);
+      G.stats_zero = true;
+    }
+    CK(cudaGetLastError());
+    G.cur ^= 1;
+    return PROP_OK;
+  }
+  G.stats_zero = false;
+  { Prof p_(h, K_CONTROL, 0);
+    k_step_reset<<<tg, tb, 0, st>>>(g.st, nsys); }
+  const int sys_inh = n_inh * P;
+  // correction right-hand sides: R0_k = -delta * IFFT2[w_hat/(zeta - p_k)]
+  { Prof p_(h, K_COLS, 2 * cs * pts * sys_inh * Cn);
+    CK(cols<T>(g, buf(g.What, F, P), buf(g.Tmp, F), -1, 0, MUL_POLE_INV, 1, 1, -1, scale, nsys, st)); }
+  { Prof p_(h, K_ROWS_INV, 3 * cs * pts * sys_inh * Cn);
+    CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), -1, 1, epi(EPI_R0), nsys, st)); }
+  { Prof p_(h, K_CONTROL, 0);
+    k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw);
+    k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
   CK(cudaGetLastError());
-
-  const double breakdown = sizeof(T) == 4 ? 1e-6 : 1e-14;
   int c3[3];
-  k_count<<<1, 256, 0, st>>>(g.st, nsys, counts);
   int rc = read_counts(h, c3);
   if (rc) return rc;
+  const bool any_used = c3[0] > 0;
+  if (any_used) {
+    { Prof p_(h, K_INIT, (cs + 16) * pts * c3[0] * Cn);
+      k_init_systems<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    { Prof p_(h, K_SCALE, 2 * cs * pts * c3[0] * Cn);
+      k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+  }
+  const double breakdown = sizeof(T) == 4 ? 1e-6 : 1e-14;
   while (c3[0] > 0) {
     for (int jj = 0; jj < m; ++jj) {
+      const double act = (double)c3[0] * Cn * pts;
       C* Vj = g.V + (long)jj * F;
       const long vs = (long)(m + 1) * F;
-      CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st));
-      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st));
-      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st));
-      k_dots<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj);
-      k_cgs<T, NT_VEC, EPT_CGS><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj);
-      k_arnoldi_finish<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown);
-      k_normalize<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj);
-      k_count<<<1, 256, 0, st>>>(g.st, nsys, counts);
+      { Prof p_(h, K_ROWS_FWD, 2 * cs * act);
+        CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st)); }
+      { Prof p_(h, K_COLS, 2 * cs * act);
+        CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
+      { Prof p_(h, K_ROWS_INV, 5 * cs * act);
+        CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
+      { Prof p_(h, K_DOTS, (jj + 2) * cs * act);
+        k_dots<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
+      { Prof p_(h, K_CGS, (2.0 * (jj + 1) + 2) * cs * act);
+        k_cgs<T, NT_VEC, EPT_CGS><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
+      { Prof p_(h, K_CONTROL, 0);
+        k_arnoldi_finish<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown, g.anorm, bw); }
+      { Prof p_(h, K_NORMALIZE, 0);
+        k_normalize<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
+      { Prof p_(h, K_CONTROL, 0);
+        k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
       CK(cudaGetLastError());
       rc = read_counts(h, c3);
       if (rc) return rc;
+      h->k_bytes[K_NORMALIZE] += (jj + 3) * cs * pts * Cn * c3[0];   // systems that continued
+      h->total_iters += (int64_t)(act / (Cn * pts));
       if (c3[0] == 0) break;
     }
     if (c3[1] == 0) break;
-    // cycle end: e += M^-1 V y (stored z_j), true residual r = R0 - (Z - p) e
-    k_update_e<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
-    CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st));
-    CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st));
-    CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st));
-    k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0);
-    k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g);
-    k_count<<<1, 256, 0, st>>>(g.st, nsys, counts);
+    // cycle end: e += M^-1 V y (stored z_j); true residual r = R0 - (Z - p) e
+    const double endp = (double)c3[1] * Cn * pts;
+    { Prof p_(h, K_UPDATE_E, (32 + m * cs) * endp);   // upper bound on the z_j read: J <= m
+      k_update_e<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
+      CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
+    { Prof p_(h, K_COLS, 2 * cs * endp);
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st)); }
+    { Prof p_(h, K_ROWS_INV, (4 * cs + 16) * endp);
+      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st)); }
+    { Prof p_(h, K_CONTROL, 0);
+      k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw); }
+    { Prof p_(h, K_SCALE, 0);
+      k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    { Prof p_(h, K_CONTROL, 0);
+      k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
     CK(cudaGetLastError());
     rc = read_counts(h, c3);
     if (rc) return rc;
+    h->k_bytes[K_SCALE] += 2 * cs * pts * Cn * c3[0];
   }
   if (c3[2] & 1) return PROP_E_NAN;
   if (c3[2] & 2) return PROP_E_NOCONV;
-  k_residue_sum<T, NT_VEC><<<dim3(vb, nb), NT_VEC, 0, st>>>(g, Wn);
+  if (any_used) {
+    Prof p_(h, K_RESIDUE, (32.0 + 16.0 * P) * pts * Cn * n_inh);   // upper bound: every pole used
+    k_residue_sum<T, NT_VEC><<<dim3(vb, nb), NT_VEC, 0, st>>>(g, Wn);
+  }
   CK(cudaGetLastError());
   G.cur ^= 1;   // commit: the new field becomes current
   return PROP_OK;
@@ -416,6 +558,8 @@ int build_groups(int nbeams, const prop_grid* grids, std::vector<Group>& groups,
     if (gi < 0) {
       Group G;
       G.nx = gr.nx; G.ny = gr.ny; G.dx = gr.dx; G.dy = gr.dy; G.npts = (long)gr.nx * gr.ny; G.cur = 0;
+      G.medium_dirty = true;
+      G.stats_zero = false;
       groups.push_back(G);
       gi = (int)groups.size() - 1;
     }
@@ -491,6 +635,8 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   h->ws = (char*)d_workspace; h->ws_bytes = ws_bytes;
   h->stream = (cudaStream_t)stream;
   h->steps = 0; h->total_iters = 0; h->last_status = 0;
+  h->launches = 0; h->profiling = 0;
+  for (int k = 0; k < PROP_NKINDS; ++k) { h->k_launches[k] = 0; h->k_ms[k] = 0.0; h->k_bytes[k] = 0.0; }
   if (cudaMemsetAsync(h->ws, 0, need, h->stream) != cudaSuccess) { delete h; return PROP_E_CUDA; }
   for (Group& G : h->groups) {
     rc = h->prec == PROP_FP64 ? upload_group_tables<double>(h, G) : upload_group_tables<float>(h, G);
@@ -510,9 +656,13 @@ int prop_set_medium(prop* h, int32_t beam, const void* n2) {
   CK(cudaMemsetAsync(nh, 0, sizeof(int), h->stream));
   const int blocks = (int)std::min<long>(1024, (G.npts + 255) / 256);
   const double n0sq = h->n0 * h->n0;
-  if (h->prec == PROP_FP64) k_medium<double, 256><<<blocks, 256, 0, h->stream>>>(view<double>(h, G), slot, (const double2*)stage, n0sq);
-  else k_medium<float, 256><<<blocks, 256, 0, h->stream>>>(view<float>(h, G), slot, (const double2*)stage, n0sq);
+  {
+    Prof p_(h, K_MEDIUM, (16.0 + 2 * elem_size(h->prec)) * G.npts);
+    if (h->prec == PROP_FP64) k_medium<double, 256><<<blocks, 256, 0, h->stream>>>(view<double>(h, G), slot, (const double2*)stage, n0sq);
+    else k_medium<float, 256><<<blocks, 256, 0, h->stream>>>(view<float>(h, G), slot, (const double2*)stage, n0sq);
+  }
   CK(cudaGetLastError());
+  G.medium_dirty = true;
   return PROP_OK;
 }
 
@@ -573,7 +723,10 @@ static int collect(prop* h, std::vector<int>& iters, std::vector<int>& cyc, std:
     int* dc = (int*)(h->ws + G.off.cycles);
     double* dr = (double*)(h->ws + G.off.resid);
     int* df = (int*)(h->ws + G.off.flags);
-    k_collect<<<(nsys + 127) / 128, 128, 0, h->stream>>>((SysState*)(h->ws + G.off.st), nsys, di, dc, dr, df);
+    {
+      Prof p_(h, K_CONTROL, 0);
+      k_collect<<<(nsys + 127) / 128, 128, 0, h->stream>>>((SysState*)(h->ws + G.off.st), nsys, di, dc, dr, df);
+    }
     std::vector<int> ti(nsys), tc(nsys);
     std::vector<double> tr(nsys);
     CK(cudaMemcpyAsync(ti.data(), di, nsys * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -607,6 +760,7 @@ int prop_get_stats(prop* h, prop_stats* out) {
     out->last_resid_max = std::max(out->last_resid_max, rs[i]);
   }
   out->total_iters = h->total_iters;
+  out->kernel_launches = h->launches;
   return PROP_OK;
 }
 
@@ -633,7 +787,35 @@ const char* prop_error_string(int status) {
   }
 }
 
-void prop_destroy(prop* h) { delete h; }
+void prop_destroy(prop* h) {
+  if (!h) return;
+  if (!h->pending.empty()) { cudaStreamSynchronize(h->stream); resolve_pending(h); }
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  delete h;
+}
+
+int prop_set_profiling(prop* h, int32_t on) {
+  if (!h) return PROP_E_ARG;
+  if (!h->pending.empty()) { CK(cudaStreamSynchronize(h->stream)); resolve_pending(h); }
+  h->profiling = on ? 1 : 0;
+  if (on)
+    for (int k = 0; k < PROP_NKINDS; ++k) { h->k_launches[k] = 0; h->k_ms[k] = 0.0; h->k_bytes[k] = 0.0; }
+  return PROP_OK;
+}
+
+int prop_get_profile(prop* h, prop_kernel_profile* out) {
+  if (!h || !out) return PROP_E_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  resolve_pending(h);
+  for (int k = 0; k < PROP_NKINDS; ++k) {
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, kind_name(k), sizeof(out[k].name) - 1);
+    out[k].launches = h->k_launches[k];
+    out[k].total_ms = h->k_ms[k];
+    out[k].alg_bytes = h->k_bytes[k];
+  }
+  return PROP_OK;
+}
 
 // ---- building blocks --------------------------------------------------------
 
@@ -711,6 +893,31 @@ template <typename T> static int apply_impl(prop* h, int beam, int pole, const v
 }
 
 extern "C" {
+
+int prop_get_correction(prop* h, int32_t beam, int32_t pole, void* out) {
+  if (!h || !out || beam < 0 || beam >= h->nbeams || pole < 0 || pole >= h->P) return PROP_E_ARG;
+  Group& G = h->groups[h->beam_group[beam]];
+  const long F = (long)h->C * G.npts;
+  const int s = h->beam_slot[beam] * h->P + pole;
+  SysState* st = (SysState*)(h->ws + G.off.st) + s;
+  int used = 0;
+  CK(cudaMemcpyAsync(&used, &st->used, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (!used || G.stats_zero) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeDevice) {
+      CK(cudaMemsetAsync(out, 0, F * 16, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    } else {
+      cudaGetLastError();
+      std::memset(out, 0, F * 16);
+    }
+    return PROP_OK;
+  }
+  CK(cudaMemcpyAsync(out, h->ws + G.off.E + (size_t)s * F * 16, F * 16, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PROP_OK;
+}
 
 int prop_apply_freespace_inverse(prop* h, int32_t beam, int32_t pole, const void* d_v, void* d_out) {
   if (!h || !d_v || !d_out || beam < 0 || beam >= h->nbeams || pole < 0 || pole >= h->P) return PROP_E_ARG;

@@ -36,7 +36,15 @@ class prop_stats(ct.Structure):
     _fields_ = [("steps", ct.c_int64), ("npoles", ct.c_int32), ("nbeams", ct.c_int32),
                 ("last_iters_max", ct.c_int32), ("last_cycles_max", ct.c_int32),
                 ("last_iters_sum", ct.c_int64), ("last_resid_max", ct.c_double),
-                ("total_iters", ct.c_int64)]
+                ("total_iters", ct.c_int64), ("kernel_launches", ct.c_int64)]
+
+
+PROP_NKINDS = 12
+
+
+class prop_kernel_profile(ct.Structure):
+    _fields_ = [("name", ct.c_char * 24), ("launches", ct.c_int64), ("total_ms", ct.c_double),
+                ("alg_bytes", ct.c_double)]
 
 
 MEDIUM_FN = ct.CFUNCTYPE(ct.c_int, ct.c_void_p, ct.c_int32, ct.c_void_p)
@@ -59,12 +67,15 @@ _SIGS = {
     "prop_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(prop_stats)]),
     "prop_get_iterations": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
     "prop_error_string": (ct.c_char_p, [ct.c_int]),
+    "prop_set_profiling": (ct.c_int, [ct.c_void_p, ct.c_int32]),
+    "prop_get_profile": (ct.c_int, [ct.c_void_p, ct.POINTER(prop_kernel_profile)]),
     "prop_destroy": (None, [ct.c_void_p]),
     "prop_fft2_workspace_size": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_size_t)]),
     "prop_fft2": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
                              ct.c_void_p, ct.c_size_t, ct.c_void_p]),
     "prop_apply_freespace_inverse": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     "prop_apply_operator": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
+    "prop_get_correction": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p]),
 }
 
 
@@ -208,9 +219,24 @@ class Propagator:
         check(lib().prop_get_iterations(self.h, out.ctypes.data_as(ct.POINTER(ct.c_int32))), "prop_get_iterations")
         return out.reshape(self.nbeams, self.npoles)
 
+    def set_profiling(self, on: bool) -> None:
+        check(lib().prop_set_profiling(self.h, 1 if on else 0), "prop_set_profiling")
+
+    def profile(self) -> dict:
+        arr = (prop_kernel_profile * PROP_NKINDS)()
+        check(lib().prop_get_profile(self.h, arr), "prop_get_profile")
+        return {a.name.decode(): {"launches": a.launches, "total_ms": a.total_ms, "alg_bytes": a.alg_bytes}
+                for a in arr}
+
     def apply_freespace_inverse(self, beam: int, pole: int, d_v, d_out) -> None:
         check(lib().prop_apply_freespace_inverse(self.h, beam, pole, _dptr(d_v), _dptr(d_out)),
               "prop_apply_freespace_inverse")
+
+    def get_correction(self, beam: int, pole: int, out=None):
+        if out is None:
+            out = np.empty(self.shape(beam), np.complex128)
+        check(lib().prop_get_correction(self.h, beam, pole, _dptr(out)), "prop_get_correction")
+        return out
 
     def apply_operator(self, beam: int, d_v, d_out) -> None:
         check(lib().prop_apply_operator(self.h, beam, _dptr(d_v), _dptr(d_out)), "prop_apply_operator")

@@ -97,3 +97,45 @@ def test_noconv_leaves_field_unchanged(P):
         pr.step()
     assert e.value.status == P.PROP_E_NOCONV
     np.testing.assert_array_equal(pr.get_field(0), W.beams[0].w0)
+
+
+def test_homogeneous_aperture_full_size_100_steps(P):
+    """1024^2, 100 steps, FP32: the configuration as benchmarked, against the
+    closed-form rational step IFFT[r(zeta_fs)^100 FFT w0] (Eq. approx_fs_prop)."""
+    from oracle import propagator as orp
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.homogeneous_aperture_1024()
+    pr = gpu_propagator(W, "homogeneous_aperture_1024", P.PROP_FP32)
+    got = gpu_run(pr, W, W.nsteps)[0]
+    g = W.beams[0].grid
+    ref = orp.homogeneous_rational_step(W.beams[0].w0, g.dx, g.dy, W.k0, oracle_table("homogeneous_aperture_1024"),
+                                        W.nsteps)
+    assert rel_l2(got, ref) < FP32_TOL
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_batched_scalar_solutions_satisfy_the_shifted_systems(P, n):
+    """Full size (and a reduced one): after a GPU step the oracle rebuilds every
+    pole's solution x_k = (Z_fs - p_k)^-1 w + e_k from the GPU's correction e_k,
+    checks its residual ||w - (Z - p_k) x_k|| with the oracle's own operator,
+    and recombines r(Z) w = r0 w + sum r_k x_k (Eq. approx_prop) against the
+    GPU's new field."""
+    from oracle import operators as ops
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.batched_scalar_1024(1, n=n)
+    T = oracle_table("batched_scalar_1024")
+    pr = gpu_propagator(W, "batched_scalar_1024", P.PROP_FP32)
+    b = W.beams[0]
+    w0 = b.w0
+    got = gpu_run(pr, W, 1)[0]
+    med = ops.Medium(b.medium(0), b.grid.dx, b.grid.dy, W.k0, W.n0, 1)
+    out = T.r0 * w0
+    worst = 0.0
+    for k, (p, r) in enumerate(zip(T.poles, T.residues)):
+        x = med.freespace_solve(w0, p) + pr.get_correction(0, k)
+        res = np.linalg.norm(w0 - med.apply_shifted(x, p)) / np.linalg.norm(w0)
+        worst = max(worst, res)
+        out = out + r * x
+    assert worst < 1e-4, worst          # FP32 solves: residual well below the field
+    assert rel_l2(got, out) < 1e-6      # the GPU's residue sum and free-space part
+    assert pr.iterations().min() >= 1
