@@ -50,7 +50,8 @@ enum prop_status {
   PROP_E_CUDA = 3,         /* a CUDA runtime call failed                          */
   PROP_E_NOCONV = 4,       /* GMRES hit max_restarts without reaching tol         */
   PROP_E_NAN = 5,          /* a residual norm became NaN or Inf                   */
-  PROP_E_UNSUPPORTED = 6   /* grid size / mode not compiled into this library     */
+  PROP_E_UNSUPPORTED = 6,  /* grid size / mode not compiled into this library     */
+  PROP_E_SCRATCH = 7       /* request exceeds the fixed scratch of prop_fft2_noalloc */
 };
 
 enum prop_precision {
@@ -165,6 +166,26 @@ void prop_destroy(prop* h);
 int prop_fft2_workspace_size(int32_t nx, int32_t ny, int32_t precision, size_t* bytes);
 int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse,
               void* d_data, void* d_work, size_t work_bytes, void* stream);
+
+/* prop_fft2 for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant.  Some callers cannot call
+ * cudaMalloc or take memory from an allocator, for instance a plugin whose host
+ * application owns every device allocation, or a program that must run inside
+ * a fixed device-memory budget decided in advance.  They pass only the data;
+ * the twiddle tables that prop_fft2 keeps in d_work live here in a file-scope
+ * __device__ array of PROP_FFT2_NOALLOC_SCRATCH_BYTES (64 KiB), which every GPU
+ * that loads this library holds until the process exits.  A call needs
+ * (nx + ny) complex twiddles of the chosen precision; requests that do not fit
+ * return PROP_E_SCRATCH.  Nothing is allocated: no cudaMalloc, cudaFree or
+ * allocating library routine is called.  The first call on each device looks
+ * up the array's device address with that device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and each call rewrites the part it uses, so calls
+ * that overlap on the GPU (different streams, or devices sharing nothing but
+ * this process) race on the same memory: serialise them. */
+#define PROP_FFT2_NOALLOC_SCRATCH_BYTES 65536
+int prop_fft2_noalloc(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse,
+                      void* d_data, void* stream);
 
 /* out = (Z_fs - p_k I)^-1 v for beam `beam`, pole k (Sec. 4.2.1): the free-space
  * preconditioner.  v, out: device complex128 [ncomp][ny][nx]. */

@@ -783,6 +783,7 @@ const char* prop_error_string(int status) {
     case PROP_E_NOCONV: return "GMRES did not converge within max_restarts";
     case PROP_E_NAN: return "NaN or Inf in a residual";
     case PROP_E_UNSUPPORTED: return "unsupported grid size or mode";
+    case PROP_E_SCRATCH: return "request exceeds the fixed scratch of prop_fft2_noalloc";
     default: return "unknown status";
   }
 }
@@ -932,3 +933,80 @@ int prop_apply_operator(prop* h, int32_t beam, const void* d_v, void* d_out) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// prop_fft2_noalloc: the batched 2-D DFT without any device allocation.
+// Its twiddle tables live in a fixed file-scope array instead of caller
+// memory.  Host code cannot use the array's name as a device address (it is a
+// host-side stand-in), so the address is looked up once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+// ===========================================================================
+namespace {
+
+static __device__ __align__(256) unsigned char g_fft2_noalloc_scratch[PROP_FFT2_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once).
+int noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PROP_E_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_fft2_noalloc_scratch) != cudaSuccess || !p) return PROP_E_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PROP_OK;
+}
+
+// w[m] = exp(-2 pi i m / n), evaluated in double and rounded once to T
+template <typename T> __global__ void k_twiddle_table(typename Cx<T>::t* tw, int n) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)m / (double)n, &sn, &cs);
+    tw[m].x = (T)cs;
+    tw[m].y = (T)sn;
+  }
+}
+
+template <typename T>
+int fft2_noalloc_impl(int nx, int ny, int batch, int inverse, void* data, cudaStream_t st) {
+  using C = typename Cx<T>::t;
+  const size_t ox = 0, oy = align_up(nx * sizeof(C));
+  if (oy + ny * sizeof(C) > PROP_FFT2_NOALLOC_SCRATCH_BYTES) return PROP_E_SCRATCH;
+  void* scratch = nullptr;
+  const int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  char* w = (char*)scratch;
+  k_twiddle_table<T><<<(nx + 255) / 256, 256, 0, st>>>((C*)(w + ox), nx);
+  k_twiddle_table<T><<<(ny + 255) / 256, 256, 0, st>>>((C*)(w + oy), ny);
+  CK(cudaGetLastError());
+  GV<T> g;
+  std::memset(&g, 0, sizeof(g));
+  g.nx = nx; g.ny = ny; g.ncomp = 1; g.P = 1; g.m = 1; g.nb = batch; g.nsys = batch; g.npts = (long)nx * ny;
+  g.twx = (const C*)(w + ox); g.twy = (const C*)(w + oy);
+  C* d = (C*)data;
+  const long F = g.npts;
+  if (!inverse) {
+    CK(rows_fwd<T, C>(g, buf(d, F), buf(d, F), -1, nullptr, batch, st));
+    CK(cols<T>(g, buf(d, F), buf(d, F), -1, 1, MUL_NONE, 0, 0, -1, (T)1, batch, st));
+  } else {
+    CK(cols<T>(g, buf(d, F), buf(d, F), -1, 0, MUL_SCALE, 1, 0, -1, (T)(1.0 / (double)F), batch, st));
+    CK(rows_inv<T>(g, buf(d, F), buf(d, F), -1, 0, epi(EPI_STORE), batch, st));
+  }
+  return PROP_OK;
+}
+
+}  // namespace
+
+extern "C" int prop_fft2_noalloc(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse,
+                                 void* d_data, void* stream) {
+  if (!supported_n(nx) || !supported_n(ny)) return PROP_E_UNSUPPORTED;
+  if (batch < 0 || !d_data) return PROP_E_ARG;
+  if (batch == 0) return PROP_OK;
+  if (precision == PROP_FP64) return fft2_noalloc_impl<double>(nx, ny, batch, inverse, d_data, (cudaStream_t)stream);
+  if (precision == PROP_FP32) return fft2_noalloc_impl<float>(nx, ny, batch, inverse, d_data, (cudaStream_t)stream);
+  return PROP_E_ARG;
+}

@@ -19,7 +19,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libprop.so")
 
-PROP_OK, PROP_E_ARG, PROP_E_WORKSPACE, PROP_E_CUDA, PROP_E_NOCONV, PROP_E_NAN, PROP_E_UNSUPPORTED = range(7)
+PROP_OK, PROP_E_ARG, PROP_E_WORKSPACE, PROP_E_CUDA, PROP_E_NOCONV, PROP_E_NAN, PROP_E_UNSUPPORTED, PROP_E_SCRATCH = range(8)
 PROP_FP64, PROP_FP32 = 0, 1
 
 
@@ -76,6 +76,8 @@ _SIGS = {
     "prop_apply_freespace_inverse": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     "prop_apply_operator": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     "prop_get_correction": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p]),
+    "prop_fft2_noalloc": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
+                                     ct.c_void_p]),
 }
 
 
@@ -137,6 +139,11 @@ def prop_fft2_workspace_size(nx: int, ny: int, precision: int) -> int:
 def prop_fft2(nx, ny, batch, precision, inverse, d_data, d_work, work_bytes, stream=0) -> None:
     check(lib().prop_fft2(nx, ny, batch, precision, inverse, _dptr(d_data), _dptr(d_work), work_bytes,
                           stream), "prop_fft2")
+
+
+def prop_fft2_noalloc(nx, ny, batch, precision, inverse, d_data, stream=0) -> None:
+    """prop_fft2 without a caller workspace, for callers that cannot allocate device memory."""
+    check(lib().prop_fft2_noalloc(nx, ny, batch, precision, inverse, _dptr(d_data), stream), "prop_fft2_noalloc")
 
 
 class Propagator:
