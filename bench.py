@@ -40,12 +40,13 @@ TABLE_OF = {"homogeneous_aperture_1024": "homogeneous_aperture_1024", "batched_s
             "uneven_batch": "uneven_batch"}
 
 
-def make_workload(name: str, nsteps: int):
+def make_workload(name: str, nsteps: int, n: int = 0):
+    """The named workload; n > 0 shrinks a single-grid workload to n x n (profiling only)."""
     from paper_2410_17446_gb300 import workloads as wl
     if name == "homogeneous_aperture_1024":
-        return wl.homogeneous_aperture_1024(nsteps)
+        return wl.homogeneous_aperture_1024(nsteps, **({"n": n} if n else {}))
     if name == "batched_scalar_1024":
-        return wl.batched_scalar_1024(nsteps)
+        return wl.batched_scalar_1024(nsteps, **({"n": n} if n else {}))
     if name == "plain_scalar_64":
         return wl.plain_scalar_64(nsteps)
     if name == "vector_random_512":
@@ -219,7 +220,7 @@ def ours(args) -> None:
         cpu = run_oracle_sample(args.workload, args.cpu_seconds, 10 ** 6)
 
     total = args.warmup + args.steps
-    W = make_workload(args.workload, max(total, 1))
+    W = make_workload(args.workload, max(total, 1), args.n)
     tab = load_table(args.workload)
     grids = [(b.grid.nx, b.grid.ny, b.grid.dx, b.grid.dy) for b in W.beams]
     stream = torch.cuda.Stream(device=dev)
@@ -401,6 +402,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--n", type=int, default=0, help="shrink the grid (profiling runs only; not a bench line)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {"homogeneous_aperture_1024": 20000, "plain_scalar_64": 2000}.get(args.workload, 100)

@@ -20,6 +20,7 @@
 namespace prop_dev {
 
 constexpr int MMAX = 64;   // largest GMRES restart length
+constexpr int NSTRIPE = 16; // copies of each Gram-Schmidt accumulator (spreads the atomics)
 
 enum SysStateCode { ST_DONE = 0, ST_ITER = 1, ST_CYCLE_END = 2 };
 
@@ -48,7 +49,8 @@ template <typename T> struct GV {
   C* R0;         // [nsys][ncomp][npts]       right-hand side of the correction system
   double2* E;    // [nsys][ncomp][npts]       correction e_k, FP64
   C* Tmp;        // [nsys][ncomp][npts]       FFT intermediate
-  double2* W64;  // [nb][ncomp][npts]         master field
+  double2* W64;  // master field.  FP64 path: complex128 [nb][ncomp][npts].  FP32 path:
+                 // double-float, planar: hi plane float2 [nb][ncomp][npts], then lo plane
   C* What;       // [nb][ncomp][npts]         2-D spectrum of the field (rounded to T)
   C* Btmp;       // [nb][ncomp][npts]         beam-level FFT intermediate
   C* delta;      // [nb][npts]                (n^2 - n0^2)/n0^2
@@ -63,7 +65,13 @@ template <typename T> struct GV {
   int* nonhomog;        // [nb] 1 if delta != 0 somewhere
   const double2* rk;    // [P] residues r_k
   const double* anorm;  // [P] bound on ||Z - p_k I|| over this grid (backward-error test)
+  double2* part;        // [nsys][3][NSTRIPE][MMAX+1] striped accumulators: dots1, dots2, ||w'||^2
 };
+
+// striped accumulator slot: plane 0 = first projections, 1 = second, 2 = norm
+__device__ __forceinline__ double2* part_at(double2* part, int s, int plane, int stripe, int i) {
+  return part + (((long)s * 3 + plane) * NSTRIPE + stripe) * (MMAX + 1) + i;
+}
 
 // Which buffer a pass reads or writes: item (unit u, component c) lives at
 // base + (u / div) * ustride + c * npts.
@@ -86,6 +94,25 @@ __device__ __forceinline__ float2 to_c(float2 a, float) { return a; }
 __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
 __device__ __forceinline__ double2 to_d(double2 a) { return a; }
 
+// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum) for the
+// double-float master field of the FP32 path.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+// (hi, lo) + v for one real component
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+  float s, e;
+  two_sum(hi, v, s, e);
+  e += lo;
+  fast_two_sum(s, e, hi, lo);
+}
+
 // block-wide sum of a double (blockDim.x threads, multiple of 32); result valid in thread 0
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
@@ -99,6 +126,32 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
   }
   return r;
+}
+
+// Sum a complex value over the warp in its own precision A (float on the FP32
+// path: GB300's FP64 pipe is a small fraction of its FP32 rate), then lane 0
+// adds it, widened to double, into a shared-memory slot.
+template <typename A> __device__ __forceinline__ void warp_add(A re, A im, double2* slot) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) { slot->x += (double)re; slot->y += (double)im; }
+}
+
+// After every warp has added its partials to red[w * (MMAX+1) + i], i <= n:
+// sum over warps and add the block total to acc[i] (one atomic per i).
+// acc points at stripe 0 of the target plane; this CTA adds to stripe blockIdx.x % NSTRIPE.
+__device__ __forceinline__ void flush_partials(double2* red, int nwarps, int n, double2* acc) {
+  __syncthreads();
+  double2* a = acc + (blockIdx.x % NSTRIPE) * (MMAX + 1);
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int w = 0; w < nwarps; ++w) { re += red[w * (MMAX + 1) + i].x; im += red[w * (MMAX + 1) + i].y; }
+    atomicAdd(&a[i].x, re);
+    atomicAdd(&a[i].y, im);
+  }
 }
 
 __device__ __forceinline__ bool unit_active(const SysState* st, int mask, int u) {
@@ -119,13 +172,13 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
   if (!unit_active(g.st, mask, u)) return;
   const int row0 = blockIdx.x * NR;
   const SRC* in = src.at(u, c, g.npts) + (long)row0 * N;
-  double acc = 0.0;
+  T acc = 0;
 #pragma unroll
   for (int e = threadIdx.x; e < NR * N; e += NT) {
     const int r = e / N, n = e % N;
-    SRC v = in[e];
-    if (norm_acc) acc += (double)v.x * v.x + (double)v.y * v.y;
-    s[sidx<N, NR, false>(r, n)] = to_c(v, T());
+    const C v = to_c(in[e], T());
+    if (norm_acc) acc += v.x * v.x + v.y * v.y;
+    s[sidx<N, NR, false>(r, n)] = v;
   }
   __syncthreads();
   fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
@@ -133,7 +186,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
 #pragma unroll
   for (int e = threadIdx.x; e < NR * N; e += NT) out[e] = s[sidx<N, NR, false>(e / N, e % N)];
   if (norm_acc) {
-    const double t = block_sum(acc, red);
+    const double t = block_sum((double)acc, red);
     if (threadIdx.x == 0) atomicAdd(&norm_acc[u], t);
   }
 }
@@ -237,16 +290,63 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   fft_smem<C, N, true, NR, NT, false>(s, g.twx, threadIdx.x);
   const C* dl = g.delta + (long)beam * g.npts + off;
   const long unit_off = ((long)u * g.ncomp + c) * g.npts + off;   // [unit][c][pt] arrays
+  if (ep.mode == EPI_ARNOLDI) {
+    // z_j = M^-1 v_j (stored), w = v_j + delta z_j (stored as v_{j+1}), and the
+    // first Gram-Schmidt projections <v_i, w>, i <= j, while w is in registers.
+    constexpr int TPT = NR * N / NT;
+    __shared__ double2 red2[(NT / 32) * (MMAX + 1)];
+    for (int i = threadIdx.x; i < (NT / 32) * (MMAX + 1); i += NT) red2[i] = make_double2(0.0, 0.0);
+    const long vj = (((long)u * (g.m + 1) + ep.jj) * g.ncomp + c) * g.npts + off;
+    const long zb = (((long)u * g.m + ep.jj) * g.ncomp + c) * g.npts + off;
+    C wv[TPT];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int e = threadIdx.x + q * NT;
+      const C val = s[sidx<N, NR, false>(e / N, e % N)];
+      g.Zb[zb + e] = val;
+      const C v = g.V[vj + e];
+      const C dz = cmul(dl[e], val);
+      C w; w.x = v.x + dz.x; w.y = v.y + dz.y;
+      g.V[vj + (long)g.ncomp * g.npts + e] = w;
+      wv[q] = w;
+    }
+    double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 1);
+    __syncthreads();
+    for (int i = 0; i <= ep.jj; ++i) {
+      const C* vi = g.V + (((long)u * (g.m + 1) + i) * g.ncomp + c) * g.npts + off;
+      T ar = 0, ai = 0;
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        const C a = vi[threadIdx.x + q * NT], b = wv[q];
+        ar += a.x * b.x + a.y * b.y;
+        ai += a.x * b.y - a.y * b.x;
+      }
+      warp_add<T>(ar, ai, myred + i);
+    }
+    flush_partials(red2, NT / 32, ep.jj, part_at(g.part, u, 0, 0, 0));
+    return;
+  }
   double acc = 0.0, acc2 = 0.0;
   for (int e = threadIdx.x; e < NR * N; e += NT) {
     const C val = s[sidx<N, NR, false>(e / N, e % N)];
     switch (ep.mode) {
       case EPI_STORE: dst.at(u, c, g.npts)[off + e] = val; break;
       case EPI_STORE64: ep.out64[unit_off + e] = to_d(val); break;
-      case EPI_ACCUM64: {   // out64 = W64 + val (the new field, written beside the old one)
-        double2 t = g.W64[unit_off + e];
-        t.x += (double)val.x; t.y += (double)val.y;
-        ep.out64[unit_off + e] = t;
+      case EPI_ACCUM64: {   // new field = old field + val, written beside the old one
+        if constexpr (sizeof(T) == 4) {
+          const long plane = (long)g.nb * g.ncomp * g.npts;
+          const float2* ohi = reinterpret_cast<const float2*>(g.W64);
+          float2* nhi = reinterpret_cast<float2*>(ep.out64);
+          float2 h = ohi[unit_off + e], l = ohi[plane + unit_off + e];
+          df_add(h.x, l.x, val.x);
+          df_add(h.y, l.y, val.y);
+          nhi[unit_off + e] = h;
+          nhi[plane + unit_off + e] = l;
+        } else {
+          double2 t = g.W64[unit_off + e];
+          t.x += (double)val.x; t.y += (double)val.y;
+          ep.out64[unit_off + e] = t;
+        }
       } break;
       case EPI_OPERATOR: {
         const double2 v = ep.in64[unit_off + e];
@@ -262,15 +362,6 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
         g.R0[unit_off + e] = m;
         acc += (double)m.x * m.x + (double)m.y * m.y;
         acc2 += (double)val.x * val.x + (double)val.y * val.y;
-      } break;
-      case EPI_ARNOLDI: {
-        const long vb = (((long)u * (g.m + 1) + ep.jj) * g.ncomp + c) * g.npts + off + e;
-        const long zb = (((long)u * g.m + ep.jj) * g.ncomp + c) * g.npts + off + e;
-        g.Zb[zb] = val;
-        const C v = g.V[vb];
-        const C dz = cmul(dl[e], val);
-        C w; w.x = v.x + dz.x; w.y = v.y + dz.y;
-        g.V[vb + (long)g.ncomp * g.npts] = w;
       } break;
       case EPI_TRUERES: {
         const double2 r0 = to_d(g.R0[unit_off + e]);
@@ -303,93 +394,75 @@ template <typename T> __device__ __forceinline__ typename Cx<T>::t* vslot(const 
   return g.V + ((long)s * (g.m + 1) + jj) * g.ncomp * g.npts;
 }
 
-// dots1[i] += <v_i, w>, i <= jj, with w = v_{jj+1}; nrm_b unused here.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_dots(GV<T> g, int jj) {
-  using C = typename Cx<T>::t;
-  __shared__ double red[32];
-  const int s = blockIdx.y;
-  if (g.st[s].state != ST_ITER) return;
-  const long L = (long)g.ncomp * g.npts;
-  const long chunk = (L + gridDim.x - 1) / gridDim.x;
-  const long b0 = blockIdx.x * chunk, b1 = min(L, b0 + chunk);
-  const C* w = vslot(g, s, jj + 1);
-  for (int i = 0; i <= jj; ++i) {
-    const C* v = vslot(g, s, i);
-    double ar = 0.0, ai = 0.0;
-    for (long p = b0 + threadIdx.x; p < b1; p += NT) {
-      const double2 a = to_d(v[p]), b = to_d(w[p]);
-      ar += a.x * b.x + a.y * b.y;
-      ai += a.x * b.y - a.y * b.x;
-    }
-    const double tr = block_sum(ar, red);
-    const double ti = block_sum(ai, red);
-    if (threadIdx.x == 0) {
-      atomicAdd(&g.st[s].dots1[i].x, tr);
-      atomicAdd(&g.st[s].dots1[i].y, ti);
-    }
-  }
-}
-
 // Classical Gram-Schmidt, first subtraction and the re-orthogonalisation dots:
 // w <- w - sum_i dots1[i] v_i; dots2[i] += <v_i, w>; nrm_b += ||w||^2.
+// One chunk of NT*EPT points per CTA; partial sums are reduced per warp into
+// shared memory and flushed once per CTA.
 template <typename T, int NT, int EPT>
 __global__ void __launch_bounds__(NT) k_cgs(GV<T> g, int jj) {
   using C = typename Cx<T>::t;
-  __shared__ double red[32];
   __shared__ C h[MMAX + 1];
+  __shared__ double2 red2[(NT / 32) * (MMAX + 2)];
   const int s = blockIdx.y;
   if (g.st[s].state != ST_ITER) return;
   for (int i = threadIdx.x; i <= jj; i += NT) {
-    const double2 d = g.st[s].dots1[i];
-    h[i].x = (T)d.x; h[i].y = (T)d.y;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < NSTRIPE; ++k) { const double2 d = *part_at(g.part, s, 0, k, i); re += d.x; im += d.y; }
+    h[i].x = (T)re; h[i].y = (T)im;
   }
+  for (int i = threadIdx.x; i < (NT / 32) * (MMAX + 2); i += NT) red2[i] = make_double2(0.0, 0.0);
   __syncthreads();
   const long L = (long)g.ncomp * g.npts;
   C* w = vslot(g, s, jj + 1);
-  const long per = (long)NT * EPT;
-  for (long b0 = (long)blockIdx.x * per; b0 < L; b0 += (long)gridDim.x * per) {
-    C x[EPT];
+  const long b0 = (long)blockIdx.x * NT * EPT;
+  C x[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const long p = b0 + threadIdx.x + (long)q * NT;
+    x[q] = p < L ? w[p] : C{};
+  }
+  for (int i = 0; i <= jj; ++i) {
+    const C* v = vslot(g, s, i);
+    const C hi = h[i];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const long p = b0 + threadIdx.x + (long)q * NT;
-      x[q] = p < L ? w[p] : C{};
+      if (p < L) { const C t = cmul(hi, v[p]); x[q].x -= t.x; x[q].y -= t.y; }
     }
-    for (int i = 0; i <= jj; ++i) {
-      const C* v = vslot(g, s, i);
-      const C hi = h[i];
+  }
+  T nr = 0;
 #pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const long p = b0 + threadIdx.x + (long)q * NT;
-        if (p < L) { const C t = cmul(hi, v[p]); x[q].x -= t.x; x[q].y -= t.y; }
-      }
-    }
-    double nr = 0.0;
+  for (int q = 0; q < EPT; ++q) {
+    const long p = b0 + threadIdx.x + (long)q * NT;
+    if (p < L) { w[p] = x[q]; nr += x[q].x * x[q].x + x[q].y * x[q].y; }
+  }
+  double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 2);
+  warp_add<T>(nr, (T)0, myred + MMAX + 1);
+  for (int i = 0; i <= jj; ++i) {
+    const C* v = vslot(g, s, i);
+    T ar = 0, ai = 0;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const long p = b0 + threadIdx.x + (long)q * NT;
-      if (p < L) { w[p] = x[q]; nr += (double)x[q].x * x[q].x + (double)x[q].y * x[q].y; }
+      if (p < L) {
+        const C a = v[p], b = x[q];
+        ar += a.x * b.x + a.y * b.y;
+        ai += a.x * b.y - a.y * b.x;
+      }
     }
-    const double tn = block_sum(nr, red);
-    if (threadIdx.x == 0) atomicAdd(&g.st[s].nrm_b, tn);
-    for (int i = 0; i <= jj; ++i) {
-      const C* v = vslot(g, s, i);
-      double ar = 0.0, ai = 0.0;
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const long p = b0 + threadIdx.x + (long)q * NT;
-        if (p < L) {
-          const double2 a = to_d(v[p]), b = to_d(x[q]);
-          ar += a.x * b.x + a.y * b.y;
-          ai += a.x * b.y - a.y * b.x;
-        }
-      }
-      const double tr = block_sum(ar, red);
-      const double ti = block_sum(ai, red);
-      if (threadIdx.x == 0) {
-        atomicAdd(&g.st[s].dots2[i].x, tr);
-        atomicAdd(&g.st[s].dots2[i].y, ti);
-      }
+    warp_add<T>(ar, ai, myred + i);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= jj + 1; i += NT) {
+    const int slot = i <= jj ? i : MMAX + 1;
+    double re = 0.0, im = 0.0;
+    for (int wq = 0; wq < NT / 32; ++wq) { re += red2[wq * (MMAX + 2) + slot].x; im += red2[wq * (MMAX + 2) + slot].y; }
+    const int stripe = blockIdx.x % NSTRIPE;
+    if (i <= jj) {
+      double2* a = part_at(g.part, s, 1, stripe, i);
+      atomicAdd(&a->x, re); atomicAdd(&a->y, im);
+    } else {
+      atomicAdd(&part_at(g.part, s, 2, stripe, 0)->x, re);
     }
   }
 }
@@ -459,19 +532,25 @@ __global__ void __launch_bounds__(NT) k_update_e(GV<T> g) {
   const int J = st.jend;
   const long L = (long)g.ncomp * g.npts;
   double2* e = g.E + (long)s * L;
-  double nr = 0.0;
+  using C = typename Cx<T>::t;
+  __shared__ C ys[MMAX];
+  for (int i = threadIdx.x; i < J; i += NT) { ys[i].x = (T)st.y[i].x; ys[i].y = (T)st.y[i].y; }
+  __syncthreads();
+  // the increment sum_i y_i z_i is formed in T, then added once to the FP64 correction
+  T nr = 0;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
-    double2 a = e[p];
+    C inc; inc.x = 0; inc.y = 0;
     for (int i = 0; i < J; ++i) {
-      const double2 z = to_d(g.Zb[((long)s * g.m + i) * L + p]);
-      const double2 y = st.y[i];
-      a.x += y.x * z.x - y.y * z.y;
-      a.y += y.x * z.y + y.y * z.x;
+      const C t = cmul(ys[i], g.Zb[((long)s * g.m + i) * L + p]);
+      inc.x += t.x; inc.y += t.y;
     }
+    double2 a = e[p];
+    a.x += (double)inc.x; a.y += (double)inc.y;
     e[p] = a;
-    nr += a.x * a.x + a.y * a.y;
+    const T ax = (T)a.x, ay = (T)a.y;
+    nr += ax * ax + ay * ay;
   }
-  const double t = block_sum(nr, red);
+  const double t = block_sum((double)nr, red);
   if (threadIdx.x == 0) atomicAdd(&g.st[s].enorm2, t);
 }
 
@@ -480,9 +559,16 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_residue_sum(GV<T> g, double2* Wn) {
   const int b = blockIdx.y;
   const long L = (long)g.ncomp * g.npts;
-  double2* w = Wn + (long)b * L;
+  const long plane = (long)g.nb * L;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
-    double2 a = w[p];
+    double2 a;
+    if constexpr (sizeof(T) == 4) {
+      const float2* wh = reinterpret_cast<const float2*>(Wn);
+      const float2 h = wh[(long)b * L + p], l = wh[plane + (long)b * L + p];
+      a.x = (double)h.x + (double)l.x; a.y = (double)h.y + (double)l.y;
+    } else {
+      a = Wn[(long)b * L + p];
+    }
     for (int k = 0; k < g.P; ++k) {
       if (!g.st[b * g.P + k].used) continue;
       const double2 e = g.E[((long)b * g.P + k) * L + p];
@@ -490,7 +576,43 @@ __global__ void __launch_bounds__(NT) k_residue_sum(GV<T> g, double2* Wn) {
       a.x += r.x * e.x - r.y * e.y;
       a.y += r.x * e.y + r.y * e.x;
     }
-    w[p] = a;
+    if constexpr (sizeof(T) == 4) {
+      float2* wh = reinterpret_cast<float2*>(Wn);
+      float2 h, l;
+      h.x = (float)a.x; h.y = (float)a.y;
+      l.x = (float)(a.x - (double)h.x); l.y = (float)(a.y - (double)h.y);
+      wh[(long)b * L + p] = h;
+      wh[plane + (long)b * L + p] = l;
+    } else {
+      Wn[(long)b * L + p] = a;
+    }
+  }
+}
+
+// Field <-> complex128 staging: FP32 path splits into / joins from the
+// double-float planes; FP64 path copies.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_field_io(GV<T> g, int slot, double2* stage, int to_field) {
+  const long L = (long)g.ncomp * g.npts;
+  const long plane = (long)g.nb * L;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
+    const long i = (long)slot * L + p;
+    if constexpr (sizeof(T) == 4) {
+      float2* w = reinterpret_cast<float2*>(g.W64);
+      if (to_field) {
+        const double2 a = stage[p];
+        float2 h, l;
+        h.x = (float)a.x; h.y = (float)a.y;
+        l.x = (float)(a.x - (double)h.x); l.y = (float)(a.y - (double)h.y);
+        w[i] = h; w[plane + i] = l;
+      } else {
+        const float2 h = w[i], l = w[plane + i];
+        stage[p] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+      }
+    } else {
+      if (to_field) g.W64[i] = stage[p];
+      else stage[p] = g.W64[i];
+    }
   }
 }
 
@@ -557,11 +679,31 @@ __device__ __forceinline__ double dabs2(double2 a) { return a.x * a.x + a.y * a.
 // After the dots of Arnoldi column jj: form h, rotate with the previous Givens
 // rotations, make the new one, update g and the residual estimate |g[jj+1]|;
 // end the cycle on convergence, breakdown or jj+1 == m (solving R y = g).
+// One block per system: the block first folds the striped accumulators into
+// dots1, dots2 and nrm_b (clearing the stripes), then thread 0 does the rest.
 __global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bnorm2, double tol,
-                                 int m, int jj, double breakdown, const double* anorm, int backward) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+                                 int m, int jj, double breakdown, const double* anorm, int backward,
+                                 double2* part) {
+  for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
     SysState& q = st[s];
     if (q.state != ST_ITER) continue;
+    for (int i = threadIdx.x; i <= jj; i += blockDim.x) {
+      double2 a = make_double2(0.0, 0.0), b = a;
+      for (int k = 0; k < NSTRIPE; ++k) {
+        double2* pa = part_at(part, s, 0, k, i);
+        double2* pb = part_at(part, s, 1, k, i);
+        a.x += pa->x; a.y += pa->y; b.x += pb->x; b.y += pb->y;
+        *pa = make_double2(0.0, 0.0); *pb = make_double2(0.0, 0.0);
+      }
+      q.dots1[i] = a; q.dots2[i] = b;
+    }
+    if (threadIdx.x == 0) {
+      double nb = 0.0;
+      for (int k = 0; k < NSTRIPE; ++k) { double2* pn = part_at(part, s, 2, k, 0); nb += pn->x; *pn = make_double2(0.0, 0.0); }
+      q.nrm_b = nb;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) continue;
     const int L = MMAX + 1;
     double2* col = &q.H[jj * L];
     double d2 = 0.0;

@@ -37,14 +37,19 @@ bool supported_n(int n) {
   }
 }
 
-template <typename T> constexpr int cols_per_cta() { return sizeof(T) == 4 ? 8 : 4; }
-constexpr int NT_PASS = 256;
+// Launch geometry of the FFT passes: small CTAs, so that one 1024^2 field still
+// spreads over several CTAs per SM and their load / transform / store phases overlap.
+template <typename T> constexpr int cols_per_cta() { return sizeof(T) == 4 ? 4 : 2; }   // 32-byte row segments
+template <int N> constexpr int rows_nr() { return N <= 128 ? 16 : (N == 256 ? 8 : (N <= 512 ? 4 : 2)); }
+constexpr int clamp_nt(int t) { return t < 64 ? 64 : (t > 256 ? 256 : t); }
+template <int N> constexpr int rows_nt() { return clamp_nt(rows_nr<N>() * N / 16); }
+template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * cols_per_cta<T>() / 16); }
 constexpr int NT_VEC = 256;
-constexpr int EPT_CGS = 4;
+constexpr int EPT_CGS = 8;
 
 struct Layout {
   size_t V, Zb, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
-      rk, anorm, stage, iters, cycles, resid, flags, end;
+      rk, anorm, part, stage, iters, cycles, resid, flags, end;
 };
 
 struct Group {
@@ -117,7 +122,8 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec) {
   L.nonhomog = take(nb * sizeof(int));
   L.rk = take(P * 16);
   L.anorm = take(P * sizeof(double));
-  L.stage = take(npts * 16);
+  L.part = take(nsys * 3 * NSTRIPE * (MMAX + 1) * sizeof(double2));
+  L.stage = take(C * npts * 16);
   L.iters = take(nsys * sizeof(int));
   L.cycles = take(nsys * sizeof(int));
   L.resid = take(nsys * sizeof(double));
@@ -143,6 +149,7 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   g.st = (SysState*)(b + L.st); g.bnorm2 = (double*)(b + L.bnorm2); g.nonhomog = (int*)(b + L.nonhomog);
   g.rk = (const double2*)(b + L.rk);
   g.anorm = (const double*)(b + L.anorm);
+  g.part = (double2*)(b + L.part);
   return g;
 }
 
@@ -151,7 +158,6 @@ template <typename C> Buf<C> buf(C* base, long ustride, int div = 1) { Buf<C> b;
 // ---------------------------------------------------------------------------
 // Launch dispatch over the compiled sizes
 // ---------------------------------------------------------------------------
-template <typename T, int N> constexpr int NRC() { return N <= 256 ? 16 : (N <= 512 ? 8 : 4); }
 
 // Raise the dynamic shared-memory limit of one kernel instantiation (once per process).
 template <typename K> cudaError_t set_smem_once(K kernel, size_t bytes, bool& done) {
@@ -165,14 +171,14 @@ template <typename T, int N, typename SRC>
 cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst, int mask, double* nacc,
                        int units, cudaStream_t st) {
   using C = typename Cx<T>::t;
-  constexpr int NR = NRC<T, N>();
+  constexpr int NR = rows_nr<N>(), NT = rows_nt<N>();
   const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
-  auto k = k_rows_fwd<T, N, NR, NT_PASS, SRC>;
+  auto k = k_rows_fwd<T, N, NR, NT, SRC>;
   static bool attr = false;
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units * g.ncomp);
-  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, nacc);
+  k<<<grid, NT, sm, st>>>(g, src, dst, mask, nacc);
   return cudaGetLastError();
 }
 
@@ -180,14 +186,14 @@ template <typename T, int N>
 cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask,
                        int skip, EpiArgs ep, int units, cudaStream_t st) {
   using C = typename Cx<T>::t;
-  constexpr int NR = NRC<T, N>();
+  constexpr int NR = rows_nr<N>(), NT = rows_nt<N>();
   const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
-  auto k = k_rows_inv<T, N, NR, NT_PASS>;
+  auto k = k_rows_inv<T, N, NR, NT>;
   static bool attr = false;
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units * g.ncomp);
-  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, skip, ep);
+  k<<<grid, NT, sm, st>>>(g, src, dst, mask, skip, ep);
   return cudaGetLastError();
 }
 
@@ -196,14 +202,14 @@ cudaError_t cols_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T
                    int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
                    Buf<typename Cx<T>::t> spec) {
   using C = typename Cx<T>::t;
-  constexpr int NV = cols_per_cta<T>();
+  constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
   const size_t sm = smem_elems<NY, NV, true>() * sizeof(C);
-  auto k = k_cols<T, NY, NV, NT_PASS>;
+  auto k = k_cols<T, NY, NV, NT>;
   static bool attr = false;
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.nx / NV, units * g.ncomp);
-  k<<<grid, NT_PASS, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, spec);
+  k<<<grid, NT, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, spec);
   return cudaGetLastError();
 }
 
@@ -248,7 +254,7 @@ EpiArgs epi(int mode, int jj = 0, const double2* in64 = nullptr, double2* out64 
   EpiArgs e; e.mode = mode; e.jj = jj; e.in64 = in64; e.out64 = out64; return e;
 }
 
-int vec_blocks(long L) { return (int)std::max<long>(1, std::min<long>(1024, (L + NT_VEC * 16 - 1) / (NT_VEC * 16))); }
+int vec_blocks(long L) { return (int)std::max<long>(1, std::min<long>(2048, (L + NT_VEC * 4 - 1) / (NT_VEC * 4))); }
 
 #define CK(...)                                      \
   do {                                               \
@@ -344,10 +350,10 @@ template <typename T> int upload_group_tables(prop* h, Group& G) {
 // ---------------------------------------------------------------------------
 // Launch accounting
 // ---------------------------------------------------------------------------
-enum Kind { K_ROWS_FWD, K_COLS, K_ROWS_INV, K_DOTS, K_CGS, K_NORMALIZE, K_UPDATE_E, K_RESIDUE, K_MEDIUM,
+enum Kind { K_ROWS_FWD, K_COLS, K_ROWS_INV, K_FIELD_IO, K_CGS, K_NORMALIZE, K_UPDATE_E, K_RESIDUE, K_MEDIUM,
             K_CONTROL, K_INIT, K_SCALE };
 const char* kind_name(int k) {
-  static const char* n[PROP_NKINDS] = {"rows_fwd", "cols", "rows_inv", "dots", "cgs", "normalize",
+  static const char* n[PROP_NKINDS] = {"rows_fwd", "cols", "rows_inv", "field_io", "cgs", "normalize",
                                        "update_e", "residue_sum", "medium", "control", "init_systems",
                                        "scale_v0"};
   return n[k];
@@ -414,6 +420,7 @@ template <typename T> int step_group(prop* h, Group& G) {
   double2* Wn = (double2*)(h->ws + (G.cur == 0 ? G.off.W64b : G.off.W64a));
   const int tb = 128, tg = (nsys + tb - 1) / tb;
   const int vb = vec_blocks(F);
+  const int cgs_blocks = (int)((F + NT_VEC * EPT_CGS - 1) / (NT_VEC * EPT_CGS));
 
   // which beams carry a non-zero delta (read back once per medium change)
   if (G.medium_dirty) {
@@ -427,14 +434,19 @@ template <typename T> int step_group(prop* h, Group& G) {
 
   // w_hat = FFT2(w); ||w||^2 per beam
   CK(cudaMemsetAsync(g.bnorm2, 0, nb * sizeof(double), st));
-  { Prof p_(h, K_ROWS_FWD, (16 + cs) * pts * nb * Cn);
-    CK(rows_fwd<T, double2>(g, buf(g.W64, F), buf(g.Btmp, F), -1, g.bnorm2, nb, st)); }
+  if constexpr (sizeof(T) == 4) {   // the hi plane of the double-float field is the FP32 working copy
+    Prof p_(h, K_ROWS_FWD, 2 * cs * pts * nb * Cn);
+    CK(rows_fwd<T, float2>(g, buf((float2*)g.W64, F), buf(g.Btmp, F), -1, n_inh ? g.bnorm2 : nullptr, nb, st));
+  } else {
+    Prof p_(h, K_ROWS_FWD, (16 + cs) * pts * nb * Cn);
+    CK(rows_fwd<T, double2>(g, buf(g.W64, F), buf(g.Btmp, F), -1, g.bnorm2, nb, st));
+  }
   // column DFT (spectrum kept when poles will need it), then the free-space part
   // Wn = w + IFFT2[(r - 1) w_hat] (Eq. approx_fs_prop), in one column pass
   { Prof p_(h, K_COLS, (n_inh ? 4 : 3) * cs * pts * nb * Cn);
     CK(cols<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 1, MUL_TABLE, 1, 0, -1, (T)1, nb, st,
                n_inh ? buf(g.What, F) : Buf<C>{nullptr, 0, 1})); }
-  { Prof p_(h, K_ROWS_INV, (cs + 32) * pts * nb * Cn);
+  { Prof p_(h, K_ROWS_INV, (cs + 32) * pts * nb * Cn);   // read increment, old field (16 B), write new (16 B)
     CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0, epi(EPI_ACCUM64, 0, nullptr, Wn), nb, st)); }
   const int bw = h->prec == PROP_FP32 ? 1 : 0;
   if (n_inh == 0) {           // homogeneous medium: the free-space step is exact, no correction
@@ -481,14 +493,13 @@ template <typename T> int step_group(prop* h, Group& G) {
         CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st)); }
       { Prof p_(h, K_COLS, 2 * cs * act);
         CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
-      { Prof p_(h, K_ROWS_INV, 5 * cs * act);
+      { Prof p_(h, K_ROWS_INV, (5 + jj) * cs * act);     // epilogue + first projections (v_j read once)
         CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
-      { Prof p_(h, K_DOTS, (jj + 2) * cs * act);
-        k_dots<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CGS, (2.0 * (jj + 1) + 2) * cs * act);
-        k_cgs<T, NT_VEC, EPT_CGS><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
+        k_cgs<T, NT_VEC, EPT_CGS><<<dim3(cgs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CONTROL, 0);
-        k_arnoldi_finish<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown, g.anorm, bw); }
+        k_arnoldi_finish<<<nsys, 64, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown, g.anorm, bw,
+                                               g.part); }
       { Prof p_(h, K_NORMALIZE, 0);
         k_normalize<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CONTROL, 0);
@@ -666,12 +677,24 @@ int prop_set_medium(prop* h, int32_t beam, const void* n2) {
   return PROP_OK;
 }
 
+static int field_io(prop* h, Group& G, int slot, int to_field) {
+  const long F = (long)h->C * G.npts;
+  const int blocks = (int)std::min<long>(2048, (F + 255) / 256);
+  double2* stage = (double2*)(h->ws + G.off.stage);
+  Prof p_(h, K_FIELD_IO, 32.0 * F);
+  if (h->prec == PROP_FP64) k_field_io<double, 256><<<blocks, 256, 0, h->stream>>>(view<double>(h, G), slot, stage, to_field);
+  else k_field_io<float, 256><<<blocks, 256, 0, h->stream>>>(view<float>(h, G), slot, stage, to_field);
+  CK(cudaGetLastError());
+  return PROP_OK;
+}
+
 int prop_set_field(prop* h, int32_t beam, const void* w) {
   if (!h || !w || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
   Group& G = h->groups[h->beam_group[beam]];
   const long F = (long)h->C * G.npts;
-  char* dst = h->ws + (G.cur == 0 ? G.off.W64a : G.off.W64b) + (size_t)h->beam_slot[beam] * F * 16;
-  CK(cudaMemcpyAsync(dst, w, F * 16, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(h->ws + G.off.stage, w, F * 16, cudaMemcpyDefault, h->stream));
+  const int rc = field_io(h, G, h->beam_slot[beam], 1);
+  if (rc) return rc;
   h->steps = 0;
   return PROP_OK;
 }
@@ -680,8 +703,9 @@ int prop_get_field(prop* h, int32_t beam, void* w) {
   if (!h || !w || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
   Group& G = h->groups[h->beam_group[beam]];
   const long F = (long)h->C * G.npts;
-  const char* src = h->ws + (G.cur == 0 ? G.off.W64a : G.off.W64b) + (size_t)h->beam_slot[beam] * F * 16;
-  CK(cudaMemcpyAsync(w, src, F * 16, cudaMemcpyDefault, h->stream));
+  const int rc = field_io(h, G, h->beam_slot[beam], 0);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(w, h->ws + G.off.stage, F * 16, cudaMemcpyDefault, h->stream));
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, w) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
     cudaGetLastError();
