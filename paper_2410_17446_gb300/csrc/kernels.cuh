@@ -66,7 +66,21 @@ template <typename T> struct GV {
   const double2* rk;    // [P] residues r_k
   const double* anorm;  // [P] bound on ||Z - p_k I|| over this grid (backward-error test)
   double2* part;        // [nsys][3][NSTRIPE][MMAX+1] striped accumulators: dots1, dots2, ||w'||^2
+  // vector operator (ncomp = 2) only
+  C* psi;        // [nb][5][npts]  coefficients of Z - Z_fs: D1 = delta + psit_xx, D2 = delta + psit_yy,
+                 //                X = psit_xy, px = psit_x, py = psit_y (psit = psi/(k0 n0)^2, psi = Log n^2)
+  C* Tmp2;       // [nsys][ncomp][npts] second column-pass output (the d/dy branch)
+  T kx0, ky0;    // 2 pi/(nx dx), 2 pi/(ny dy): wavenumber of FFT index 1
 };
+
+// Signed FFT frequency index of position i on an n-point grid.
+__device__ __forceinline__ int ffreq(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+// i*k for a first derivative (zero at the unpaired Nyquist index), as a complex factor
+template <typename C, typename T> __device__ __forceinline__ C ik_factor(int i, int n, T k0) {
+  C f; f.x = 0;
+  f.y = ((n % 2) == 0 && i == n / 2) ? (T)0 : (T)ffreq(i, n) * k0;
+  return f;
+}
 
 // striped accumulator slot: plane 0 = first projections, 1 = second, 2 = norm
 __device__ __forceinline__ double2* part_at(double2* part, int s, int plane, int stripe, int i) {
@@ -84,7 +98,8 @@ template <typename C> struct Buf {
   }
 };
 
-enum MulMode { MUL_NONE = 0, MUL_TABLE = 1, MUL_POLE_INV = 2, MUL_POLE_FWD = 3, MUL_SCALE = 4 };
+enum MulMode { MUL_NONE = 0, MUL_TABLE = 1, MUL_POLE_INV = 2, MUL_POLE_FWD = 3, MUL_SCALE = 4,
+               MUL_DY = 5, MUL_DYY = 6 };   // scale * i ky,  scale * (-ky^2)
 enum EpiMode { EPI_STORE = 0, EPI_STORE64 = 1, EPI_ACCUM64 = 2, EPI_R0 = 3, EPI_ARNOLDI = 4,
                EPI_TRUERES = 5, EPI_OPERATOR = 6 };
 
@@ -196,11 +211,15 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
 // grid = (nx/NV, units*ncomp).  The multiplier sees kx index i = x0 + v and ky
 // index n; pole k = unit % P for system units.
 // ---------------------------------------------------------------------------
-template <typename T, int NY, int NV, int NT>
+// With DY the tile is 2*NV wide: columns NV..2NV-1 receive i*ky times the
+// multiplied spectrum and leave through `dy` (the d/dy branch of the vector
+// operator), transformed in the same shared-memory FFT.
+template <typename T, int NY, int NV, int NT, bool DY>
 __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                              int mask, int fwd, int mul, int inv, int skip_homog, int pole,
-                                             T scale, Buf<typename Cx<T>::t> spec) {
+                                             T scale, Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
   using C = typename Cx<T>::t;
+  constexpr int W = DY ? 2 * NV : NV;     // tile width in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
@@ -211,14 +230,14 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
 #pragma unroll 8
   for (int e = threadIdx.x; e < NY * NV; e += NT) {
     const int n = e / NV, v = e % NV;
-    s[n * NV + v] = in[(long)n * g.nx + x0 + v];
+    s[n * W + v] = in[(long)n * g.nx + x0 + v];
   }
   __syncthreads();
-  if (fwd) fft_smem<C, NY, false, NV, NT, true>(s, g.twy, threadIdx.x);
+  if (fwd) fft_smem<C, NY, false, W, NT, true>(s, g.twy, threadIdx.x);   // (DY: the extra columns are unused here)
   if (spec.base) {   // keep the 2-D spectrum as well (read again by the pole solves)
     C* sp = spec.at(u, c, g.npts);
 #pragma unroll 8
-    for (int e = threadIdx.x; e < NY * NV; e += NT) sp[(long)(e / NV) * g.nx + x0 + e % NV] = s[e];
+    for (int e = threadIdx.x; e < NY * NV; e += NT) sp[(long)(e / NV) * g.nx + x0 + e % NV] = s[(e / NV) * W + e % NV];
   }
   if (mul != MUL_NONE) {
     const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD);
@@ -228,11 +247,17 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
     const T pim = pm ? g.pim[k] : (T)0;
     for (int e = threadIdx.x; e < NY * NV; e += NT) {
       const int n = e / NV, v = e % NV, i = x0 + v;
-      C a = s[e];
+      C a = s[n * W + v];
       if (mul == MUL_TABLE) {
         a = cmul(a, g.basemul[(long)n * g.nx + i]);
       } else if (mul == MUL_SCALE) {
         a.x *= scale; a.y *= scale;
+      } else if (mul == MUL_DY) {
+        a = cmul(a, ik_factor<C>(n, g.ny, g.ky0));
+        a.x *= scale; a.y *= scale;
+      } else if (mul == MUL_DYY) {
+        const T k = (T)ffreq(n, g.ny) * g.ky0;
+        a.x *= -k * k * scale; a.y *= -k * k * scale;
       } else {
         // Re(zeta_fs - p) = ax + ay from (hi, lo) pairs: the hi parts cancel
         // exactly near the pole (Sterbenz), the lo parts restore the rest.
@@ -246,16 +271,25 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
         }
         a = cmul(a, f);
       }
-      s[e] = a;
+      s[n * W + v] = a;
+      if constexpr (DY) s[n * W + NV + v] = cmul(a, ik_factor<C>(n, g.ny, g.ky0));
     }
     __syncthreads();
   }
-  if (inv) fft_smem<C, NY, true, NV, NT, true>(s, g.twy, threadIdx.x);
+  if (inv) fft_smem<C, NY, true, W, NT, true>(s, g.twy, threadIdx.x);
   C* out = dst.at(u, c, g.npts);
 #pragma unroll 8
   for (int e = threadIdx.x; e < NY * NV; e += NT) {
     const int n = e / NV, v = e % NV;
-    out[(long)n * g.nx + x0 + v] = s[e];
+    out[(long)n * g.nx + x0 + v] = s[n * W + v];
+  }
+  if constexpr (DY) {
+    C* o2 = dy.at(u, c, g.npts);
+#pragma unroll 8
+    for (int e = threadIdx.x; e < NY * NV; e += NT) {
+      const int n = e / NV, v = e % NV;
+      o2[(long)n * g.nx + x0 + v] = s[n * W + NV + v];
+    }
   }
 }
 
@@ -267,6 +301,8 @@ struct EpiArgs {
   int jj;              // Arnoldi column (EPI_ARNOLDI)
   const double2* in64; // EPI_OPERATOR input
   double2* out64;      // EPI_STORE64 / EPI_OPERATOR output
+  const void* aux;     // vector operator: (Z - Z_fs) applied to the same field, complex T
+  int kxsel;           // before the inverse row DFT multiply by 1 (0), i kx (1) or -kx^2 (2)
 };
 
 template <typename T, int N, int NR, int NT>
@@ -285,7 +321,12 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   const long off = (long)row0 * N;
   const C* in = src.at(u, c, g.npts) + off;
 #pragma unroll
-  for (int e = threadIdx.x; e < NR * N; e += NT) s[sidx<N, NR, false>(e / N, e % N)] = in[e];
+  for (int e = threadIdx.x; e < NR * N; e += NT) {
+    C a = in[e];
+    if (ep.kxsel == 1) a = cmul(a, ik_factor<C>(e % N, N, g.kx0));
+    else if (ep.kxsel == 2) { const T k = (T)ffreq(e % N, N) * g.kx0; a.x *= -k * k; a.y *= -k * k; }
+    s[sidx<N, NR, false>(e / N, e % N)] = a;
+  }
   __syncthreads();
   fft_smem<C, N, true, NR, NT, false>(s, g.twx, threadIdx.x);
   const C* dl = g.delta + (long)beam * g.npts + off;
@@ -349,11 +390,16 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
         }
       } break;
       case EPI_OPERATOR: {
-        const double2 v = ep.in64[unit_off + e];
-        const double2 d = to_d(dl[e]);
         double2 o;
-        o.x = (double)val.x + d.x * v.x - d.y * v.y;
-        o.y = (double)val.y + d.x * v.y + d.y * v.x;
+        if (g.ncomp == 2) {   // Z_fs v (this pass) + (Z - Z_fs) v (computed before into aux)
+          const double2 a = to_d(reinterpret_cast<const C*>(ep.aux)[unit_off + e]);
+          o.x = (double)val.x + a.x; o.y = (double)val.y + a.y;
+        } else {
+          const double2 v = ep.in64[unit_off + e];
+          const double2 d = to_d(dl[e]);
+          o.x = (double)val.x + d.x * v.x - d.y * v.y;
+          o.y = (double)val.y + d.x * v.y + d.y * v.x;
+        }
         ep.out64[unit_off + e] = o;
       } break;
       case EPI_R0: {
@@ -365,12 +411,18 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
       } break;
       case EPI_TRUERES: {
         const double2 r0 = to_d(g.R0[unit_off + e]);
-        const double2 ee = g.E[unit_off + e];
-        const double2 d = to_d(dl[e]);
-        double2 r;
-        r.x = r0.x - (double)val.x - (d.x * ee.x - d.y * ee.y);
-        r.y = r0.y - (double)val.y - (d.x * ee.y + d.y * ee.x);
         const long vb = (((long)u * (g.m + 1)) * g.ncomp + c) * g.npts + off + e;
+        double2 r;
+        if (g.ncomp == 2) {   // (Z - Z_fs) e was written into v_0 by the preceding pass
+          const double2 a = to_d(g.V[vb]);
+          r.x = r0.x - (double)val.x - a.x;
+          r.y = r0.y - (double)val.y - a.y;
+        } else {
+          const double2 ee = g.E[unit_off + e];
+          const double2 d = to_d(dl[e]);
+          r.x = r0.x - (double)val.x - (d.x * ee.x - d.y * ee.y);
+          r.y = r0.y - (double)val.y - (d.x * ee.y + d.y * ee.x);
+        }
         g.V[vb] = to_c(r, T());
         acc += r.x * r.x + r.y * r.y;
       } break;
@@ -383,6 +435,129 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   if (ep.mode == EPI_R0) {
     const double t = block_sum(acc2, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3 of the vector operator (ncomp = 2), Eq. (Z_bar_eq).  A unit's two
+// components arrive as column-pass outputs A_c = colIDFT(m x_hat_c) and
+// B_c = colIDFT(i ky m x_hat_c).  Six inverse row DFTs in one shared-memory
+// transform give z_c, d_x z_c (from i kx A_c) and d_y z_c (from B_c); the
+// epilogue applies the psi and delta terms:
+//   ((Z - Z_fs) z)_1 = D1 z1 + X z2 + px d_x z1 + py d_x z2
+//   ((Z - Z_fs) z)_2 = X z1 + D2 z2 + px d_y z1 + py d_y z2
+// grid = (ny/NR, units).
+// ---------------------------------------------------------------------------
+enum VecEpi { VEPI_ARNOLDI = 0, VEPI_R0 = 1, VEPI_OPDIFF = 2 };
+
+template <typename T, int N, int NR, int NT>
+__global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
+                                                     Buf<typename Cx<T>::t> out, int mask, int skip_homog,
+                                                     int mode, int jj) {
+  using C = typename Cx<T>::t;
+  constexpr int NVV = 6 * NR;                 // vectors: (c, {z, dx, dy}) x NR rows
+  constexpr int TPT = NR * N / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[32];
+  __shared__ double2 red2[(NT / 32) * (MMAX + 1)];
+  const int u = blockIdx.y;
+  if (!unit_active(g.st, mask, u)) return;
+  const int beam = (mode == VEPI_OPDIFF && mask < 0) ? u : u / g.P;
+  if (skip_homog && !g.nonhomog[beam]) return;
+  const int row0 = blockIdx.x * NR;
+  const long off = (long)row0 * N;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const C* a = A.at(u, c, g.npts) + off;
+    const C* b = B.at(u, c, g.npts) + off;
+    for (int e = threadIdx.x; e < NR * N; e += NT) {
+      const int r = e / N, n = e % N;
+      const C x = a[e];
+      s[sidx<N, NVV, false>((c * 3 + 0) * NR + r, n)] = x;
+      s[sidx<N, NVV, false>((c * 3 + 1) * NR + r, n)] = cmul(x, ik_factor<C>(n, N, g.kx0));
+      s[sidx<N, NVV, false>((c * 3 + 2) * NR + r, n)] = b[e];
+    }
+  }
+  __syncthreads();
+  fft_smem<C, N, true, NVV, NT, false>(s, g.twx, threadIdx.x);
+  const C* cf = g.psi + (long)beam * 5 * g.npts + off;    // D1, D2, X, px, py planes
+  const long F = 2 * g.npts;
+  double acc = 0.0, acc2 = 0.0;
+  C w1v[TPT], w2v[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int e = threadIdx.x + q * NT, r = e / N, n = e % N;
+    const C z1 = s[sidx<N, NVV, false>(0 * NR + r, n)], x1 = s[sidx<N, NVV, false>(1 * NR + r, n)],
+            y1 = s[sidx<N, NVV, false>(2 * NR + r, n)];
+    const C z2 = s[sidx<N, NVV, false>(3 * NR + r, n)], x2 = s[sidx<N, NVV, false>(4 * NR + r, n)],
+            y2 = s[sidx<N, NVV, false>(5 * NR + r, n)];
+    const C D1 = cf[e], D2 = cf[g.npts + e], X = cf[2 * g.npts + e], px = cf[3 * g.npts + e], py = cf[4 * g.npts + e];
+    C d1 = cmul(D1, z1), d2 = cmul(X, z1), t;
+    t = cmul(X, z2);  d1.x += t.x; d1.y += t.y;
+    t = cmul(px, x1); d1.x += t.x; d1.y += t.y;
+    t = cmul(py, x2); d1.x += t.x; d1.y += t.y;
+    t = cmul(D2, z2); d2.x += t.x; d2.y += t.y;
+    t = cmul(px, y1); d2.x += t.x; d2.y += t.y;
+    t = cmul(py, y2); d2.x += t.x; d2.y += t.y;
+    if (mode == VEPI_ARNOLDI) {
+      const long vj = ((long)u * (g.m + 1) + jj) * F + off + e;
+      const long zb = ((long)u * g.m + jj) * F + off + e;
+      g.Zb[zb] = z1; g.Zb[zb + g.npts] = z2;
+      const C v1 = g.V[vj], v2 = g.V[vj + g.npts];
+      C w1, w2;
+      w1.x = v1.x + d1.x; w1.y = v1.y + d1.y;
+      w2.x = v2.x + d2.x; w2.y = v2.y + d2.y;
+      g.V[vj + F] = w1; g.V[vj + F + g.npts] = w2;
+      w1v[q] = w1; w2v[q] = w2;
+    } else if (mode == VEPI_R0) {
+      const long rb = (long)u * F + off + e;
+      C m1, m2; m1.x = -d1.x; m1.y = -d1.y; m2.x = -d2.x; m2.y = -d2.y;
+      g.R0[rb] = m1; g.R0[rb + g.npts] = m2;
+      acc += (double)m1.x * m1.x + (double)m1.y * m1.y + (double)m2.x * m2.x + (double)m2.y * m2.y;
+      acc2 += (double)z1.x * z1.x + (double)z1.y * z1.y + (double)z2.x * z2.x + (double)z2.y * z2.y;
+    } else {
+      out.at(u, 0, g.npts)[off + e] = d1;
+      out.at(u, 1, g.npts)[off + e] = d2;
+    }
+  }
+  if (mode == VEPI_ARNOLDI) {   // first Gram-Schmidt projections over both components
+    for (int i = threadIdx.x; i < (NT / 32) * (MMAX + 1); i += NT) red2[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 1);
+    for (int i = 0; i <= jj; ++i) {
+      const C* vi = g.V + ((long)u * (g.m + 1) + i) * F + off;
+      T ar = 0, ai = 0;
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        const int e = threadIdx.x + q * NT;
+        const C a1 = vi[e], a2 = vi[g.npts + e];
+        ar += a1.x * w1v[q].x + a1.y * w1v[q].y + a2.x * w2v[q].x + a2.y * w2v[q].y;
+        ai += a1.x * w1v[q].y - a1.y * w1v[q].x + a2.x * w2v[q].y - a2.y * w2v[q].x;
+      }
+      warp_add<T>(ar, ai, myred + i);
+    }
+    flush_partials(red2, NT / 32, jj, part_at(g.part, u, 0, 0, 0));
+  } else if (mode == VEPI_R0) {
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&g.st[u].nrm_a, t);
+    const double t2 = block_sum(acc2, red);
+    if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t2);
+  }
+}
+
+// psi coefficient planes, after psit_xx, psit_yy, psit_xy, psit_x, psit_y have
+// been written into planes 0..4: planes 0, 1 become delta + psit_xx, delta + psit_yy.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_psi_combine(GV<T> g, int beam) {
+  using C = typename Cx<T>::t;
+  C* pl = g.psi + (long)beam * 5 * g.npts;
+  const C* d = g.delta + (long)beam * g.npts;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < g.npts; p += (long)gridDim.x * NT) {
+    const C a = d[p];
+    C x = pl[p], y = pl[g.npts + p];
+    x.x += a.x; x.y += a.y; y.x += a.x; y.y += a.y;
+    pl[p] = x; pl[g.npts + p] = y;
   }
 }
 
@@ -616,9 +791,11 @@ __global__ void __launch_bounds__(NT) k_field_io(GV<T> g, int slot, double2* sta
   }
 }
 
-// delta = (n^2 - n0^2)/n0^2 from a complex128 slab; flags a non-zero delta.
+// delta = (n^2 - n0^2)/n0^2 from a complex128 slab; flags a non-zero delta;
+// with psi_out also writes psi = Log n^2 (principal branch) for the vector operator.
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2* n2, double n0sq) {
+__global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2* n2, double n0sq,
+                                               typename Cx<T>::t* psi_out) {
   using C = typename Cx<T>::t;
   C* d = g.delta + (long)beam * g.npts;
   int nz = 0;
@@ -627,6 +804,10 @@ __global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2*
     double2 v; v.x = (a.x - n0sq) / n0sq; v.y = a.y / n0sq;
     const C t = to_c(v, T());
     d[p] = t;
+    if (psi_out) {
+      const double2 lg = make_double2(0.5 * log(a.x * a.x + a.y * a.y), atan2(a.y, a.x));
+      psi_out[p] = to_c(lg, T());
+    }
     nz |= (t.x != (T)0 || t.y != (T)0);
   }
   if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&g.nonhomog[beam], 1);

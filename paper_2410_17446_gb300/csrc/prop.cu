@@ -49,7 +49,7 @@ constexpr int EPT_CGS = 8;
 
 struct Layout {
   size_t V, Zb, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
-      rk, anorm, part, stage, iters, cycles, resid, flags, end;
+      rk, anorm, part, psi, Tmp2, stage, iters, cycles, resid, flags, end;
 };
 
 struct Group {
@@ -123,6 +123,8 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec) {
   L.rk = take(P * 16);
   L.anorm = take(P * sizeof(double));
   L.part = take(nsys * 3 * NSTRIPE * (MMAX + 1) * sizeof(double2));
+  L.psi = take(C == 2 ? nb * 5 * npts * cs : 0);
+  L.Tmp2 = take(C == 2 ? nsys * C * npts * cs : 0);
   L.stage = take(C * npts * 16);
   L.iters = take(nsys * sizeof(int));
   L.cycles = take(nsys * sizeof(int));
@@ -150,6 +152,10 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   g.rk = (const double2*)(b + L.rk);
   g.anorm = (const double*)(b + L.anorm);
   g.part = (double2*)(b + L.part);
+  g.psi = (C*)(b + L.psi);
+  g.Tmp2 = (C*)(b + L.Tmp2);
+  g.kx0 = (T)(2.0 * M_PI / ((double)G.nx * G.dx));
+  g.ky0 = (T)(2.0 * M_PI / ((double)G.ny * G.dy));
   return g;
 }
 
@@ -197,19 +203,46 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
   return cudaGetLastError();
 }
 
-template <typename T, int NY>
-cudaError_t cols_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
-                   int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
-                   Buf<typename Cx<T>::t> spec) {
+template <typename T, int NY, bool DY>
+cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
+                    int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
+                    Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
   using C = typename Cx<T>::t;
-  constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
-  const size_t sm = smem_elems<NY, NV, true>() * sizeof(C);
-  auto k = k_cols<T, NY, NV, NT>;
+  constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>() * (DY ? 2 : 1) > 256 ? 256 : cols_nt<T, NY>() * (DY ? 2 : 1);
+  const size_t sm = smem_elems<NY, DY ? 2 * NV : NV, true>() * sizeof(C);
+  auto k = k_cols<T, NY, NV, NT, DY>;
   static bool attr = false;
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.nx / NV, units * g.ncomp);
-  k<<<grid, NT, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, spec);
+  k<<<grid, NT, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, spec, dy);
+  return cudaGetLastError();
+}
+template <typename T, int NY>
+cudaError_t cols_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
+                   int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
+                   Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
+  if (dy.base) return cols_nd<T, NY, true>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy);
+  return cols_nd<T, NY, false>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy);
+}
+
+template <int N> constexpr int vrows_nr() { return rows_nr<N>() / 2; }
+constexpr int pow2_floor(int x) { int p = 1; while (p * 2 <= x) p *= 2; return p; }
+template <int N> constexpr int vrows_nt() { return clamp_nt(pow2_floor(6 * vrows_nr<N>() * N / 16)); }
+template <typename T, int N>
+cudaError_t rows_inv_vec_n(const GV<T>& g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
+                           Buf<typename Cx<T>::t> out, int mask, int skip, int mode, int jj, int units,
+                           cudaStream_t st) {
+  using C = typename Cx<T>::t;
+  constexpr int NR = vrows_nr<N>(), NT = vrows_nt<N>();
+  static_assert((NR * N) % NT == 0, "vector epilogue needs a whole number of points per thread");
+  const size_t sm = smem_elems<N, 6 * NR, false>() * sizeof(C);
+  auto k = k_rows_inv_vec<T, N, NR, NT>;
+  static bool attr = false;
+  cudaError_t e = set_smem_once(k, sm, attr);
+  if (e != cudaSuccess) return e;
+  dim3 grid(g.ny / NR, units);
+  k<<<grid, NT, sm, st>>>(g, A, B, out, mask, skip, mode, jj);
   return cudaGetLastError();
 }
 
@@ -244,14 +277,24 @@ cudaError_t rows_inv(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx
 template <typename T>
 cudaError_t cols(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd, int mul,
                  int inv, int skip, int pole, T scale, int units, cudaStream_t st,
-                 Buf<typename Cx<T>::t> spec = Buf<typename Cx<T>::t>{nullptr, 0, 1}) {
-#define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec)
+                 Buf<typename Cx<T>::t> spec = Buf<typename Cx<T>::t>{nullptr, 0, 1},
+                 Buf<typename Cx<T>::t> dy = Buf<typename Cx<T>::t>{nullptr, 0, 1}) {
+#define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy)
   PROP_SIZE_SWITCH(g.ny, CALL)
 #undef CALL
 }
+template <typename T>
+cudaError_t rows_inv_vec(const GV<T>& g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
+                         Buf<typename Cx<T>::t> out, int mask, int skip, int mode, int jj, int units,
+                         cudaStream_t st) {
+#define CALL(N) rows_inv_vec_n<T, N>(g, A, B, out, mask, skip, mode, jj, units, st)
+  PROP_SIZE_SWITCH(g.nx, CALL)
+#undef CALL
+}
 
-EpiArgs epi(int mode, int jj = 0, const double2* in64 = nullptr, double2* out64 = nullptr) {
-  EpiArgs e; e.mode = mode; e.jj = jj; e.in64 = in64; e.out64 = out64; return e;
+EpiArgs epi(int mode, int jj = 0, const double2* in64 = nullptr, double2* out64 = nullptr,
+            const void* aux = nullptr, int kxsel = 0) {
+  EpiArgs e; e.mode = mode; e.jj = jj; e.in64 = in64; e.out64 = out64; e.aux = aux; e.kxsel = kxsel; return e;
 }
 
 int vec_blocks(long L) { return (int)std::max<long>(1, std::min<long>(2048, (L + NT_VEC * 4 - 1) / (NT_VEC * 4))); }
@@ -465,10 +508,18 @@ template <typename T> int step_group(prop* h, Group& G) {
     k_step_reset<<<tg, tb, 0, st>>>(g.st, nsys); }
   const int sys_inh = n_inh * P;
   // correction right-hand sides: R0_k = -delta * IFFT2[w_hat/(zeta - p_k)]
-  { Prof p_(h, K_COLS, 2 * cs * pts * sys_inh * Cn);
-    CK(cols<T>(g, buf(g.What, F, P), buf(g.Tmp, F), -1, 0, MUL_POLE_INV, 1, 1, -1, scale, nsys, st)); }
-  { Prof p_(h, K_ROWS_INV, 3 * cs * pts * sys_inh * Cn);
-    CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), -1, 1, epi(EPI_R0), nsys, st)); }
+  if (Cn == 2) {   // vector: R0 = -(Z - Z_fs) z_k with the psi and cross-polarisation terms
+    { Prof p_(h, K_COLS, 3 * cs * pts * sys_inh * Cn);
+      CK(cols<T>(g, buf(g.What, F, P), buf(g.Tmp, F), -1, 0, MUL_POLE_INV, 1, 1, -1, scale, nsys, st,
+                 Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+    { Prof p_(h, K_ROWS_INV, 11 * cs * pts * sys_inh);
+      CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), -1, 1, VEPI_R0, 0, nsys, st)); }
+  } else {
+    { Prof p_(h, K_COLS, 2 * cs * pts * sys_inh * Cn);
+      CK(cols<T>(g, buf(g.What, F, P), buf(g.Tmp, F), -1, 0, MUL_POLE_INV, 1, 1, -1, scale, nsys, st)); }
+    { Prof p_(h, K_ROWS_INV, 3 * cs * pts * sys_inh * Cn);
+      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), -1, 1, epi(EPI_R0), nsys, st)); }
+  }
   { Prof p_(h, K_CONTROL, 0);
     k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw);
     k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
@@ -491,10 +542,19 @@ template <typename T> int step_group(prop* h, Group& G) {
       const long vs = (long)(m + 1) * F;
       { Prof p_(h, K_ROWS_FWD, 2 * cs * act);
         CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st)); }
-      { Prof p_(h, K_COLS, 2 * cs * act);
-        CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
-      { Prof p_(h, K_ROWS_INV, (5 + jj) * cs * act);     // epilogue + first projections (v_j read once)
-        CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
+      if (Cn == 2) {
+        { Prof p_(h, K_COLS, 3 * cs * act);
+          CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st,
+                     Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+        { Prof p_(h, K_ROWS_INV, (6 + 2.5 + jj) * cs * act);   // A, B, v_j, 5/2 coefficient planes, z, w, projections
+          CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, nsys,
+                             st)); }
+      } else {
+        { Prof p_(h, K_COLS, 2 * cs * act);
+          CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
+        { Prof p_(h, K_ROWS_INV, (5 + jj) * cs * act);     // epilogue + first projections (v_j read once)
+          CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
+      }
       { Prof p_(h, K_CGS, (2.0 * (jj + 1) + 2) * cs * act);
         k_cgs<T, NT_VEC, EPT_CGS><<<dim3(cgs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CONTROL, 0);
@@ -516,6 +576,16 @@ template <typename T> int step_group(prop* h, Group& G) {
     const double endp = (double)c3[1] * Cn * pts;
     { Prof p_(h, K_UPDATE_E, (32 + m * cs) * endp);   // upper bound on the z_j read: J <= m
       k_update_e<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    if (Cn == 2) {   // (Z - Z_fs) e into v_0, from a derivative round trip of e
+      { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
+        CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
+      { Prof p_(h, K_COLS, 3 * cs * endp);
+        CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
+                   Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+      { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
+        CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 1) * F), ST_CYCLE_END, 0,
+                           VEPI_OPDIFF, 0, nsys, st)); }
+    }
     { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
       CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
     { Prof p_(h, K_COLS, 2 * cs * endp);
@@ -544,9 +614,42 @@ template <typename T> int step_group(prop* h, Group& G) {
   return PROP_OK;
 }
 
+// Spectral derivatives of psi = Log n^2 for the vector operator (Eq. Z_bar_eq),
+// scaled by (k0 n0)^-2, into the beam's coefficient planes; the beam's Btmp holds
+// psi in plane 0 (written by k_medium) and What serves as scratch.
+template <typename T> int psi_derivatives(prop* h, Group& G, int slot) {
+  using C = typename Cx<T>::t;
+  GV<T> g = view<T>(h, G);
+  g.ncomp = 1;   // single planes
+  cudaStream_t st = h->stream;
+  const long npts = g.npts;
+  C* psi = g.Btmp + (long)slot * 2 * npts;
+  C* rowft = psi + npts;
+  C* colout = g.What + (long)slot * 2 * npts;
+  C* planes = g.psi + (long)slot * 5 * npts;
+  const double k0n0 = h->k0 * h->n0;
+  const T sc = (T)(1.0 / ((double)npts * k0n0 * k0n0));
+  { Prof p_(h, K_MEDIUM, 2.0 * sizeof(C) * npts);
+    CK(rows_fwd<T, C>(g, buf(psi, npts), buf(rowft, npts), -1, nullptr, 1, st)); }
+  // plane: 0 psi_xx, 1 psi_yy, 2 psi_xy, 3 psi_x, 4 psi_y  -> (column factor, row factor)
+  const int colmul[5] = {MUL_SCALE, MUL_DYY, MUL_DY, MUL_SCALE, MUL_DY};
+  const int rowmul[5] = {2, 0, 1, 1, 0};
+  for (int d = 0; d < 5; ++d) {
+    { Prof p_(h, K_MEDIUM, 2.0 * sizeof(C) * npts);
+      CK(cols<T>(g, buf(rowft, npts), buf(colout, npts), -1, 1, colmul[d], 1, 0, -1, sc, 1, st)); }
+    { Prof p_(h, K_MEDIUM, 2.0 * sizeof(C) * npts);
+      CK(rows_inv<T>(g, buf(colout, npts), buf(planes + (long)d * npts, npts), -1, 0,
+                     epi(EPI_STORE, 0, nullptr, nullptr, nullptr, rowmul[d]), 1, st)); }
+  }
+  { Prof p_(h, K_MEDIUM, 6.0 * sizeof(C) * npts);
+    k_psi_combine<T, 256><<<(int)std::min<long>(1024, (npts + 255) / 256), 256, 0, st>>>(view<T>(h, G), slot); }
+  CK(cudaGetLastError());
+  return PROP_OK;
+}
+
 int validate_opts(const prop_opts* o) {
   if (!o) return PROP_E_ARG;
-  if (o->ncomp != 1) return PROP_E_UNSUPPORTED;
+  if (o->ncomp != 1 && o->ncomp != 2) return PROP_E_UNSUPPORTED;
   if (o->precision != PROP_FP32 && o->precision != PROP_FP64) return PROP_E_ARG;
   if (o->restart < 1 || o->restart > MMAX) return PROP_E_ARG;
   if (o->max_restarts < 1) return PROP_E_ARG;
@@ -669,10 +772,21 @@ int prop_set_medium(prop* h, int32_t beam, const void* n2) {
   const double n0sq = h->n0 * h->n0;
   {
     Prof p_(h, K_MEDIUM, (16.0 + 2 * elem_size(h->prec)) * G.npts);
-    if (h->prec == PROP_FP64) k_medium<double, 256><<<blocks, 256, 0, h->stream>>>(view<double>(h, G), slot, (const double2*)stage, n0sq);
-    else k_medium<float, 256><<<blocks, 256, 0, h->stream>>>(view<float>(h, G), slot, (const double2*)stage, n0sq);
+    if (h->prec == PROP_FP64) {
+      GV<double> g = view<double>(h, G);
+      k_medium<double, 256><<<blocks, 256, 0, h->stream>>>(g, slot, (const double2*)stage, n0sq,
+                                                           h->C == 2 ? g.Btmp + (long)slot * 2 * G.npts : nullptr);
+    } else {
+      GV<float> g = view<float>(h, G);
+      k_medium<float, 256><<<blocks, 256, 0, h->stream>>>(g, slot, (const double2*)stage, n0sq,
+                                                          h->C == 2 ? g.Btmp + (long)slot * 2 * G.npts : nullptr);
+    }
   }
   CK(cudaGetLastError());
+  if (h->C == 2) {
+    const int rc = h->prec == PROP_FP64 ? psi_derivatives<double>(h, G, slot) : psi_derivatives<float>(h, G, slot);
+    if (rc) return rc;
+  }
   G.medium_dirty = true;
   return PROP_OK;
 }
@@ -908,11 +1022,22 @@ template <typename T> static int apply_impl(prop* h, int beam, int pole, const v
   C* scratch = g.Btmp + (long)slot * F;
   const T scale = (T)(1.0 / (double)g.npts);
   cudaStream_t st = h->stream;
+  C* diff = nullptr;
+  if (op && h->C == 2) {   // (Z - Z_fs) v from a derivative round trip, kept for the final epilogue
+    g.psi += (long)slot * 5 * g.npts;
+    C* bscr = g.What + (long)slot * F;
+    diff = g.Tmp + (long)slot * h->P * F;
+    CK(rows_fwd<T, double2>(g, buf((double2*)v, F), buf(scratch, F), -1, nullptr, 1, st));
+    CK(cols<T>(g, buf(scratch, F), buf(scratch, F), -1, 1, MUL_SCALE, 1, 0, -1, scale, 1, st, Buf<C>{nullptr, 0, 1},
+               buf(bscr, F)));
+    CK(rows_inv_vec<T>(g, buf(scratch, F), buf(bscr, F), buf(diff, F), -1, 0, VEPI_OPDIFF, 0, 1, st));
+  }
   CK(rows_fwd<T, double2>(g, buf((double2*)v, F), buf(scratch, F), -1, nullptr, 1, st));
   CK(cols<T>(g, buf(scratch, F), buf(scratch, F), -1, 1, op ? MUL_POLE_FWD : MUL_POLE_INV, 1, 0,
              op ? h->P : pole, scale, 1, st));
   CK(rows_inv<T>(g, buf(scratch, F), buf(scratch, F), -1, 0,
-                 op ? epi(EPI_OPERATOR, 0, (const double2*)v, (double2*)out) : epi(EPI_STORE64, 0, nullptr, (double2*)out),
+                 op ? epi(EPI_OPERATOR, 0, (const double2*)v, (double2*)out, diff)
+                    : epi(EPI_STORE64, 0, nullptr, (double2*)out),
                  1, st));
   return PROP_OK;
 }

@@ -139,3 +139,48 @@ def test_batched_scalar_solutions_satisfy_the_shifted_systems(P, n):
     assert worst < 1e-4, worst          # FP32 solves: residual well below the field
     assert rel_l2(got, out) < 1e-6      # the GPU's residue sum and free-space part
     assert pr.iterations().min() >= 1
+
+
+def test_small_vector_fp64(P):
+    """Two-component (w1, w2) propagation with psi and cross-polarisation terms, FP64, 16^2."""
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.small_vector(16)
+    pr = gpu_propagator(W, "plain_scalar_64", P.PROP_FP64, tol=1e-12)
+    got = gpu_run(pr, W, 2)[0]
+    ref = oracle_run(W, oracle_table("plain_scalar_64"), 2)
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("n,steps,prec", [(64, 3, "fp32"), (128, 1, "fp64")])
+def test_vector_random_reduced(P, n, steps, prec):
+    """Gaussian random medium (l = lambda, seed 7) with border, x-polarised beam, 14 poles."""
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.vector_random_512(steps, n=n)
+    pr = gpu_propagator(W, "vector_random_512", P.PROP_FP32 if prec == "fp32" else P.PROP_FP64,
+                        **({} if prec == "fp32" else {"tol": 1e-12}))
+    got = gpu_run(pr, W, steps)[0]
+    ref = oracle_run(W, oracle_table("vector_random_512"), steps)
+    assert rel_l2(got, ref) < (FP32_TOL if prec == "fp32" else FP64_TOL)
+    assert np.linalg.norm(got[1]) > 0        # cross-polarisation has coupled energy into w2
+
+
+def test_vector_random_full_size_solutions(P):
+    """512^2 vector step: every pole's x_k = (Z_fs - p_k)^-1 w + e_k satisfies
+    (Z - p_k) x_k = w under the oracle's operator, and the GPU field is
+    r0 w + sum r_k x_k."""
+    from oracle import operators as ops
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.vector_random_512(1)
+    T = oracle_table("vector_random_512")
+    pr = gpu_propagator(W, "vector_random_512", P.PROP_FP32)
+    b = W.beams[0]
+    got = gpu_run(pr, W, 1)[0]
+    med = ops.Medium(b.medium(0), b.grid.dx, b.grid.dy, W.k0, W.n0, 2)
+    out = T.r0 * b.w0
+    worst = 0.0
+    for k, (p, r) in enumerate(zip(T.poles, T.residues)):
+        x = med.freespace_solve(b.w0, p) + pr.get_correction(0, k)
+        worst = max(worst, np.linalg.norm(b.w0 - med.apply_shifted(x, p)) / np.linalg.norm(b.w0))
+        out = out + r * x
+    assert worst < 1e-4, worst
+    assert rel_l2(got, out) < 1e-6
