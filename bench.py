@@ -130,7 +130,7 @@ import numpy as np
 from oracle import aaa_lawson as al, propagator as pr, operators as ops
 from paper_2410_17446_gb300 import workloads as wl
 import bench
-W = bench.make_workload({name!r}, 10**6)
+W = bench.make_workload({name!r}, 64)
 T = al.PoleTable.from_json(bench.load_table({name!r}))
 budget = {budget}
 t0 = time.perf_counter(); steps = 0; pts = 0

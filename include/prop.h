@@ -70,8 +70,10 @@ typedef struct prop_opts {
   int32_t ncomp;           /* 1: scalar (psi terms dropped, Sec. 2); 2: (w1, w2)  */
   int32_t precision;       /* enum prop_precision                                 */
   int32_t restart;         /* GMRES restart length m, 1..64 (default 20)          */
-  int32_t max_restarts;    /* cycles per solve before PROP_E_NOCONV (default 50)  */
-  double tol;              /* stop when ||w - (Z - p_k) x_k|| <= tol ||w||         */
+  int32_t max_restarts;    /* cycles per solve before PROP_E_NOCONV (default 50 FP64, 200 FP32) */
+  double tol;              /* FP64: stop when ||w - (Z - p_k) x_k|| <= tol ||w||.  FP32: when it is
+                              <= tol mu_k (||w|| + ||Z - p_k|| ||x_k||), the normwise backward error,
+                              with mu_k >= 1 equalising each pole's share of the field error */
 } prop_opts;
 
 typedef struct prop_stats {

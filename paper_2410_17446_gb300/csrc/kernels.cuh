@@ -64,7 +64,8 @@ template <typename T> struct GV {
   double* bnorm2;       // [nb] ||w||^2 of the step's right-hand side
   int* nonhomog;        // [nb] 1 if delta != 0 somewhere
   const double2* rk;    // [P] residues r_k
-  const double* anorm;  // [P] bound on ||Z - p_k I|| over this grid (backward-error test)
+  const double* anorm;  // [2P]: bound on ||Z - p_k I|| over this grid (backward-error test), then the
+                        //       per-pole tolerance factor mu_k >= 1 (error equidistribution)
   double2* part;        // [nsys][3][NSTRIPE][MMAX+1] striped accumulators: dots1, dots2, ||w'||^2
   // vector operator (ncomp = 2) only
   C* psi;        // [nb][5][npts]  coefficients of Z - Z_fs: D1 = delta + psit_xx, D2 = delta + psit_yy,
@@ -823,9 +824,14 @@ __global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2*
 // backward = 1 the normwise backward-error bound tol (||w|| + ||A|| ||x_k||),
 // x_k = z_k + e_k, for arithmetic whose transforms cannot resolve residuals
 // below eps ||A|| ||x||.
-__device__ __forceinline__ double conv_threshold(const SysState& q, double tol, double wn, double anorm, int backward) {
+//
+// Pole k's residual reaches the step output through r_k (Z - p_k)^-1, whose size
+// is about |r_k| / dist(p_k, spectrum); mu_k = max_j(that) / (that)_k gives each
+// pole the same bound on its share of the field error (FP32 path only).
+__device__ __forceinline__ double conv_threshold(const SysState& q, double tol, double wn, const double* anorm,
+                                                 int k, int P, int backward) {
   if (!backward) return tol * wn;
-  return tol * (wn + anorm * (sqrt(q.z0norm2) + sqrt(q.enorm2)));
+  return tol * anorm[P + k] * (wn + anorm[k] * (sqrt(q.z0norm2) + sqrt(q.enorm2)));
 }
 
 __global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm2, double tol,
@@ -840,7 +846,7 @@ __global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm
     q.beta = beta;
     q.resid = wn > 0 ? beta / wn : 0.0;
     if (!isfinite(beta)) { q.flags |= 1; q.state = ST_DONE; continue; }
-    if (beta <= conv_threshold(q, tol, wn, anorm[s % P], backward)) { q.state = ST_DONE; continue; }
+    if (beta <= conv_threshold(q, tol, wn, anorm, s % P, P, backward)) { q.state = ST_DONE; continue; }
     if (q.cycles >= max_cycles) { q.flags |= 2; q.state = ST_DONE; continue; }
     q.cycles += 1;
     q.used = 1;
@@ -927,7 +933,7 @@ __global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bn
     const double nb = q.nrm_b;
     q.nrm_b = 0.0;
     if (!isfinite(est) || !isfinite(hn)) { q.flags |= 1; q.state = ST_DONE; continue; }
-    if (est <= conv_threshold(q, tol, wn, anorm[s % P], backward) || jj + 1 == m ||
+    if (est <= conv_threshold(q, tol, wn, anorm, s % P, P, backward) || jj + 1 == m ||
         hn <= breakdown * sqrt(fmax(nb, 0.0)) || hn == 0.0) {
       const int J = jj + 1;
       for (int i = J - 1; i >= 0; --i) {

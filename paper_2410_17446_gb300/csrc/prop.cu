@@ -121,7 +121,7 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec) {
   L.bnorm2 = take(nb * sizeof(double));
   L.nonhomog = take(nb * sizeof(int));
   L.rk = take(P * 16);
-  L.anorm = take(P * sizeof(double));
+  L.anorm = take(2 * P * sizeof(double));
   L.part = take(nsys * 3 * NSTRIPE * (MMAX + 1) * sizeof(double2));
   L.psi = take(C == 2 ? nb * 5 * npts * cs : 0);
   L.Tmp2 = take(C == 2 ? nsys * C * npts * cs : 0);
@@ -373,12 +373,24 @@ template <typename T> int upload_group_tables(prop* h, Group& G) {
       bm[((size_t)j * G.nx + i) * 2 + 1] = (T)r.imag();
     }
   CK(cudaMemcpyAsync(b + G.off.basemul, bm.data(), bm.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
-  // ||Z - p_k I|| <= max over the grid's free-space spectrum of |zeta - p_k| + 0.5 (|delta| <= 0.5)
+  // ||Z - p_k I|| <= max over the grid's free-space spectrum of |zeta - p_k| + 0.5 (|delta| <= 0.5),
+  // and the per-pole tolerance factors mu_k (see conv_threshold): the spectrum is taken as the
+  // segment [zeta_min - 0.5, 0.5] of the real axis.
   {
     const double kxm = M_PI / G.dx, kym = M_PI / G.dy;
     const double zmin = -(kxm * kxm + kym * kym) / (k0n0 * k0n0);
-    std::vector<double> an(h->P);
-    for (int k = 0; k < h->P; ++k) an[k] = std::max(std::abs(cplx(zmin, 0.0) - h->poles[k]), std::abs(h->poles[k])) + 0.5;
+    std::vector<double> an(2 * h->P);
+    std::vector<double> ratio(h->P);
+    double rmax = 0.0;
+    for (int k = 0; k < h->P; ++k) {
+      an[k] = std::max(std::abs(cplx(zmin, 0.0) - h->poles[k]), std::abs(h->poles[k])) + 0.5;
+      const double re = h->poles[k].real(), im = h->poles[k].imag();
+      const double dxs = std::max(0.0, std::max((zmin - 0.5) - re, re - 0.5));
+      const double dist = std::max(std::hypot(dxs, im), 1e-12);
+      ratio[k] = std::abs(h->res[k]) / dist;
+      rmax = std::max(rmax, ratio[k]);
+    }
+    for (int k = 0; k < h->P; ++k) an[h->P + k] = ratio[k] > 0 ? std::min(100.0, std::max(1.0, rmax / ratio[k])) : 100.0;
     CK(cudaMemcpyAsync(b + G.off.anorm, an.data(), an.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   }
@@ -703,7 +715,7 @@ int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision) {
   o->ncomp = ncomp;
   o->precision = precision;
   o->restart = 20;
-  o->max_restarts = 50;
+  o->max_restarts = precision == PROP_FP64 ? 50 : 200;
   o->tol = precision == PROP_FP64 ? 1e-12 : 1e-7;
   return PROP_OK;
 }

@@ -150,7 +150,7 @@ class Propagator:
     """Owns one handle and its torch-allocated workspace."""
 
     def __init__(self, grids, k0: float, n0: float, dz: float, poles, residues, r0,
-                 ncomp: int = 1, precision: int = PROP_FP32, restart: int = 20, max_restarts: int = 50,
+                 ncomp: int = 1, precision: int = PROP_FP32, restart: int = 20, max_restarts: Optional[int] = None,
                  tol: Optional[float] = None, device: str = "cuda", stream=None):
         import torch
         self.torch = torch
@@ -160,7 +160,8 @@ class Propagator:
         self.ncomp = ncomp
         self.opts = prop_default_opts(ncomp, precision)
         self.opts.restart = restart
-        self.opts.max_restarts = max_restarts
+        if max_restarts is not None:
+            self.opts.max_restarts = max_restarts
         if tol is not None:
             self.opts.tol = tol
         poles = np.asarray(poles, np.complex128)

@@ -184,3 +184,22 @@ def test_vector_random_full_size_solutions(P):
         out = out + r * x
     assert worst < 1e-4, worst
     assert rel_l2(got, out) < 1e-6
+
+
+def test_hard_scattering_beam_fp32_six_steps(P):
+    """The hardest beam of the uneven batch (eps = 0.083, period 1.498 lambda:
+    first-order scattering lands next to the evanescent boundary, where the poles
+    crowd) at 128^2, six FP32 steps against the FP64 oracle."""
+    from paper_2410_17446_gb300 import workloads as wl
+    g = wl.Grid(128, 128, 0.25, 0.25)
+    dz = 0.5
+
+    def med(s):
+        return wl.sine_product_n2(g, 0.0831792411594809, 1.4983412918408128, (s + 0.5) * dz, 8, 0.2)
+
+    beam = wl.Beam(g, wl.gaussian_beam(g, 2.827372867618358)[None], med, lambda s: True, 8, 0.2)
+    W = wl.Workload("hard_beam_128", wl.K0, 1.0, dz, 6, 12, 1, "fp32", 20, 1e-7, [beam])
+    pr = gpu_propagator(W, "uneven_batch", P.PROP_FP32)
+    got = gpu_run(pr, W, 6)[0]
+    ref = oracle_run(W, oracle_table("uneven_batch"), 6)
+    assert rel_l2(got, ref) < FP32_TOL
