@@ -237,49 +237,79 @@ def ours(args) -> None:
                 media[(s, i)] = torch.tensor(b.medium(s), dtype=torch.complex128, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def one_step(s):
-        for i in range(len(W.beams)):
-            m = media.get((s, i))
-            if m is not None:
-                pr.set_medium(i, m)
-        pr.step()
+    def timed(prx, clocks_on=True):
+        """W warm-up steps, then K steps each timed by events on the library stream."""
+        def step_of(s):
+            for i in range(len(W.beams)):
+                m = media.get((s, i))
+                if m is not None:
+                    prx.set_medium(i, m)
+            prx.step()
+        with torch.cuda.stream(stream):
+            for s in range(args.warmup):
+                step_of(s)
+            torch.cuda.synchronize(dev)
+            l0 = prx.stats().kernel_launches
+            prx.set_profiling(True)
+            st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            clocks = ClockSampler(local) if clocks_on else None
+            if ws > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize(dev)
+            if clocks:
+                clocks.start()
+                time.sleep(0.3)
+            t0 = time.perf_counter()
+            its_total = 0
+            for k in range(args.steps):
+                flush.zero_()
+                # keep the GPU busy while the host enqueues the step, so that the
+                # timed interval holds device work, not host launch latency
+                torch.cuda._sleep(GATE_CYCLES)
+                st_ev[k].record(stream)
+                step_of(args.warmup + k)
+                en_ev[k].record(stream)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            clk = None
+            if clocks:
+                time.sleep(0.3)
+                clk = clocks.stop(t0, t1)
+            if ws > 1:
+                torch.distributed.barrier()
+            dms = sum(a.elapsed_time(b) for a, b in zip(st_ev, en_ev))
+            prof = prx.profile()
+            prx.set_profiling(False)
+            stx = prx.stats()
+            return {"dev_ms": dms, "wall": t1 - t0, "clk": clk, "prof": prof,
+                    "launches": stx.kernel_launches - l0, "st": stx, "iters": prx.iterations()}
 
-    with torch.cuda.stream(stream):
-        for s in range(args.warmup):
-            one_step(s)
-        torch.cuda.synchronize(dev)
-        launches0 = pr.stats().kernel_launches
-        pr.set_profiling(True)
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        clocks = ClockSampler(local)
+    res = timed(pr)
+    dev_ms, wall, clk, prof = res["dev_ms"], res["wall"], res["clk"], res["prof"]
+    launches, st, iters = res["launches"], res["st"], res["iters"]
+
+    learned = None
+    if args.guess == "both":
+        from paper_2410_17446_gb300 import guess_train as GT
+        fam = "vector" if W.ncomp == 2 else "scalar"
+        net = GT.load(os.path.join(ROOT, "paper_2410_17446_gb300", "nets", f"guess_{fam}.npz"))
+        with torch.cuda.stream(stream):
+            prl = P.Propagator.from_table(grids, W.k0, W.n0, W.dz, tab, ncomp=W.ncomp, precision=P.PROP_FP32,
+                                          restart=W.restart, stream=stream, guess=P.PROP_GUESS_LEARNED)
+            prl.set_guess_net(net["channels"], net["weights"], net["biases"])
+            for i, b in enumerate(W.beams):
+                prl.set_field(i, np.ascontiguousarray(b.w0))
+        rl = timed(prl, clocks_on=False)
+        ml = rl["dev_ms"]
         if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize(dev)
-        clocks.start()
-        time.sleep(0.3)
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            # keep the GPU busy while the host enqueues the step, so that the
-            # timed interval holds device work, not host launch latency
-            torch.cuda._sleep(GATE_CYCLES)
-            starts[k].record(stream)
-            one_step(args.warmup + k)
-            ends[k].record(stream)
-        torch.cuda.synchronize(dev)
-        t1 = time.perf_counter()
-        wall = t1 - t0
-        time.sleep(0.3)
-        clk = clocks.stop(t0, t1)
-        if ws > 1:
-            torch.distributed.barrier()
-        dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-        prof = pr.profile()
-        pr.set_profiling(False)
-        launches = pr.stats().kernel_launches - launches0
-        st = pr.stats()
-        iters = pr.iterations()
+            t = torch.tensor([ml], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ml = float(t.item())
+        learned = {"value": ws * W.points * args.steps / (ml / 1e3) / 1e6, "ms_per_step": ml / args.steps,
+                   "arnoldi_steps_total": int(rl["st"].total_iters), "net": net["meta"],
+                   "guess_net_ms": round(rl["prof"]["guess_net"]["total_ms"], 3)}
+        prl.close()
 
     ms = dev_ms
     if ws > 1:
@@ -381,6 +411,8 @@ def ours(args) -> None:
                                 "GBps": (v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9) if v["total_ms"] > 0 else None}
                             for k, v in prof.items() if v["launches"]},
                 "rel_err_vs_closed_form": acc,
+                "learned_guess": learned,
+                "plain_arnoldi_steps_total": int(st.total_iters),
                 "rel_err_steps": CONFIG_STEPS[args.workload] if acc is not None else None, "e2e": e2e}
         if cpu is not None:
             line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
@@ -403,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=0, help="shrink the grid (profiling runs only; not a bench line)")
+    ap.add_argument("--guess", default="plain", choices=["plain", "both"],
+                    help="both: also time the learned initial guess (GMRES to the same tolerance)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {"homogeneous_aperture_1024": 20000, "plain_scalar_64": 2000}.get(args.workload, 100)

@@ -74,7 +74,12 @@ typedef struct prop_opts {
   double tol;              /* FP64: stop when ||w - (Z - p_k) x_k|| <= tol ||w||.  FP32: when it is
                               <= tol mu_k (||w|| + ||Z - p_k|| ||x_k||), the normwise backward error,
                               with mu_k >= 1 equalising each pole's share of the field error */
+  int32_t guess;           /* PROP_GUESS_ZERO (x0 = 0) or PROP_GUESS_LEARNED (x0 from the network
+                              installed by prop_set_guess_net; reserves activation memory)      */
 } prop_opts;
+
+enum prop_guess { PROP_GUESS_ZERO = 0, PROP_GUESS_LEARNED = 1 };
+#define PROP_GUESS_CHANNELS 16   /* padded input / output width of the guess network */
 
 typedef struct prop_stats {
   int64_t steps;           /* steps completed since prop_create / prop_set_field  */
@@ -97,7 +102,7 @@ typedef struct prop_kernel_profile {
   double alg_bytes;
 } prop_kernel_profile;
 
-#define PROP_NKINDS 12
+#define PROP_NKINDS 13
 
 typedef struct prop prop; /* opaque handle */
 
@@ -168,6 +173,23 @@ void prop_destroy(prop* h);
 int prop_fft2_workspace_size(int32_t nx, int32_t ny, int32_t precision, size_t* bytes);
 int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse,
               void* d_data, void* d_work, size_t work_bytes, void* stream);
+
+/* Install the initial-guess network (include/prop_cnn.h) for PROP_GUESS_LEARNED.
+ * The paper has no learned part: GMRES still runs to the same tolerance, the
+ * network only sets x0 of each correction system (Z - p_k) e_k = R0_k.
+ * channels[nlayers + 1]: widths 16 or 32, first and last 16
+ * (PROP_GUESS_CHANNELS).  weights: bfloat16 bits, layers concatenated, each
+ * [9][c_out][c_in]; biases: float32, concatenated.  Host or device memory.
+ * Input channels per pixel: R0_k / rms(R0_k) (re, im per component), then
+ * 10 delta (re, im), then Re p_k, Im p_k, zero padding; output channels:
+ * e_k / rms(R0_k) (re, im per component), rest ignored.  At most 8 layers. */
+int prop_set_guess_net(prop* h, int32_t nlayers, const int32_t* channels, const uint16_t* weights_bf16,
+                       const float* biases);
+
+/* Training pair of the last step for (beam, pole): the network input above
+ * (bfloat16 [ny][nx][16]) and the target e_k / rms(R0_k) (float32 [ny][nx][16],
+ * padding zero).  Device pointers. */
+int prop_get_net_io(prop* h, int32_t beam, int32_t pole, void* d_in_bf16, float* d_target);
 
 /* prop_fft2 for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant.  Some callers cannot call

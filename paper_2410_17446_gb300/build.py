@@ -11,9 +11,9 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRC = [os.path.join(PKG, "csrc", "prop.cu")]
+SRC = [os.path.join(PKG, "csrc", "prop.cu"), os.path.join(PKG, "csrc", "cnn.cu")]
 DEPS = SRC + [os.path.join(PKG, "csrc", f) for f in ("fft.cuh", "kernels.cuh")] + [
-    os.path.join(ROOT, "include", "prop.h")]
+    os.path.join(ROOT, "include", h) for h in ("prop.h", "prop_cnn.h")]
 LIB = os.path.join(PKG, "libprop.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,17 +33,32 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile each translation unit in parallel, then link libprop.so."""
     if not force and not needs_build():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
+    objs = [os.path.join(PKG, "_obj_" + os.path.basename(s) + ".o") for s in SRC]
+    flags = ["-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC"]
+
+    def compile_one(pair):
+        src, obj = pair
+        cmd = [nvcc(), *flags, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    with ThreadPoolExecutor(len(SRC)) as ex:
+        results = list(ex.map(compile_one, zip(SRC, objs)))
+    for r in results:
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed ({r.returncode}):\n{r.stdout}\n{r.stderr}")
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp, *SRC]
-    if verbose:
-        print(" ".join(cmd), flush=True)
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed ({r.returncode}):\n{r.stdout}\n{r.stderr}")
+        raise RuntimeError(f"nvcc link failed ({r.returncode}):\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    for o in objs:
+        os.remove(o)
     return LIB
 
 

@@ -15,6 +15,7 @@
 // so the free-space solve (Z_fs - p I)^-1 of Sec. 4.2 -- diagonal in Fourier
 // space on the periodic grid -- and the operator Z of Eq. (Z_bar_eq) share them.
 #pragma once
+#include <cuda_bf16.h>
 #include "fft.cuh"
 
 namespace prop_dev {
@@ -28,8 +29,9 @@ enum SysStateCode { ST_DONE = 0, ST_ITER = 1, ST_CYCLE_END = 2 };
 struct SysState {
   int state, j, jend, iters, cycles, flags;   // flags: 1 = NaN seen, 2 = hit max cycles
   int used, pad_i;                            // used: iterated this step (E is meaningful)
-  double beta, resid, scale, nrm_a, nrm_b, pad;
+  double beta, resid, scale, nrm_a, nrm_b, beta0;  // beta0: ||R0|| at the step start
   double z0norm2, enorm2;                     // ||z_k||^2 (free-space solve), ||e_k||^2
+  double2 r0r;                                // <R0, r> of the last true-residual pass
   double2 g[MMAX + 1];
   double2 sn[MMAX];
   double cs[MMAX];
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     flush_partials(red2, NT / 32, ep.jj, part_at(g.part, u, 0, 0, 0));
     return;
   }
-  double acc = 0.0, acc2 = 0.0;
+  double acc = 0.0, acc2 = 0.0, accr = 0.0, acci = 0.0;
   for (int e = threadIdx.x; e < NR * N; e += NT) {
     const C val = s[sidx<N, NR, false>(e / N, e % N)];
     switch (ep.mode) {
@@ -426,6 +428,8 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
         }
         g.V[vb] = to_c(r, T());
         acc += r.x * r.x + r.y * r.y;
+        accr += r0.x * r.x + r0.y * r.y;      // <R0, r> = sum conj(R0) r
+        acci += r0.x * r.y - r0.y * r.x;
       } break;
     }
   }
@@ -436,6 +440,11 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   if (ep.mode == EPI_R0) {
     const double t = block_sum(acc2, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t);
+  }
+  if (ep.mode == EPI_TRUERES) {
+    const double tr = block_sum(accr, red);
+    const double ti = block_sum(acci, red);
+    if (threadIdx.x == 0) { atomicAdd(&g.st[u].r0r.x, tr); atomicAdd(&g.st[u].r0r.y, ti); }
   }
 }
 
@@ -839,8 +848,9 @@ __global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     SysState& q = st[s];
     if (!first && q.state != from) continue;
-    if (first) { q.iters = 0; q.cycles = 0; q.flags = 0; q.used = 0; q.enorm2 = 0.0; }
+    if (first) { q.iters = 0; q.cycles = 0; q.flags = 0; q.used = 0; q.enorm2 = 0.0; q.r0r = make_double2(0.0, 0.0); }
     const double beta = sqrt(q.nrm_a);
+    if (first) q.beta0 = beta;
     const double wn = sqrt(bnorm2[s / P]);
     q.nrm_a = 0.0;
     q.beta = beta;
@@ -951,6 +961,140 @@ __global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bn
       q.state = ST_CYCLE_END;
     } else {
       q.scale = 1.0 / hn;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Learned initial guess: pack the network input, unpack its output into E.
+// Input channels (bf16, 16 per pixel): R0 / rms (re, im per component),
+// 10 delta (re, im), Re p, Im p, zeros.  rms = ||R0|| / sqrt(ncomp npts).
+// ---------------------------------------------------------------------------
+constexpr int GUESS_CH = 16;
+constexpr double GUESS_ACCEPT = 0.9;   // keep a guess only if it cuts ||R0|| by at least 10%
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_guess_pack(GV<T> g, __nv_bfloat16* in, const double2* poles, int only_iter,
+                                                   int s0) {
+  const int s = s0 + blockIdx.y;
+  const SysState& q = g.st[s];
+  if (only_iter && q.state != ST_ITER) return;
+  const int b = s / g.P, k = s % g.P;
+  const double rms = q.beta0 / sqrt((double)g.ncomp * g.npts);
+  const float inv = rms > 0 ? (float)(1.0 / rms) : 0.f;
+  const double2 p = poles[k];
+  __nv_bfloat16* o = in + (long)blockIdx.y * g.npts * GUESS_CH;
+  const long L = (long)g.ncomp * g.npts;
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < g.npts; i += (long)gridDim.x * NT) {
+    float v[GUESS_CH];
+#pragma unroll
+    for (int c = 0; c < GUESS_CH; ++c) v[c] = 0.f;
+    for (int c = 0; c < g.ncomp; ++c) {
+      const auto r = g.R0[(long)s * L + (long)c * g.npts + i];
+      v[2 * c] = (float)r.x * inv; v[2 * c + 1] = (float)r.y * inv;
+    }
+    const auto d = g.delta[(long)b * g.npts + i];
+    v[2 * g.ncomp] = 10.f * (float)d.x; v[2 * g.ncomp + 1] = 10.f * (float)d.y;
+    v[2 * g.ncomp + 2] = (float)p.x; v[2 * g.ncomp + 3] = (float)p.y;
+#pragma unroll
+    for (int c = 0; c < GUESS_CH; c += 2)
+      *reinterpret_cast<__nv_bfloat162*>(o + i * GUESS_CH + c) = __floats2bfloat162_rn(v[c], v[c + 1]);
+  }
+}
+
+// E = out * rms for systems still iterating; they move to ST_CYCLE_END so that the
+// cycle-end true residual R0 - (Z - p) E starts GMRES from the guess.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_guess_unpack(GV<T> g, const float* out) {
+  __shared__ double red[32];
+  const int s = blockIdx.y;
+  SysState& q = g.st[s];
+  if (q.state != ST_ITER) return;
+  const double rms = q.beta0 / sqrt((double)g.ncomp * g.npts);
+  const float* o = out + (long)s * g.npts * GUESS_CH;
+  const long L = (long)g.ncomp * g.npts;
+  float nr = 0.f;
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < g.npts; i += (long)gridDim.x * NT) {
+    for (int c = 0; c < g.ncomp; ++c) {
+      const float fx = o[i * GUESS_CH + 2 * c], fy = o[i * GUESS_CH + 2 * c + 1];
+      g.E[(long)s * L + (long)c * g.npts + i] = make_double2((double)fx * rms, (double)fy * rms);
+      nr += fx * fx + fy * fy;
+    }
+  }
+  const double t = block_sum((double)nr, red) * rms * rms;
+  if (threadIdx.x == 0) atomicAdd(&q.enorm2, t);
+}
+
+// Minimal-residual scaling of the guess.  With u = A e0 = R0 - r (r the true
+// residual of the guess), alpha = <u, R0>/||u||^2 minimises ||R0 - alpha u||, so
+// the scaled start e0 <- alpha e0, r <- (1 - alpha) R0 + alpha r is never worse
+// than x0 = 0; a guess that does not cut the residual by 10% is dropped (alpha = 0)
+// so that GMRES then runs exactly as without it.  One thread per system computes
+// alpha; the kernel below applies it.
+__global__ void k_guess_alpha(SysState* st, int nsys) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    SysState& q = st[s];
+    if (q.state != ST_CYCLE_END) continue;
+    const double b2 = q.beta0 * q.beta0, r2 = q.nrm_a;
+    const double2 c = q.r0r;                                  // <R0, r>
+    const double2 uR = make_double2(b2 - c.x, c.y);          // <u, R0> = ||R0||^2 - conj(<R0, r>)
+    const double u2 = fmax(b2 - 2.0 * c.x + r2, 0.0);
+    double2 a = make_double2(0.0, 0.0);
+    if (u2 > 0.0) a = make_double2(uR.x / u2, uR.y / u2);
+    double rn2 = fmax(b2 - (uR.x * uR.x + uR.y * uR.y) / (u2 > 0.0 ? u2 : 1.0), 0.0);
+    if (!(rn2 <= GUESS_ACCEPT * GUESS_ACCEPT * b2)) {      // not worth it: start from x0 = 0 exactly
+      a = make_double2(0.0, 0.0);
+      rn2 = b2;
+    }
+    q.coef[0] = a;                                           // alpha, read by k_guess_apply
+    q.nrm_a = rn2;
+    q.enorm2 *= a.x * a.x + a.y * a.y;
+    q.r0r = make_double2(0.0, 0.0);
+  }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_guess_apply(GV<T> g) {
+  using C = typename Cx<T>::t;
+  const int s = blockIdx.y;
+  const SysState& q = g.st[s];
+  if (q.state != ST_CYCLE_END) return;
+  const double2 a = q.coef[0];
+  const long L = (long)g.ncomp * g.npts;
+  C* v = g.V + (long)s * (g.m + 1) * L;
+  const C* r0 = g.R0 + (long)s * L;
+  double2* e = g.E + (long)s * L;
+  const T ax = (T)a.x, ay = (T)a.y, bx = (T)(1.0 - a.x), by = (T)(-a.y);
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
+    const C rr = v[p], R = r0[p];
+    C o;
+    o.x = bx * R.x - by * R.y + ax * rr.x - ay * rr.y;
+    o.y = bx * R.y + by * R.x + ax * rr.y + ay * rr.x;
+    v[p] = o;
+    const double2 ee = e[p];
+    e[p] = make_double2(a.x * ee.x - a.y * ee.y, a.x * ee.y + a.y * ee.x);
+  }
+}
+
+// After the unpack: every system that received a guess becomes a cycle end.
+__global__ void k_guess_mark(SysState* st, int nsys) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x)
+    if (st[s].state == ST_ITER) { st[s].state = ST_CYCLE_END; st[s].jend = 0; }
+}
+
+// Training target: E / rms (float32, 16 channels, padding zero) of one system.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_guess_target(GV<T> g, int s, float* tgt) {
+  const SysState& q = g.st[s];
+  const double rms = q.beta0 / sqrt((double)g.ncomp * g.npts);
+  const double inv = (rms > 0 && q.used) ? 1.0 / rms : 0.0;
+  const long L = (long)g.ncomp * g.npts;
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < g.npts; i += (long)gridDim.x * NT) {
+    for (int c = 0; c < GUESS_CH; ++c) tgt[i * GUESS_CH + c] = 0.f;
+    for (int c = 0; c < g.ncomp; ++c) {
+      const double2 e = g.E[(long)s * L + (long)c * g.npts + i];
+      tgt[i * GUESS_CH + 2 * c] = (float)(e.x * inv);
+      tgt[i * GUESS_CH + 2 * c + 1] = (float)(e.y * inv);
     }
   }
 }

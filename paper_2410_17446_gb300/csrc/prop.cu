@@ -12,6 +12,7 @@
 // written so that rounding errors scale with the increment, not with w; the
 // field itself is accumulated in FP64.
 #include "../../include/prop.h"
+#include "../../include/prop_cnn.h"
 #include "kernels.cuh"
 
 #include <algorithm>
@@ -28,6 +29,9 @@ using cplx = std::complex<double>;
 namespace {
 
 constexpr size_t ALIGN = 256;
+constexpr int NET_MAX_LAYERS = 8;                                   // guess network limits
+constexpr size_t NET_W_BYTES = NET_MAX_LAYERS * 9 * 32 * 32 * 2;
+constexpr size_t NET_B_BYTES = NET_MAX_LAYERS * 32 * 4;
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 bool supported_n(int n) {
@@ -49,7 +53,7 @@ constexpr int EPT_CGS = 8;
 
 struct Layout {
   size_t V, Zb, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
-      rk, anorm, part, psi, Tmp2, stage, iters, cycles, resid, flags, end;
+      rk, anorm, part, psi, Tmp2, poles, act0, act1, netout, stage, iters, cycles, resid, flags, end;
 };
 
 struct Group {
@@ -78,6 +82,9 @@ struct prop {
   char* ws;
   size_t ws_bytes;
   size_t counts_off;
+  size_t net_off;          // guess network: bf16 weights, then float32 biases
+  int guess, net_layers;
+  int net_ch[9];
   int64_t steps, total_iters;
   int last_status;
   // launch accounting and optional per-launch event timing
@@ -95,7 +102,7 @@ namespace {
 size_t elem_size(int prec) { return prec == PROP_FP64 ? sizeof(double) : sizeof(float); }
 
 // Carve one group's buffers starting at `base`; returns the end offset.
-size_t carve(Group& G, size_t base, int P, int C, int m, int prec) {
+size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
   const size_t es = elem_size(prec), cs = 2 * es;
   const size_t nb = G.beams.size(), nsys = nb * P, npts = G.npts;
   Layout& L = G.off;
@@ -125,6 +132,10 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec) {
   L.part = take(nsys * 3 * NSTRIPE * (MMAX + 1) * sizeof(double2));
   L.psi = take(C == 2 ? nb * 5 * npts * cs : 0);
   L.Tmp2 = take(C == 2 ? nsys * C * npts * cs : 0);
+  L.poles = take(P * 16);
+  L.act0 = take(guess ? nsys * npts * 32 * 2 : 0);     // bf16 NHWC activations of the guess network
+  L.act1 = take(guess ? nsys * npts * 32 * 2 : 0);
+  L.netout = take(guess ? nsys * npts * 16 * 4 : 0);   // float32 output
   L.stage = take(C * npts * 16);
   L.iters = take(nsys * sizeof(int));
   L.cycles = take(nsys * sizeof(int));
@@ -394,6 +405,9 @@ template <typename T> int upload_group_tables(prop* h, Group& G) {
     CK(cudaMemcpyAsync(b + G.off.anorm, an.data(), an.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   }
+  std::vector<double> pl(2 * h->P);
+  for (int k = 0; k < h->P; ++k) { pl[2 * k] = h->poles[k].real(); pl[2 * k + 1] = h->poles[k].imag(); }
+  CK(cudaMemcpyAsync(b + G.off.poles, pl.data(), pl.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   std::vector<double> rk(2 * h->P);
   for (int k = 0; k < h->P; ++k) { rk[2 * k] = h->res[k].real(); rk[2 * k + 1] = h->res[k].imag(); }
   CK(cudaMemcpyAsync(b + G.off.rk, rk.data(), rk.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -406,11 +420,11 @@ template <typename T> int upload_group_tables(prop* h, Group& G) {
 // Launch accounting
 // ---------------------------------------------------------------------------
 enum Kind { K_ROWS_FWD, K_COLS, K_ROWS_INV, K_FIELD_IO, K_CGS, K_NORMALIZE, K_UPDATE_E, K_RESIDUE, K_MEDIUM,
-            K_CONTROL, K_INIT, K_SCALE };
+            K_CONTROL, K_INIT, K_SCALE, K_GUESS };
 const char* kind_name(int k) {
   static const char* n[PROP_NKINDS] = {"rows_fwd", "cols", "rows_inv", "field_io", "cgs", "normalize",
                                        "update_e", "residue_sum", "medium", "control", "init_systems",
-                                       "scale_v0"};
+                                       "scale_v0", "guess_net"};
   return n[k];
 }
 
@@ -540,7 +554,64 @@ template <typename T> int step_group(prop* h, Group& G) {
   int rc = read_counts(h, c3);
   if (rc) return rc;
   const bool any_used = c3[0] > 0;
-  if (any_used) {
+  if (any_used && h->guess == PROP_GUESS_LEARNED && h->net_layers > 0) {
+    // x0 from the network: E = net(R0/rms, delta, p) * rms, then the true residual R0 - (Z - p) E
+    // (the cycle-end pass) starts GMRES from it.
+    const int blocks = (int)std::min<long>(1024, (g.npts + 255) / 256);
+    __nv_bfloat16* a0 = (__nv_bfloat16*)(h->ws + G.off.act0);
+    __nv_bfloat16* a1 = (__nv_bfloat16*)(h->ws + G.off.act1);
+    float* nout = (float*)(h->ws + G.off.netout);
+    { Prof p_(h, K_GUESS, (Cn * cs + cs + 32.0) * pts * c3[0]);
+      k_guess_pack<T, 256><<<dim3(blocks, nsys), 256, 0, st>>>(g, a0, (const double2*)(h->ws + G.off.poles), 1, 0); }
+    const char* wbase = h->ws + h->net_off;
+    const float* bbase = (const float*)(h->ws + h->net_off + NET_W_BYTES);
+    size_t woff = 0, boff = 0;
+    for (int l = 0; l < h->net_layers; ++l) {
+      const int ci = h->net_ch[l], co = h->net_ch[l + 1];
+      const bool last = l == h->net_layers - 1;
+      const void* in = (l % 2 == 0) ? (const void*)a0 : (const void*)a1;
+      void* out = last ? (void*)nout : ((l % 2 == 0) ? (void*)a1 : (void*)a0);
+      Prof p_(h, K_GUESS, (2.0 * ci + (last ? 4.0 : 2.0) * co) * pts * c3[0]);
+      if (prop_cnn_conv(ci, co, last ? PROP_CNN_LINEAR_F32 : PROP_CNN_RELU_BF16, in, wbase + woff, bbase + boff, out,
+                        nsys, g.ny, g.nx, (const int32_t*)g.st, (int)(sizeof(SysState) / 4), ST_ITER, st) != 0)
+        return PROP_E_CUDA;
+      woff += (size_t)9 * co * ci * 2;
+      boff += co;
+    }
+    { Prof p_(h, K_GUESS, (64.0 + 16.0 * Cn) * pts * c3[0]);
+      k_guess_unpack<T, 256><<<dim3(blocks, nsys), 256, 0, st>>>(g, nout);
+      k_guess_mark<<<tg, tb, 0, st>>>(g.st, nsys); }
+    const double endp = (double)c3[0] * Cn * pts;
+    if (Cn == 2) {
+      { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
+        CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
+      { Prof p_(h, K_COLS, 3 * cs * endp);
+        CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
+                   Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+      { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
+        CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 1) * F), ST_CYCLE_END, 0,
+                           VEPI_OPDIFF, 0, nsys, st)); }
+    }
+    { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
+      CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
+    { Prof p_(h, K_COLS, 2 * cs * endp);
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st)); }
+    { Prof p_(h, K_ROWS_INV, (4 * cs + 16) * endp);
+      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st)); }
+    { Prof p_(h, K_CONTROL, 0);
+      k_guess_alpha<<<tg, tb, 0, st>>>(g.st, nsys); }
+    { Prof p_(h, K_GUESS, (4.0 * cs + 32.0) * endp);
+      k_guess_apply<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    { Prof p_(h, K_CONTROL, 0);
+      k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw); }
+    { Prof p_(h, K_SCALE, 2 * cs * endp);
+      k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    { Prof p_(h, K_CONTROL, 0);
+      k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
+    CK(cudaGetLastError());
+    rc = read_counts(h, c3);
+    if (rc) return rc;
+  } else if (any_used) {
     { Prof p_(h, K_INIT, (cs + 16) * pts * c3[0] * Cn);
       k_init_systems<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
     { Prof p_(h, K_SCALE, 2 * cs * pts * c3[0] * Cn);
@@ -666,6 +737,7 @@ int validate_opts(const prop_opts* o) {
   if (o->restart < 1 || o->restart > MMAX) return PROP_E_ARG;
   if (o->max_restarts < 1) return PROP_E_ARG;
   if (!(o->tol > 0.0)) return PROP_E_ARG;
+  if (o->guess != PROP_GUESS_ZERO && o->guess != PROP_GUESS_LEARNED) return PROP_E_ARG;
   return PROP_OK;
 }
 
@@ -696,10 +768,12 @@ int build_groups(int nbeams, const prop_grid* grids, std::vector<Group>& groups,
   return PROP_OK;
 }
 
-size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, size_t* counts_off) {
+size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, int guess, size_t* counts_off,
+                    size_t* net_off) {
   size_t o = 0;
-  for (Group& G : groups) o = carve(G, o, P, C, m, prec);
-  *counts_off = align_up(o);
+  for (Group& G : groups) o = carve(G, o, P, C, m, prec, guess);
+  *net_off = align_up(o);
+  *counts_off = align_up(*net_off + NET_W_BYTES + NET_B_BYTES);
   return *counts_off + ALIGN;
 }
 
@@ -717,6 +791,7 @@ int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision) {
   o->restart = 20;
   o->max_restarts = precision == PROP_FP64 ? 50 : 200;
   o->tol = precision == PROP_FP64 ? 1e-12 : 1e-7;
+  o->guess = PROP_GUESS_ZERO;
   return PROP_OK;
 }
 
@@ -728,8 +803,8 @@ int prop_workspace_size(int32_t nbeams, const prop_grid* grids, int32_t npoles, 
   std::vector<int> bg, bs;
   rc = build_groups(nbeams, grids, groups, bg, bs);
   if (rc) return rc;
-  size_t co;
-  *bytes = total_layout(groups, npoles, opts->ncomp, opts->restart, opts->precision, &co);
+  size_t co, no;
+  *bytes = total_layout(groups, npoles, opts->ncomp, opts->restart, opts->precision, opts->guess, &co, &no);
   return PROP_OK;
 }
 
@@ -756,7 +831,9 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   h->grids.assign(grids, grids + nbeams);
   rc = build_groups(nbeams, grids, h->groups, h->beam_group, h->beam_slot);
   if (rc) { delete h; return rc; }
-  const size_t need = total_layout(h->groups, h->P, h->C, h->m, h->prec, &h->counts_off);
+  h->guess = opts->guess;
+  h->net_layers = 0;
+  const size_t need = total_layout(h->groups, h->P, h->C, h->m, h->prec, h->guess, &h->counts_off, &h->net_off);
   if (ws_bytes < need) { delete h; return PROP_E_WORKSPACE; }
   h->ws = (char*)d_workspace; h->ws_bytes = ws_bytes;
   h->stream = (cudaStream_t)stream;
@@ -1055,6 +1132,44 @@ template <typename T> static int apply_impl(prop* h, int beam, int pole, const v
 }
 
 extern "C" {
+
+int prop_set_guess_net(prop* h, int32_t nlayers, const int32_t* channels, const uint16_t* weights_bf16,
+                       const float* biases) {
+  if (!h || nlayers < 1 || nlayers > NET_MAX_LAYERS || !channels || !weights_bf16 || !biases) return PROP_E_ARG;
+  if (h->guess != PROP_GUESS_LEARNED) return PROP_E_ARG;
+  if (channels[0] != PROP_GUESS_CHANNELS || channels[nlayers] != PROP_GUESS_CHANNELS) return PROP_E_ARG;
+  size_t wb = 0, bb = 0;
+  for (int l = 0; l <= nlayers; ++l)
+    if (channels[l] != 16 && channels[l] != 32) return PROP_E_ARG;
+  for (int l = 0; l < nlayers; ++l) { wb += (size_t)9 * channels[l + 1] * channels[l] * 2; bb += channels[l + 1] * 4; }
+  CK(cudaMemcpyAsync(h->ws + h->net_off, weights_bf16, wb, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(h->ws + h->net_off + NET_W_BYTES, biases, bb, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->net_layers = nlayers;
+  for (int l = 0; l <= nlayers; ++l) h->net_ch[l] = channels[l];
+  return PROP_OK;
+}
+
+int prop_get_net_io(prop* h, int32_t beam, int32_t pole, void* d_in_bf16, float* d_target) {
+  if (!h || !d_in_bf16 || !d_target || beam < 0 || beam >= h->nbeams || pole < 0 || pole >= h->P) return PROP_E_ARG;
+  Group& G = h->groups[h->beam_group[beam]];
+  const int s = h->beam_slot[beam] * h->P + pole;
+  const int blocks = (int)std::min<long>(1024, (G.npts + 255) / 256);
+  Prof p_(h, K_GUESS, 0);
+  if (h->prec == PROP_FP64) {
+    GV<double> g = view<double>(h, G);
+    k_guess_pack<double, 256><<<dim3(blocks, 1), 256, 0, h->stream>>>(g, (__nv_bfloat16*)d_in_bf16,
+                                                                     (const double2*)(h->ws + G.off.poles), 0, s);
+    k_guess_target<double, 256><<<blocks, 256, 0, h->stream>>>(g, s, d_target);
+  } else {
+    GV<float> g = view<float>(h, G);
+    k_guess_pack<float, 256><<<dim3(blocks, 1), 256, 0, h->stream>>>(g, (__nv_bfloat16*)d_in_bf16,
+                                                                    (const double2*)(h->ws + G.off.poles), 0, s);
+    k_guess_target<float, 256><<<blocks, 256, 0, h->stream>>>(g, s, d_target);
+  }
+  CK(cudaGetLastError());
+  return PROP_OK;
+}
 
 int prop_get_correction(prop* h, int32_t beam, int32_t pole, void* out) {
   if (!h || !out || beam < 0 || beam >= h->nbeams || pole < 0 || pole >= h->P) return PROP_E_ARG;

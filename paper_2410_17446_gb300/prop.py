@@ -29,7 +29,11 @@ class prop_grid(ct.Structure):
 
 class prop_opts(ct.Structure):
     _fields_ = [("ncomp", ct.c_int32), ("precision", ct.c_int32), ("restart", ct.c_int32),
-                ("max_restarts", ct.c_int32), ("tol", ct.c_double)]
+                ("max_restarts", ct.c_int32), ("tol", ct.c_double), ("guess", ct.c_int32)]
+
+
+PROP_GUESS_ZERO, PROP_GUESS_LEARNED = 0, 1
+PROP_GUESS_CHANNELS = 16
 
 
 class prop_stats(ct.Structure):
@@ -39,7 +43,7 @@ class prop_stats(ct.Structure):
                 ("total_iters", ct.c_int64), ("kernel_launches", ct.c_int64)]
 
 
-PROP_NKINDS = 12
+PROP_NKINDS = 13
 
 
 class prop_kernel_profile(ct.Structure):
@@ -76,8 +80,25 @@ _SIGS = {
     "prop_apply_freespace_inverse": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     "prop_apply_operator": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     "prop_get_correction": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p]),
+    "prop_set_guess_net": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_int32), ct.c_void_p, ct.c_void_p]),
+    "prop_get_net_io": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     "prop_fft2_noalloc": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
                                      ct.c_void_p]),
+    # learned initial guess (include/prop_cnn.h)
+    "prop_cnn_conv": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                 ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32,
+                                 ct.c_int32, ct.c_void_p]),
+    "prop_cnn_wgrad_workspace": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32,
+                                            ct.POINTER(ct.c_size_t)]),
+    "prop_cnn_wgrad": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int32,
+                                  ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p]),
+    "prop_cnn_flip_transpose": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p]),
+    "prop_cnn_relu_mask": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p]),
+    "prop_cnn_to_bf16": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p]),
+    "prop_cnn_mse": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_int32,
+                                ct.c_void_p, ct.c_void_p]),
+    "prop_cnn_adam": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_float,
+                                 ct.c_float, ct.c_float, ct.c_float, ct.c_int32, ct.c_void_p, ct.c_void_p]),
 }
 
 
@@ -151,7 +172,7 @@ class Propagator:
 
     def __init__(self, grids, k0: float, n0: float, dz: float, poles, residues, r0,
                  ncomp: int = 1, precision: int = PROP_FP32, restart: int = 20, max_restarts: Optional[int] = None,
-                 tol: Optional[float] = None, device: str = "cuda", stream=None):
+                 tol: Optional[float] = None, device: str = "cuda", stream=None, guess: int = PROP_GUESS_ZERO):
         import torch
         self.torch = torch
         self.grids = [prop_grid(int(g[0]), int(g[1]), float(g[2]), float(g[3])) if not isinstance(g, prop_grid)
@@ -164,6 +185,7 @@ class Propagator:
             self.opts.max_restarts = max_restarts
         if tol is not None:
             self.opts.tol = tol
+        self.opts.guess = guess
         poles = np.asarray(poles, np.complex128)
         residues = np.asarray(residues, np.complex128)
         self.npoles = poles.size
@@ -239,6 +261,19 @@ class Propagator:
     def apply_freespace_inverse(self, beam: int, pole: int, d_v, d_out) -> None:
         check(lib().prop_apply_freespace_inverse(self.h, beam, pole, _dptr(d_v), _dptr(d_out)),
               "prop_apply_freespace_inverse")
+
+    def set_guess_net(self, channels, weights, biases) -> None:
+        """weights: per layer float arrays [9, co, ci] (rounded to bf16 here); biases: per layer [co]."""
+        import torch
+        ch = (ct.c_int32 * len(channels))(*channels)
+        wb = torch.cat([torch.as_tensor(np.asarray(w, np.float32)).reshape(-1) for w in weights]).to(torch.bfloat16)
+        bb = torch.cat([torch.as_tensor(np.asarray(b, np.float32)).reshape(-1) for b in biases])
+        wb, bb = wb.contiguous(), bb.contiguous()
+        check(lib().prop_set_guess_net(self.h, len(channels) - 1, ch, wb.data_ptr(), bb.data_ptr()),
+              "prop_set_guess_net")
+
+    def get_net_io(self, beam: int, pole: int, d_in_bf16, d_target) -> None:
+        check(lib().prop_get_net_io(self.h, beam, pole, _dptr(d_in_bf16), _dptr(d_target)), "prop_get_net_io")
 
     def get_correction(self, beam: int, pole: int, out=None):
         if out is None:
