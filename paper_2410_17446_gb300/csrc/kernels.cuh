@@ -306,6 +306,7 @@ struct EpiArgs {
   double2* out64;      // EPI_STORE64 / EPI_OPERATOR output
   const void* aux;     // vector operator: (Z - Z_fs) applied to the same field, complex T
   int kxsel;           // before the inverse row DFT multiply by 1 (0), i kx (1) or -kx^2 (2)
+  void* fwd_out;       // EPI_ACCUM64: also write the forward row DFT of the new field (next step's pass 1)
 };
 
 template <typename T, int N, int NR, int NT>
@@ -356,6 +357,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     }
     double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 1);
     __syncthreads();
+    #pragma unroll 4
     for (int i = 0; i <= ep.jj; ++i) {
       const C* vi = g.V + (((long)u * (g.m + 1) + i) * g.ncomp + c) * g.npts + off;
       T ar = 0, ai = 0;
@@ -377,6 +379,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
       case EPI_STORE: dst.at(u, c, g.npts)[off + e] = val; break;
       case EPI_STORE64: ep.out64[unit_off + e] = to_d(val); break;
       case EPI_ACCUM64: {   // new field = old field + val, written beside the old one
+        C nw;
         if constexpr (sizeof(T) == 4) {
           const long plane = (long)g.nb * g.ncomp * g.npts;
           const float2* ohi = reinterpret_cast<const float2*>(g.W64);
@@ -386,11 +389,14 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
           df_add(h.y, l.y, val.y);
           nhi[unit_off + e] = h;
           nhi[plane + unit_off + e] = l;
+          nw = h;
         } else {
           double2 t = g.W64[unit_off + e];
           t.x += (double)val.x; t.y += (double)val.y;
           ep.out64[unit_off + e] = t;
+          nw = t;
         }
+        if (ep.fwd_out) s[sidx<N, NR, false>(e / N, e % N)] = nw;   // same element, same thread
       } break;
       case EPI_OPERATOR: {
         double2 o;
@@ -432,6 +438,13 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
         acci += r0.x * r.y - r0.y * r.x;
       } break;
     }
+  }
+  if (ep.mode == EPI_ACCUM64 && ep.fwd_out) {   // forward row DFT of the new field for the next step
+    __syncthreads();
+    fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
+    C* o = reinterpret_cast<C*>(ep.fwd_out) + unit_off;
+#pragma unroll
+    for (int e = threadIdx.x; e < NR * N; e += NT) o[e] = s[sidx<N, NR, false>(e / N, e % N)];
   }
   if (ep.mode == EPI_R0 || ep.mode == EPI_TRUERES) {
     const double t = block_sum(acc, red);
@@ -535,6 +548,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
     for (int i = threadIdx.x; i < (NT / 32) * (MMAX + 1); i += NT) red2[i] = make_double2(0.0, 0.0);
     __syncthreads();
     double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 1);
+    #pragma unroll 4
     for (int i = 0; i <= jj; ++i) {
       const C* vi = g.V + ((long)u * (g.m + 1) + i) * F + off;
       T ar = 0, ai = 0;
@@ -606,6 +620,7 @@ __global__ void __launch_bounds__(NT) k_cgs(GV<T> g, int jj) {
     const long p = b0 + threadIdx.x + (long)q * NT;
     x[q] = p < L ? w[p] : C{};
   }
+  #pragma unroll 4
   for (int i = 0; i <= jj; ++i) {
     const C* v = vslot(g, s, i);
     const C hi = h[i];
@@ -623,6 +638,7 @@ __global__ void __launch_bounds__(NT) k_cgs(GV<T> g, int jj) {
   }
   double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 2);
   warp_add<T>(nr, (T)0, myred + MMAX + 1);
+  #pragma unroll 4
   for (int i = 0; i <= jj; ++i) {
     const C* v = vslot(g, s, i);
     T ar = 0, ai = 0;
@@ -669,6 +685,7 @@ __global__ void __launch_bounds__(NT) k_normalize(GV<T> g, int jj) {
   C* w = vslot(g, s, jj + 1);
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
     C x = w[p];
+    #pragma unroll 4
     for (int i = 0; i <= jj; ++i) {
       const C t = cmul(h[i], vslot(g, s, i)[p]);
       x.x -= t.x; x.y -= t.y;
@@ -725,6 +742,7 @@ __global__ void __launch_bounds__(NT) k_update_e(GV<T> g) {
   T nr = 0;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
     C inc; inc.x = 0; inc.y = 0;
+    #pragma unroll 4
     for (int i = 0; i < J; ++i) {
       const C t = cmul(ys[i], g.Zb[((long)s * g.m + i) * L + p]);
       inc.x += t.x; inc.y += t.y;

@@ -50,6 +50,7 @@ template <int N> constexpr int rows_nt() { return clamp_nt(rows_nr<N>() * N / 16
 template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * cols_per_cta<T>() / 16); }
 constexpr int NT_VEC = 256;
 constexpr int EPT_CGS = 8;
+constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host reads of the GMRES state
 
 struct Layout {
   size_t V, Zb, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
@@ -65,6 +66,7 @@ struct Group {
   int cur;                 // which of W64a / W64b holds the field
   bool medium_dirty;       // a medium was set since the homogeneity flags were read
   bool stats_zero;         // per-system statistics already record a homogeneous step
+  bool carry;              // Btmp holds the forward row DFT of the current field (from the last step)
   std::vector<int> nonhomog_host;
 };
 
@@ -304,8 +306,10 @@ cudaError_t rows_inv_vec(const GV<T>& g, Buf<typename Cx<T>::t> A, Buf<typename 
 }
 
 EpiArgs epi(int mode, int jj = 0, const double2* in64 = nullptr, double2* out64 = nullptr,
-            const void* aux = nullptr, int kxsel = 0) {
-  EpiArgs e; e.mode = mode; e.jj = jj; e.in64 = in64; e.out64 = out64; e.aux = aux; e.kxsel = kxsel; return e;
+            const void* aux = nullptr, int kxsel = 0, void* fwd_out = nullptr) {
+  EpiArgs e; e.mode = mode; e.jj = jj; e.in64 = in64; e.out64 = out64; e.aux = aux; e.kxsel = kxsel;
+  e.fwd_out = fwd_out;
+  return e;
 }
 
 int vec_blocks(long L) { return (int)std::max<long>(1, std::min<long>(2048, (L + NT_VEC * 4 - 1) / (NT_VEC * 4))); }
@@ -503,20 +507,30 @@ template <typename T> int step_group(prop* h, Group& G) {
 
   // w_hat = FFT2(w); ||w||^2 per beam
   CK(cudaMemsetAsync(g.bnorm2, 0, nb * sizeof(double), st));
-  if constexpr (sizeof(T) == 4) {   // the hi plane of the double-float field is the FP32 working copy
+  if (n_inh == 0 && G.carry) {
+    // homogeneous step after a homogeneous step: the previous inverse row pass already
+    // left the forward row DFT of this field in Btmp
+  } else if constexpr (sizeof(T) == 4) {   // the hi plane of the double-float field is the FP32 working copy
     Prof p_(h, K_ROWS_FWD, 2 * cs * pts * nb * Cn);
     CK(rows_fwd<T, float2>(g, buf((float2*)g.W64, F), buf(g.Btmp, F), -1, n_inh ? g.bnorm2 : nullptr, nb, st));
   } else {
     Prof p_(h, K_ROWS_FWD, (16 + cs) * pts * nb * Cn);
     CK(rows_fwd<T, double2>(g, buf(g.W64, F), buf(g.Btmp, F), -1, g.bnorm2, nb, st));
   }
+  G.carry = false;
   // column DFT (spectrum kept when poles will need it), then the free-space part
   // Wn = w + IFFT2[(r - 1) w_hat] (Eq. approx_fs_prop), in one column pass
   { Prof p_(h, K_COLS, (n_inh ? 4 : 3) * cs * pts * nb * Cn);
     CK(cols<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 1, MUL_TABLE, 1, 0, -1, (T)1, nb, st,
                n_inh ? buf(g.What, F) : Buf<C>{nullptr, 0, 1})); }
-  { Prof p_(h, K_ROWS_INV, (cs + 32) * pts * nb * Cn);   // read increment, old field (16 B), write new (16 B)
-    CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0, epi(EPI_ACCUM64, 0, nullptr, Wn), nb, st)); }
+  if (n_inh == 0) {   // homogeneous: the new field is final, so its row DFT for the next step is formed here
+    Prof p_(h, K_ROWS_INV, (2 * cs + 32) * pts * nb * Cn);   // increment, old field, new field, next row DFT
+    CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0,
+                   epi(EPI_ACCUM64, 0, nullptr, Wn, nullptr, 0, g.Btmp), nb, st));
+  } else {
+    Prof p_(h, K_ROWS_INV, (cs + 32) * pts * nb * Cn);   // read increment, old field (16 B), write new (16 B)
+    CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0, epi(EPI_ACCUM64, 0, nullptr, Wn), nb, st));
+  }
   const int bw = h->prec == PROP_FP32 ? 1 : 0;
   if (n_inh == 0) {           // homogeneous medium: the free-space step is exact, no correction
     if (!G.stats_zero) {      // record zero iterations for every system (once)
@@ -527,6 +541,7 @@ template <typename T> int step_group(prop* h, Group& G) {
     }
     CK(cudaGetLastError());
     G.cur ^= 1;
+    G.carry = true;
     return PROP_OK;
   }
   G.stats_zero = false;
@@ -619,26 +634,33 @@ template <typename T> int step_group(prop* h, Group& G) {
   }
   const double breakdown = sizeof(T) == 4 ? 1e-6 : 1e-14;
   while (c3[0] > 0) {
+    // Iterations are launched in batches of SYNC_EVERY between host reads: every
+    // kernel skips systems that have left ST_ITER, so launches past a cycle end
+    // are empty.  k_count records the active count after each iteration in its own
+    // slot, from which the algorithmic bytes of each launch are charged exactly.
+    int slot_base = 0;                       // slot holding the count before iteration jj0
+    std::vector<int> cnt(3 * (m + 2));
+    int jj0 = 0;
+    cnt[0] = c3[0];
     for (int jj = 0; jj < m; ++jj) {
-      const double act = (double)c3[0] * Cn * pts;
       C* Vj = g.V + (long)jj * F;
       const long vs = (long)(m + 1) * F;
-      { Prof p_(h, K_ROWS_FWD, 2 * cs * act);
+      { Prof p_(h, K_ROWS_FWD, 0);
         CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st)); }
       if (Cn == 2) {
-        { Prof p_(h, K_COLS, 3 * cs * act);
+        { Prof p_(h, K_COLS, 0);
           CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st,
                      Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
-        { Prof p_(h, K_ROWS_INV, (6 + 2.5 + jj) * cs * act);   // A, B, v_j, 5/2 coefficient planes, z, w, projections
+        { Prof p_(h, K_ROWS_INV, 0);
           CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, nsys,
                              st)); }
       } else {
-        { Prof p_(h, K_COLS, 2 * cs * act);
+        { Prof p_(h, K_COLS, 0);
           CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
-        { Prof p_(h, K_ROWS_INV, (5 + jj) * cs * act);     // epilogue + first projections (v_j read once)
+        { Prof p_(h, K_ROWS_INV, 0);
           CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
       }
-      { Prof p_(h, K_CGS, (2.0 * (jj + 1) + 2) * cs * act);
+      { Prof p_(h, K_CGS, 0);
         k_cgs<T, NT_VEC, EPT_CGS><<<dim3(cgs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CONTROL, 0);
         k_arnoldi_finish<<<nsys, 64, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown, g.anorm, bw,
@@ -646,12 +668,31 @@ template <typename T> int step_group(prop* h, Group& G) {
       { Prof p_(h, K_NORMALIZE, 0);
         k_normalize<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CONTROL, 0);
-        k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
+        k_count<<<1, 256, 0, st>>>(g.st, nsys, counts + 3 * (jj - jj0 + 1)); }
       CK(cudaGetLastError());
-      rc = read_counts(h, c3);
-      if (rc) return rc;
-      h->k_bytes[K_NORMALIZE] += (jj + 3) * cs * pts * Cn * c3[0];   // systems that continued
-      h->total_iters += (int64_t)(act / (Cn * pts));
+      const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj + 1 == m;
+      if (!sync_now) continue;
+      // read the slots of this batch; slot 0 already holds the count before jj0
+      const int nb = jj + 1 - jj0;
+      if (cudaMemcpyAsync(cnt.data() + 3, counts + 3, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return PROP_E_CUDA;
+      if (!h->pending.empty()) resolve_pending(h);
+      for (int b2 = 0; b2 < nb; ++b2) {
+        const int j = jj0 + b2;
+        const double act = (double)cnt[3 * b2] * Cn * pts;          // systems iterating in iteration j
+        const double cont = (double)cnt[3 * (b2 + 1)] * Cn * pts;   // systems that continued after it
+        h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
+        h->k_bytes[K_COLS] += (Cn == 2 ? 3 : 2) * cs * act;
+        h->k_bytes[K_ROWS_INV] += (Cn == 2 ? (8.5 + j) : (5.0 + j)) * cs * act;
+        h->k_bytes[K_CGS] += (2.0 * (j + 1) + 2) * cs * act;
+        h->k_bytes[K_NORMALIZE] += (j + 3) * cs * cont;
+        h->total_iters += cnt[3 * b2];
+      }
+      c3[0] = cnt[3 * nb]; c3[1] = cnt[3 * nb + 1]; c3[2] = cnt[3 * nb + 2];
+      cnt[0] = c3[0];
+      jj0 = jj + 1;
+      (void)slot_base;
       if (c3[0] == 0) break;
     }
     if (c3[1] == 0) break;
@@ -758,6 +799,7 @@ int build_groups(int nbeams, const prop_grid* grids, std::vector<Group>& groups,
       G.nx = gr.nx; G.ny = gr.ny; G.dx = gr.dx; G.dy = gr.dy; G.npts = (long)gr.nx * gr.ny; G.cur = 0;
       G.medium_dirty = true;
       G.stats_zero = false;
+      G.carry = false;
       groups.push_back(G);
       gi = (int)groups.size() - 1;
     }
@@ -774,7 +816,7 @@ size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, i
   for (Group& G : groups) o = carve(G, o, P, C, m, prec, guess);
   *net_off = align_up(o);
   *counts_off = align_up(*net_off + NET_W_BYTES + NET_B_BYTES);
-  return *counts_off + ALIGN;
+  return *counts_off + align_up(3 * (MMAX + 2) * sizeof(int));
 }
 
 }  // namespace
@@ -877,6 +919,7 @@ int prop_set_medium(prop* h, int32_t beam, const void* n2) {
     if (rc) return rc;
   }
   G.medium_dirty = true;
+  G.carry = false;        // the vector psi pipeline uses the beam scratch that holds the carried row DFT
   return PROP_OK;
 }
 
@@ -898,6 +941,7 @@ int prop_set_field(prop* h, int32_t beam, const void* w) {
   CK(cudaMemcpyAsync(h->ws + G.off.stage, w, F * 16, cudaMemcpyDefault, h->stream));
   const int rc = field_io(h, G, h->beam_slot[beam], 1);
   if (rc) return rc;
+  G.carry = false;
   h->steps = 0;
   return PROP_OK;
 }
@@ -1104,6 +1148,7 @@ int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t 
 template <typename T> static int apply_impl(prop* h, int beam, int pole, const void* v, void* out, bool op) {
   using C = typename Cx<T>::t;
   Group& G = h->groups[h->beam_group[beam]];
+  G.carry = false;        // Btmp is used as scratch here
   const int slot = h->beam_slot[beam];
   GV<T> g = view<T>(h, G);
   const long F = (long)h->C * g.npts;
