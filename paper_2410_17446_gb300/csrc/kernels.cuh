@@ -112,6 +112,11 @@ __device__ __forceinline__ float2 to_c(float2 a, float) { return a; }
 __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
 __device__ __forceinline__ double2 to_d(double2 a) { return a; }
 
+// Hint: bring the 128-byte line holding p into L2 (PTX prefetch.global.L2).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum) for the
 // double-float master field of the FP32 path.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -230,6 +235,8 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   const int x0 = blockIdx.x * NV;
   const C* in = src.at(u, c, g.npts);
+  if (mul == MUL_TABLE)   // the multiplier is read after the forward DFT: start its DRAM fetch now
+    for (int n = threadIdx.x; n < NY; n += NT) prefetch_l2(g.basemul + (long)n * g.nx + x0);
 #pragma unroll 8
   for (int e = threadIdx.x; e < NY * NV; e += NT) {
     const int n = e / NV, v = e % NV;
@@ -324,6 +331,19 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   const int row0 = blockIdx.x * NR;
   const long off = (long)row0 * N;
   const C* in = src.at(u, c, g.npts) + off;
+  if (ep.mode == EPI_ACCUM64) {   // the old field is read after the inverse DFT: start its DRAM fetch now
+    const long uo = ((long)u * g.ncomp + c) * g.npts + off;
+    const char* w0 = reinterpret_cast<const char*>(g.W64);
+    if constexpr (sizeof(T) == 4) {
+      const long plane = (long)g.nb * g.ncomp * g.npts * 8;
+      for (int e = threadIdx.x * 16; e < NR * N; e += NT * 16) {
+        prefetch_l2(w0 + (uo + e) * 8);
+        prefetch_l2(w0 + plane + (uo + e) * 8);
+      }
+    } else {
+      for (int e = threadIdx.x * 8; e < NR * N; e += NT * 8) prefetch_l2(w0 + (uo + e) * 16);
+    }
+  }
 #pragma unroll
   for (int e = threadIdx.x; e < NR * N; e += NT) {
     C a = in[e];
