@@ -32,14 +32,16 @@ struct SysState {
   double beta, resid, scale, nrm_a, nrm_b, beta0;  // beta0: ||R0|| at the step start
   double z0norm2, enorm2;                     // ||z_k||^2 (free-space solve), ||e_k||^2
   double2 r0r;                                // <R0, r> of the last true-residual pass
-  double2 g[MMAX + 1];
+  double2 g[MMAX + 1];             // Givens-rotated right-hand side beta e_1
+  double2 gsave;                    // g[j] before rotation j (rotation j is redone when column j is final)
   double2 sn[MMAX];
   double cs[MMAX];
-  double2 H[(MMAX + 1) * MMAX];   // H[i + j*(MMAX+1)]
+  double2 H[(MMAX + 1) * MMAX];     // rotated (upper-triangular) columns, H[i + j*(MMAX+1)]
+  double2 Hu[(MMAX + 1) * MMAX];    // Hessenberg columns as built (same indexing)
   double2 y[MMAX];
-  double2 dots1[MMAX + 1];
-  double2 dots2[MMAX + 1];
-  double2 coef[MMAX + 1];
+  double2 dots1[MMAX + 1];          // <v_i, w>
+  double2 dots2[MMAX + 1];          // <v_i, u_j>: the delayed re-orthogonalisation coefficients
+  double2 coef[MMAX + 1];           // projection coefficients of the next candidate
 };
 
 template <typename T> struct GV {
@@ -47,7 +49,6 @@ template <typename T> struct GV {
   int nx, ny, ncomp, P, m, nb, nsys;
   long npts;
   C* V;          // [nsys][m+1][ncomp][npts]  Krylov basis
-  C* Zb;         // [nsys][m][ncomp][npts]    preconditioned basis z_j = M^-1 v_j
   C* R0;         // [nsys][ncomp][npts]       right-hand side of the correction system
   double2* E;    // [nsys][ncomp][npts]       correction e_k, FP64
   C* Tmp;        // [nsys][ncomp][npts]       FFT intermediate
@@ -68,7 +69,8 @@ template <typename T> struct GV {
   const double2* rk;    // [P] residues r_k
   const double* anorm;  // [2P]: bound on ||Z - p_k I|| over this grid (backward-error test), then the
                         //       per-pole tolerance factor mu_k >= 1 (error equidistribution)
-  double2* part;        // [nsys][3][NSTRIPE][MMAX+1] striped accumulators: dots1, dots2, ||w'||^2
+  double2* part;        // [nsys][3][NSTRIPE][MMAX+1] striped accumulators: <v_i, w>, <v_i, u_j>
+                        //   (slot MMAX: ||w||^2), plane 2 slot 0: ||u_{j+1}||^2
   // vector operator (ncomp = 2) only
   C* psi;        // [nb][5][npts]  coefficients of Z - Z_fs: D1 = delta + psit_xx, D2 = delta + psit_yy,
                  //                X = psit_xy, px = psit_x, py = psit_y (psit = psi/(k0 n0)^2, psi = Log n^2)
@@ -85,7 +87,7 @@ template <typename C, typename T> __device__ __forceinline__ C ik_factor(int i, 
   return f;
 }
 
-// striped accumulator slot: plane 0 = first projections, 1 = second, 2 = norm
+// striped accumulator slot: plane 0 = <v_i, w>, 1 = <v_i, u_j>, 2 = candidate norm
 __device__ __forceinline__ double2* part_at(double2* part, int s, int plane, int stripe, int i) {
   return part + (((long)s * 3 + plane) * NSTRIPE + stripe) * (MMAX + 1) + i;
 }
@@ -104,7 +106,7 @@ template <typename C> struct Buf {
 enum MulMode { MUL_NONE = 0, MUL_TABLE = 1, MUL_POLE_INV = 2, MUL_POLE_FWD = 3, MUL_SCALE = 4,
                MUL_DY = 5, MUL_DYY = 6 };   // scale * i ky,  scale * (-ky^2)
 enum EpiMode { EPI_STORE = 0, EPI_STORE64 = 1, EPI_ACCUM64 = 2, EPI_R0 = 3, EPI_ARNOLDI = 4,
-               EPI_TRUERES = 5, EPI_OPERATOR = 6 };
+               EPI_TRUERES = 5, EPI_OPERATOR = 6, EPI_ADD_E = 7 };
 
 __device__ __forceinline__ float2 to_c(double2 a, float) { return make_float2((float)a.x, (float)a.y); }
 __device__ __forceinline__ double2 to_c(double2 a, double) { return a; }
@@ -174,6 +176,32 @@ __device__ __forceinline__ void flush_partials(double2* red, int nwarps, int n, 
     for (int w = 0; w < nwarps; ++w) { re += red[w * (MMAX + 1) + i].x; im += red[w * (MMAX + 1) + i].y; }
     atomicAdd(&a[i].x, re);
     atomicAdd(&a[i].y, im);
+  }
+}
+
+// warp_add into a slot of the working precision (per-warp partials of the FP32
+// path are float sums already; the cross-warp and cross-CTA sums are FP64).
+template <typename A, typename S> __device__ __forceinline__ void warp_acc(A re, A im, S* slot) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) { slot->x += re; slot->y += im; }
+}
+
+// flush_partials for per-warp slots red[w * (MMAX+1) + i] of type S: slots
+// 0..n-1 and, when extra >= 0, slot extra.  Caller synchronises first.
+template <typename S>
+__device__ __forceinline__ void flush_slots(const S* red, int nwarps, int n, double2* acc, int extra = -1) {
+  double2* a = acc + (blockIdx.x % NSTRIPE) * (MMAX + 1);
+  for (int t = threadIdx.x; t <= n; t += blockDim.x) {
+    const int i = (t == n) ? extra : t;
+    if (i < 0) continue;
+    double re = 0.0, im = 0.0;
+    for (int w = 0; w < nwarps; ++w) { re += (double)red[w * (MMAX + 1) + i].x; im += (double)red[w * (MMAX + 1) + i].y; }
+    atomicAdd(&a[i].x, re);
+    if (im != 0.0) atomicAdd(&a[i].y, im);
   }
 }
 
@@ -316,7 +344,9 @@ struct EpiArgs {
   void* fwd_out;       // EPI_ACCUM64: also write the forward row DFT of the new field (next step's pass 1)
 };
 
-template <typename T, int N, int NR, int NT>
+// ARN: the instantiation for the EPI_ARNOLDI epilogue (kept apart so that the
+// other epilogues do not carry its register footprint).
+template <typename T, int N, int NR, int NT, bool ARN>
 __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, int skip_homog, EpiArgs ep) {
   using C = typename Cx<T>::t;
@@ -325,7 +355,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   __shared__ double red[32];
   const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
-  const bool sys = (ep.mode == EPI_R0 || ep.mode == EPI_ARNOLDI || ep.mode == EPI_TRUERES);
+  const bool sys = (ep.mode == EPI_R0 || ep.mode == EPI_ARNOLDI || ep.mode == EPI_TRUERES || ep.mode == EPI_ADD_E);
   const int beam = sys ? u / g.P : u;
   if (skip_homog && !g.nonhomog[beam]) return;
   const int row0 = blockIdx.x * NR;
@@ -355,43 +385,20 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   fft_smem<C, N, true, NR, NT, false>(s, g.twx, threadIdx.x);
   const C* dl = g.delta + (long)beam * g.npts + off;
   const long unit_off = ((long)u * g.ncomp + c) * g.npts + off;   // [unit][c][pt] arrays
-  if (ep.mode == EPI_ARNOLDI) {
-    // z_j = M^-1 v_j (stored), w = v_j + delta z_j (stored as v_{j+1}), and the
-    // first Gram-Schmidt projections <v_i, w>, i <= j, while w is in registers.
-    constexpr int TPT = NR * N / NT;
-    __shared__ double2 red2[(NT / 32) * (MMAX + 1)];
-    for (int i = threadIdx.x; i < (NT / 32) * (MMAX + 1); i += NT) red2[i] = make_double2(0.0, 0.0);
+  if constexpr (ARN) {
+    // Arnoldi step: u = v_j (the candidate left by the last update pass),
+    // z = M^-1 u from this transform, w = u + delta z stored as v_{j+1}; the
+    // inner products follow in k_dcgs_gram.
     const long vj = (((long)u * (g.m + 1) + ep.jj) * g.ncomp + c) * g.npts + off;
-    const long zb = (((long)u * g.m + ep.jj) * g.ncomp + c) * g.npts + off;
-    C wv[TPT];
 #pragma unroll
-    for (int q = 0; q < TPT; ++q) {
-      const int e = threadIdx.x + q * NT;
+    for (int e = threadIdx.x; e < NR * N; e += NT) {
       const C val = s[sidx<N, NR, false>(e / N, e % N)];
-      g.Zb[zb + e] = val;
       const C v = g.V[vj + e];
       const C dz = cmul(dl[e], val);
       C w; w.x = v.x + dz.x; w.y = v.y + dz.y;
       g.V[vj + (long)g.ncomp * g.npts + e] = w;
-      wv[q] = w;
     }
-    double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 1);
-    __syncthreads();
-    #pragma unroll 4
-    for (int i = 0; i <= ep.jj; ++i) {
-      const C* vi = g.V + (((long)u * (g.m + 1) + i) * g.ncomp + c) * g.npts + off;
-      T ar = 0, ai = 0;
-#pragma unroll
-      for (int q = 0; q < TPT; ++q) {
-        const C a = vi[threadIdx.x + q * NT], b = wv[q];
-        ar += a.x * b.x + a.y * b.y;
-        ai += a.x * b.y - a.y * b.x;
-      }
-      warp_add<T>(ar, ai, myred + i);
-    }
-    flush_partials(red2, NT / 32, ep.jj, part_at(g.part, u, 0, 0, 0));
-    return;
-  }
+  } else {
   double acc = 0.0, acc2 = 0.0, accr = 0.0, acci = 0.0;
   for (int e = threadIdx.x; e < NR * N; e += NT) {
     const C val = s[sidx<N, NR, false>(e / N, e % N)];
@@ -430,6 +437,13 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
           o.y = (double)val.y + d.x * v.y + d.y * v.x;
         }
         ep.out64[unit_off + e] = o;
+      } break;
+      case EPI_ADD_E: {   // e += M^-1 V y, accumulated in FP64; ||e||^2 for the backward-error test
+        double2 a = g.E[unit_off + e];
+        a.x += (double)val.x; a.y += (double)val.y;
+        g.E[unit_off + e] = a;
+        const T ax = (T)a.x, ay = (T)a.y;
+        acc += (double)(ax * ax + ay * ay);
       } break;
       case EPI_R0: {
         const C r = cmul(dl[e], val);
@@ -474,10 +488,15 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     const double t = block_sum(acc2, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t);
   }
+  if (ep.mode == EPI_ADD_E) {
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&g.st[u].enorm2, t);
+  }
   if (ep.mode == EPI_TRUERES) {
     const double tr = block_sum(accr, red);
     const double ti = block_sum(acci, red);
     if (threadIdx.x == 0) { atomicAdd(&g.st[u].r0r.x, tr); atomicAdd(&g.st[u].r0r.y, ti); }
+  }
   }
 }
 
@@ -503,7 +522,6 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  __shared__ double2 red2[(NT / 32) * (MMAX + 1)];
   const int u = blockIdx.y;
   if (!unit_active(g.st, mask, u)) return;
   const int beam = (mode == VEPI_OPDIFF && mask < 0) ? u : u / g.P;
@@ -527,7 +545,6 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   const C* cf = g.psi + (long)beam * 5 * g.npts + off;    // D1, D2, X, px, py planes
   const long F = 2 * g.npts;
   double acc = 0.0, acc2 = 0.0;
-  C w1v[TPT], w2v[TPT];
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
     const int e = threadIdx.x + q * NT, r = e / N, n = e % N;
@@ -543,16 +560,13 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
     t = cmul(D2, z2); d2.x += t.x; d2.y += t.y;
     t = cmul(px, y1); d2.x += t.x; d2.y += t.y;
     t = cmul(py, y2); d2.x += t.x; d2.y += t.y;
-    if (mode == VEPI_ARNOLDI) {
+    if (mode == VEPI_ARNOLDI) {   // w = u + (Z - Z_fs) M^-1 u, stored as v_{j+1}
       const long vj = ((long)u * (g.m + 1) + jj) * F + off + e;
-      const long zb = ((long)u * g.m + jj) * F + off + e;
-      g.Zb[zb] = z1; g.Zb[zb + g.npts] = z2;
       const C v1 = g.V[vj], v2 = g.V[vj + g.npts];
       C w1, w2;
       w1.x = v1.x + d1.x; w1.y = v1.y + d1.y;
       w2.x = v2.x + d2.x; w2.y = v2.y + d2.y;
       g.V[vj + F] = w1; g.V[vj + F + g.npts] = w2;
-      w1v[q] = w1; w2v[q] = w2;
     } else if (mode == VEPI_R0) {
       const long rb = (long)u * F + off + e;
       C m1, m2; m1.x = -d1.x; m1.y = -d1.y; m2.x = -d2.x; m2.y = -d2.y;
@@ -564,25 +578,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
       out.at(u, 1, g.npts)[off + e] = d2;
     }
   }
-  if (mode == VEPI_ARNOLDI) {   // first Gram-Schmidt projections over both components
-    for (int i = threadIdx.x; i < (NT / 32) * (MMAX + 1); i += NT) red2[i] = make_double2(0.0, 0.0);
-    __syncthreads();
-    double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 1);
-    #pragma unroll 4
-    for (int i = 0; i <= jj; ++i) {
-      const C* vi = g.V + ((long)u * (g.m + 1) + i) * F + off;
-      T ar = 0, ai = 0;
-#pragma unroll
-      for (int q = 0; q < TPT; ++q) {
-        const int e = threadIdx.x + q * NT;
-        const C a1 = vi[e], a2 = vi[g.npts + e];
-        ar += a1.x * w1v[q].x + a1.y * w1v[q].y + a2.x * w2v[q].x + a2.y * w2v[q].y;
-        ai += a1.x * w1v[q].y - a1.y * w1v[q].x + a2.x * w2v[q].y - a2.y * w2v[q].x;
-      }
-      warp_add<T>(ar, ai, myred + i);
-    }
-    flush_partials(red2, NT / 32, jj, part_at(g.part, u, 0, 0, 0));
-  } else if (mode == VEPI_R0) {
+  if (mode == VEPI_R0) {
     const double t = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].nrm_a, t);
     const double t2 = block_sum(acc2, red);
@@ -613,106 +609,165 @@ template <typename T> __device__ __forceinline__ typename Cx<T>::t* vslot(const 
   return g.V + ((long)s * (g.m + 1) + jj) * g.ncomp * g.npts;
 }
 
-// Classical Gram-Schmidt, first subtraction and the re-orthogonalisation dots:
-// w <- w - sum_i dots1[i] v_i; dots2[i] += <v_i, w>; nrm_b += ||w||^2.
-// One chunk of NT*EPT points per CTA; partial sums are reduced per warp into
-// shared memory and flushed once per CTA.
-template <typename T, int NT, int EPT>
-__global__ void __launch_bounds__(NT) k_cgs(GV<T> g, int jj) {
-  using C = typename Cx<T>::t;
-  __shared__ C h[MMAX + 1];
-  __shared__ double2 red2[(NT / 32) * (MMAX + 2)];
-  const int s = blockIdx.y;
-  if (g.st[s].state != ST_ITER) return;
-  for (int i = threadIdx.x; i <= jj; i += NT) {
-    double re = 0.0, im = 0.0;
-    for (int k = 0; k < NSTRIPE; ++k) { const double2 d = *part_at(g.part, s, 0, k, i); re += d.x; im += d.y; }
-    h[i].x = (T)re; h[i].y = (T)im;
-  }
-  for (int i = threadIdx.x; i < (NT / 32) * (MMAX + 2); i += NT) red2[i] = make_double2(0.0, 0.0);
-  __syncthreads();
-  const long L = (long)g.ncomp * g.npts;
-  C* w = vslot(g, s, jj + 1);
-  const long b0 = (long)blockIdx.x * NT * EPT;
-  C x[EPT];
+// Sum each of 32 per-lane values over the warp: on return v[0] of lane l holds
+// the warp total of value l (a butterfly that halves the live values at each
+// of its five levels: 31 shuffles in all).
+template <typename A> __device__ __forceinline__ void warp_transpose_reduce(A (&v)[32]) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const long p = b0 + threadIdx.x + (long)q * NT;
-    x[q] = p < L ? w[p] : C{};
-  }
-  #pragma unroll 4
-  for (int i = 0; i <= jj; ++i) {
-    const C* v = vslot(g, s, i);
-    const C hi = h[i];
+  for (int k = 16; k >= 1; k >>= 1) {
+    const bool up = (lane & k) != 0;
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const long p = b0 + threadIdx.x + (long)q * NT;
-      if (p < L) { const C t = cmul(hi, v[p]); x[q].x -= t.x; x[q].y -= t.y; }
-    }
-  }
-  T nr = 0;
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const long p = b0 + threadIdx.x + (long)q * NT;
-    if (p < L) { w[p] = x[q]; nr += x[q].x * x[q].x + x[q].y * x[q].y; }
-  }
-  double2* myred = red2 + (threadIdx.x >> 5) * (MMAX + 2);
-  warp_add<T>(nr, (T)0, myred + MMAX + 1);
-  #pragma unroll 4
-  for (int i = 0; i <= jj; ++i) {
-    const C* v = vslot(g, s, i);
-    T ar = 0, ai = 0;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const long p = b0 + threadIdx.x + (long)q * NT;
-      if (p < L) {
-        const C a = v[p], b = x[q];
-        ar += a.x * b.x + a.y * b.y;
-        ai += a.x * b.y - a.y * b.x;
-      }
-    }
-    warp_add<T>(ar, ai, myred + i);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i <= jj + 1; i += NT) {
-    const int slot = i <= jj ? i : MMAX + 1;
-    double re = 0.0, im = 0.0;
-    for (int wq = 0; wq < NT / 32; ++wq) { re += red2[wq * (MMAX + 2) + slot].x; im += red2[wq * (MMAX + 2) + slot].y; }
-    const int stripe = blockIdx.x % NSTRIPE;
-    if (i <= jj) {
-      double2* a = part_at(g.part, s, 1, stripe, i);
-      atomicAdd(&a->x, re); atomicAdd(&a->y, im);
-    } else {
-      atomicAdd(&part_at(g.part, s, 2, stripe, 0)->x, re);
+    for (int i = 0; i < k; ++i) {
+      const A send = up ? v[i] : v[i + k];
+      const A keep = up ? v[i + k] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
     }
   }
 }
 
-// v_{jj+1} = (w - sum_i coef[i] v_i) * scale  for systems still iterating.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_normalize(GV<T> g, int jj) {
+// The inner products of iteration j of the delayed re-orthogonalisation (see
+// k_dcgs_finish): b_i = <v_i, w>, a_i = <v_i, u> (i < j), d = <u, w>, c = <u, u>
+// and ||w||^2, with u = v_j and w = v_{j+1}, for every iterating system.  Each
+// thread keeps EPT points of u and w in registers and takes the basis in
+// groups of 8 vectors (8*EPT loads in flight); a group's 32 partial sums leave
+// the warp in one transpose-reduce.  Per-warp totals are summed in FP64 and
+// added to the striped accumulators (planes 0 and 1; slot MMAX of plane 1 takes ||w||^2).
+template <typename T, int NT, int EPT>
+__global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj) {
   using C = typename Cx<T>::t;
-  __shared__ C h[MMAX + 1];
+  constexpr int NW = NT / 32;
+  __shared__ T red[NW][4 * (MMAX + 1)];
   const int s = blockIdx.y;
   if (g.st[s].state != ST_ITER) return;
-  for (int i = threadIdx.x; i <= jj; i += NT) {
-    const double2 d = g.st[s].coef[i];
-    h[i].x = (T)d.x; h[i].y = (T)d.y;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long L = (long)g.ncomp * g.npts;
+  const C* up = vslot(g, s, jj);
+  const C* wpv = vslot(g, s, jj + 1);
+  const long b0 = (long)blockIdx.x * NT * EPT + threadIdx.x;
+  C uv[EPT], wv[EPT];
+  T uwr = 0, uwi = 0, uu = 0, ww = 0;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const long p = b0 + (long)e * NT;
+    uv[e] = C{}; wv[e] = C{};
+    if (p < L) { uv[e] = up[p]; wv[e] = wpv[p]; }
+    uwr += uv[e].x * wv[e].x + uv[e].y * wv[e].y; uwi += uv[e].x * wv[e].y - uv[e].y * wv[e].x;
+    uu += uv[e].x * uv[e].x + uv[e].y * uv[e].y;
+    ww += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
+  }
+  for (int g0 = 0; g0 <= jj; g0 += 8) {   // slots g0..g0+7; slot jj carries (d, c, ||w||^2)
+    C vv[8][EPT];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const C* vi = vslot(g, s, g0 + k);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const long p = b0 + (long)e * NT;
+        vv[k][e] = (g0 + k < jj && p < L) ? vi[p] : C{};
+      }
+    }
+    T acc[32];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      T br = 0, bi = 0, ar = 0, ai = 0;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const C a = vv[k][e], w = wv[e], x = uv[e];
+        br += a.x * w.x + a.y * w.y; bi += a.x * w.y - a.y * w.x;
+        ar += a.x * x.x + a.y * x.y; ai += a.x * x.y - a.y * x.x;
+      }
+      if (g0 + k == jj) { br = uwr; bi = uwi; ar = uu; ai = ww; }
+      acc[4 * k] = br; acc[4 * k + 1] = bi; acc[4 * k + 2] = ar; acc[4 * k + 3] = ai;
+    }
+    warp_transpose_reduce(acc);
+    if (g0 + (lane >> 2) <= jj) red[wp][4 * g0 + lane] = acc[0];
   }
   __syncthreads();
-  const T sc = (T)g.st[s].scale;
-  const long L = (long)g.ncomp * g.npts;
-  C* w = vslot(g, s, jj + 1);
-  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
-    C x = w[p];
-    #pragma unroll 4
-    for (int i = 0; i <= jj; ++i) {
-      const C t = cmul(h[i], vslot(g, s, i)[p]);
-      x.x -= t.x; x.y -= t.y;
-    }
-    x.x *= sc; x.y *= sc;
-    w[p] = x;
+  double2* pb = part_at(g.part, s, 0, blockIdx.x % NSTRIPE, 0);
+  double2* pa = part_at(g.part, s, 1, blockIdx.x % NSTRIPE, 0);
+  for (int t = threadIdx.x; t < 4 * (jj + 1); t += NT) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v += (double)red[w][t];
+    const int i = t >> 2, comp = t & 3;
+    if (comp == 0) atomicAdd(&pb[i].x, v);
+    else if (comp == 1) atomicAdd(&pb[i].y, v);
+    else if (comp == 2) atomicAdd(&pa[i].x, v);
+    else if (i < jj) atomicAdd(&pa[i].y, v);
+    else atomicAdd(&pa[MMAX].x, v);   // ||w||^2
   }
+}
+
+// Update pass of the delayed re-orthogonalisation (see k_dcgs_finish):
+//   q_j     = (u - sum_{i<j} a_i v_i) / rho                  (written over u = v_j)
+//   u_{j+1} = w / rho - sum_{i<j} gamma_i v_i - gamma_j q_j  (written over w = v_{j+1})
+// with a_i = dots2[i], gamma_i = coef[i], 1/rho = scale; adds ||u_{j+1}||^2 to
+// the norm accumulator.  One sweep over v_0..v_{j-1} in groups of 8 vectors
+// (8*EPT loads in flight per thread); each CTA owns NT*EPT points.
+template <typename T, int NT, int EPT>
+__global__ void __launch_bounds__(NT) k_dcgs_update(GV<T> g, int jj) {
+  using C = typename Cx<T>::t;
+  __shared__ C ca[MMAX + 8], cg[MMAX + 8];
+  __shared__ double red[32];
+  const int s = blockIdx.y;
+  if (g.st[s].state != ST_ITER) return;
+  for (int i = threadIdx.x; i < jj + 8; i += NT) {
+    C a{}, c{};
+    if (i <= jj) { const double2 d = g.st[s].coef[i]; c.x = (T)d.x; c.y = (T)d.y; }
+    if (i < jj) { const double2 d = g.st[s].dots2[i]; a.x = (T)d.x; a.y = (T)d.y; }
+    ca[i] = a; cg[i] = c;
+  }
+  __syncthreads();
+  const T ir = (T)g.st[s].scale;
+  const long L = (long)g.ncomp * g.npts;
+  C* uj = vslot(g, s, jj);
+  C* wj = vslot(g, s, jj + 1);
+  const long b0 = (long)blockIdx.x * NT * EPT + threadIdx.x;
+  C qv[EPT], x[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const long p = b0 + (long)e * NT;
+    qv[e] = C{}; x[e] = C{};
+    if (p < L) { qv[e] = uj[p]; const C w = wj[p]; x[e].x = w.x * ir; x[e].y = w.y * ir; }
+  }
+  for (int i0 = 0; i0 < jj; i0 += 8) {
+    C vv[8][EPT];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const C* v = vslot(g, s, i0 + k);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const long p = b0 + (long)e * NT;
+        vv[k][e] = (i0 + k < jj && p < L) ? v[p] : C{};
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const C a = ca[i0 + k], gm = cg[i0 + k];   // vv is zero past v_{j-1}: padded terms vanish
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const C t1 = cmul(a, vv[k][e]), t2 = cmul(gm, vv[k][e]);
+        qv[e].x -= t1.x; qv[e].y -= t1.y;
+        x[e].x -= t2.x; x[e].y -= t2.y;
+      }
+    }
+  }
+  const C gj = cg[jj];
+  T nr = 0;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const long p = b0 + (long)e * NT;
+    if (p < L) {
+      C q = qv[e]; q.x *= ir; q.y *= ir;
+      const C t = cmul(gj, q);
+      C xx = x[e]; xx.x -= t.x; xx.y -= t.y;
+      uj[p] = q; wj[p] = xx;
+      nr += xx.x * xx.x + xx.y * xx.y;
+    }
+  }
+  const double t = block_sum((double)nr, red);
+  if (threadIdx.x == 0) atomicAdd(&part_at(g.part, s, 2, blockIdx.x % NSTRIPE, 0)->x, t);
 }
 
 // v_0 *= scale (start of a cycle)
@@ -744,37 +799,30 @@ __global__ void __launch_bounds__(NT) k_init_systems(GV<T> g) {
   }
 }
 
-// E += sum_{i < jend} y_i z_i  (FP64 accumulation) for systems at a cycle end.
+// Cycle end, first half of e += M^-1 V y: Tmp = sum_{i < jend} y_i v_i for the
+// systems at a cycle end (the free-space solve and the FP64 accumulation into E
+// follow as an FFT round trip with the EPI_ADD_E epilogue).
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_update_e(GV<T> g) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(NT) k_combine(GV<T> g) {
+  using C = typename Cx<T>::t;
+  __shared__ C ys[MMAX];
   const int s = blockIdx.y;
   const SysState& st = g.st[s];
   if (st.state != ST_CYCLE_END) return;
   const int J = st.jend;
-  const long L = (long)g.ncomp * g.npts;
-  double2* e = g.E + (long)s * L;
-  using C = typename Cx<T>::t;
-  __shared__ C ys[MMAX];
   for (int i = threadIdx.x; i < J; i += NT) { ys[i].x = (T)st.y[i].x; ys[i].y = (T)st.y[i].y; }
   __syncthreads();
-  // the increment sum_i y_i z_i is formed in T, then added once to the FP64 correction
-  T nr = 0;
+  const long L = (long)g.ncomp * g.npts;
+  C* t = g.Tmp + (long)s * L;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
     C inc; inc.x = 0; inc.y = 0;
     #pragma unroll 4
     for (int i = 0; i < J; ++i) {
-      const C t = cmul(ys[i], g.Zb[((long)s * g.m + i) * L + p]);
-      inc.x += t.x; inc.y += t.y;
+      const C a = cmul(ys[i], vslot(g, s, i)[p]);
+      inc.x += a.x; inc.y += a.y;
     }
-    double2 a = e[p];
-    a.x += (double)inc.x; a.y += (double)inc.y;
-    e[p] = a;
-    const T ax = (T)a.x, ay = (T)a.y;
-    nr += ax * ax + ay * ay;
+    t[p] = inc;
   }
-  const double t = block_sum((double)nr, red);
-  if (threadIdx.x == 0) atomicAdd(&g.st[s].enorm2, t);
 }
 
 // Wn[b] += sum_k r_k E[b, k]  (the residue sum of Eq. approx_prop, correction part).
@@ -911,96 +959,297 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double dabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
-// After the dots of Arnoldi column jj: form h, rotate with the previous Givens
-// rotations, make the new one, update g and the residual estimate |g[jj+1]|;
-// end the cycle on convergence, breakdown or jj+1 == m (solving R y = g).
-// One block per system: the block first folds the striped accumulators into
-// dots1, dots2 and nrm_b (clearing the stripes), then thread 0 does the rest.
-__global__ void k_arnoldi_finish(SysState* st, int nsys, int P, const double* bnorm2, double tol,
-                                 int m, int jj, double breakdown, const double* anorm, int backward,
-                                 double2* part) {
-  for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
-    SysState& q = st[s];
-    if (q.state != ST_ITER) continue;
-    for (int i = threadIdx.x; i <= jj; i += blockDim.x) {
-      double2 a = make_double2(0.0, 0.0), b = a;
-      for (int k = 0; k < NSTRIPE; ++k) {
-        double2* pa = part_at(part, s, 0, k, i);
-        double2* pb = part_at(part, s, 1, k, i);
-        a.x += pa->x; a.y += pa->y; b.x += pb->x; b.y += pb->y;
-        *pa = make_double2(0.0, 0.0); *pb = make_double2(0.0, 0.0);
-      }
-      q.dots1[i] = a; q.dots2[i] = b;
-    }
-    if (threadIdx.x == 0) {
-      double nb = 0.0;
-      for (int k = 0; k < NSTRIPE; ++k) { double2* pn = part_at(part, s, 2, k, 0); nb += pn->x; *pn = make_double2(0.0, 0.0); }
-      q.nrm_b = nb;
+// Apply the Givens rotation (c, sn) to the pair (x, y) of one column.
+__device__ __forceinline__ void givens_apply(double c, double2 sn, double2& x, double2& y) {
+  const double2 a = x, b = y;
+  x = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
+  const double2 t = dmul(dconj(sn), a);
+  y = make_double2(c * b.x - t.x, c * b.y - t.y);
+}
+// Rotation zeroing y against x; x becomes the rotated diagonal, y zero.
+__device__ __forceinline__ void givens_make(double2& x, double2& y, double& c, double2& sn) {
+  const double an = sqrt(dabs2(x)), hn = sqrt(dabs2(y));
+  const double r = sqrt(an * an + hn * hn);
+  if (hn == 0.0) { c = 1.0; sn = make_double2(0.0, 0.0); }
+  else if (an == 0.0) { c = 0.0; sn = make_double2(y.x / hn, -y.y / hn); }
+  else {
+    c = an / r;
+    // sn = (x/|x|) conj(y) / r, so that -conj(sn) x + c y = 0
+    const double2 ux = make_double2(x.x / an, x.y / an);
+    sn = make_double2((ux.x * y.x + ux.y * y.y) / r, (ux.y * y.x - ux.x * y.y) / r);
+  }
+  x = (an == 0.0) ? make_double2(hn, 0.0) : make_double2(x.x / an * r, x.y / an * r);
+  y = make_double2(0.0, 0.0);
+}
+
+// Packed upper triangle of the rotated columns 0..MMAX-1: column i holds rows 0..i.
+constexpr int RPACK = MMAX * (MMAX + 1) / 2;
+__device__ __forceinline__ int rp(int row, int col) { return col * (col + 1) / 2 + row; }
+
+// Back substitution R y = g over the rotated columns 0..J-1, by the whole block
+// (column-oriented: after y_i is known every thread updates its rows), from a
+// shared-memory copy of R; ends the cycle.  Rs must hold columns 0..J-1 packed
+// and acc the right-hand side g[0..J-1].
+__device__ void end_cycle_block(SysState& q, int J, double2* Rs, double2* acc) {
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int i = J - 1; i >= 0; --i) {
+    if (tid == 0) {
+      const double2 d = Rs[rp(i, i)], a = acc[i];
+      const double dd = dabs2(d);
+      acc[i] = make_double2((a.x * d.x + a.y * d.y) / dd, (a.y * d.x - a.x * d.y) / dd);
     }
     __syncthreads();
-    if (threadIdx.x != 0) continue;
-    const int L = MMAX + 1;
-    double2* col = &q.H[jj * L];
-    double d2 = 0.0;
-    for (int i = 0; i <= jj; ++i) {
-      col[i] = make_double2(q.dots1[i].x + q.dots2[i].x, q.dots1[i].y + q.dots2[i].y);
-      d2 += dabs2(q.dots2[i]);
-      q.coef[i] = q.dots2[i];
+    const double2 y = acc[i];
+    for (int k = tid; k < i; k += blockDim.x) {
+      const double2 t = dmul(Rs[rp(k, i)], y);
+      acc[k].x -= t.x; acc[k].y -= t.y;
     }
-    const double hn = sqrt(fmax(q.nrm_b - d2, 0.0));
-    col[jj + 1] = make_double2(hn, 0.0);
-    // previous rotations
-    for (int i = 0; i < jj; ++i) {
-      const double2 a = col[i], b = col[i + 1];
-      const double c = q.cs[i];
-      const double2 sn = q.sn[i];
-      col[i] = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
-      const double2 t = dmul(dconj(sn), a);
-      col[i + 1] = make_double2(c * b.x - t.x, c * b.y - t.y);
+    __syncthreads();
+  }
+  for (int i = tid; i < J; i += blockDim.x) q.y[i] = acc[i];
+  if (tid == 0) {
+    q.jend = J;
+    q.enorm2 = 0.0;          // recomputed by the correction update
+    q.state = ST_CYCLE_END;
+  }
+}
+
+// Stage rotated columns 0..J-1 of q.H (column c <= J-1 from global, except that
+// column `own` comes from `owncol`) and g[0..J-1] (g[ownrow..] overridden by
+// gown[]) for end_cycle_block.
+__device__ void stage_ls(const SysState& q, int J, int own, const double2* owncol, int ownrow, const double2* gown,
+                         double2* Rs, double2* acc) {
+  constexpr int L = MMAX + 1;
+  for (int c = 0; c < J; ++c)
+    for (int r = threadIdx.x; r <= c; r += blockDim.x) Rs[rp(r, c)] = (c == own) ? owncol[r] : q.H[r + c * L];
+  for (int i = threadIdx.x; i < J; i += blockDim.x) acc[i] = i >= ownrow ? gown[i - ownrow] : q.g[i];
+}
+
+// ---------------------------------------------------------------------------
+// Arnoldi with delayed re-orthogonalisation (the DCGS2 scheme of Swirydowicz,
+// Langou, Ananthan, Yang and Thomas, 2020, and Bielich et al., 2022), right-
+// preconditioned: B = (Z - p) M^-1.  At iteration j, v_0..v_{j-1} are final and
+// orthonormal and u = v_j is the candidate, projected once.  The Arnoldi
+// epilogue forms w = B u; k_dcgs_gram the products a_i = <v_i, u>,
+// b_i = <v_i, w> (i < j), c = <u, u>, d = <u, w>.  Then, with rho^2 = c - sum |a_i|^2:
+//   q_j = (u - V a) / rho  re-orthogonalises u, which finalises Hessenberg
+//     column j-1:  h_{i,j-1} += a_i,  h_{j,j-1} = rho;
+//   B q_j = (w - V_{j+1} t) / rho,  t = Hbar a over the final columns, so the
+//     first projection of B q_j gives column j:
+//     h_{i,j} = (b_i - t_i)/rho (i < j),  h_{j,j} = (d - a^H b)/rho^2 - t_j/rho;
+//   u_{j+1} = (I - V_{j+1} V_{j+1}^H) w / rho
+//           = w/rho - sum_{i<j} (b_i/rho) v_i - ((d - a^H b)/rho^2) q_j,
+//     and h_{j+1,j} = ||u_{j+1}|| until the next iteration finalises it.
+// Per iteration the basis is swept twice (products, update) instead of four
+// times for classical Gram-Schmidt run twice.
+//
+// The control kernels below run one block per system.  GB300 issues FP64 at a
+// small fraction of its FP32 rate and a lone thread's global round trips are
+// long, so each kernel stages everything it reads into shared memory with
+// parallel loads, lets thread 0 run the serial Givens work there, and writes
+// back in parallel.
+// ---------------------------------------------------------------------------
+
+// Finish of the products: finalise column j-1 and redo its Givens rotation,
+// form column j's first projection and the update-pass coefficients.
+__global__ void __launch_bounds__(128) k_dcgs_finish(SysState* st, int jj, double2* part) {
+  constexpr int L = MMAX + 1;
+  __shared__ double2 a[MMAX + 1], b[MMAX + 1], t[MMAX + 1], hu[MMAX + 1], col[MMAX + 1], sn_s[MMAX];
+  __shared__ double2 Rs[RPACK], acc[MMAX + 1];
+  __shared__ double cs_s[MMAX];
+  __shared__ double rho_s, nw_s;
+  __shared__ double2 ahb_s, gsave_s, g0_s, gout[2];
+  __shared__ int code_s;
+  const int s = blockIdx.x, j = jj, tid = threadIdx.x;
+  SysState& q = st[s];
+  if (q.state != ST_ITER) return;
+  // fold the stripes: thread (plane, i) loads all NSTRIPE copies at once, then clears them
+  for (int t2 = tid; t2 < 2 * (j + 1) + 1; t2 += blockDim.x) {
+    const int plane = t2 < j + 1 ? 0 : 1;
+    const int i = t2 == 2 * (j + 1) ? MMAX : (plane == 0 ? t2 : t2 - (j + 1));
+    double2 x[NSTRIPE];
+#pragma unroll
+    for (int k = 0; k < NSTRIPE; ++k) x[k] = *part_at(part, s, plane, k, i);
+    double2 sum = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < NSTRIPE; ++k) { sum.x += x[k].x; sum.y += x[k].y; *part_at(part, s, plane, k, i) = make_double2(0.0, 0.0); }
+    if (i == MMAX) nw_s = sum.x;
+    else if (plane == 0) b[i] = sum;
+    else a[i] = sum;
+  }
+  for (int i = tid; i + 1 < j; i += blockDim.x) { cs_s[i] = q.cs[i]; sn_s[i] = q.sn[i]; }
+  if (j >= 1) for (int i = tid; i < j; i += blockDim.x) hu[i] = q.Hu[i + (j - 1) * L];
+  if (tid == blockDim.x - 1) { gsave_s = q.gsave; g0_s = q.g[0]; }
+  __syncthreads();
+  if (tid < 32) {
+    double s2 = 0.0, hr = 0.0, hi = 0.0;
+    for (int i = tid; i < j; i += 32) {
+      s2 += dabs2(a[i]);
+      hr += a[i].x * b[i].x + a[i].y * b[i].y;
+      hi += a[i].x * b[i].y - a[i].y * b[i].x;
     }
-    // new rotation zeroing col[jj+1]
-    const double2 a = col[jj];
-    const double an = sqrt(dabs2(a));
-    const double r = sqrt(an * an + hn * hn);
-    double c; double2 sn;
-    if (hn == 0.0) { c = 1.0; sn = make_double2(0.0, 0.0); }
-    else if (an == 0.0) { c = 0.0; sn = make_double2(1.0, 0.0); }
-    else { c = an / r; sn = make_double2(a.x / an * hn / r, a.y / an * hn / r); }
-    q.cs[jj] = c; q.sn[jj] = sn;
-    col[jj] = (an == 0.0) ? make_double2(hn, 0.0) : make_double2(a.x / an * r, a.y / an * r);
-    col[jj + 1] = make_double2(0.0, 0.0);
-    const double2 gj = q.g[jj];
-    q.g[jj] = make_double2(c * gj.x, c * gj.y);
-    const double2 t = dmul(dconj(sn), gj);
-    q.g[jj + 1] = make_double2(-t.x, -t.y);
-    q.iters += 1;
-    q.j = jj + 1;
-    const double est = sqrt(dabs2(q.g[jj + 1]));
-    const double wn = sqrt(bnorm2[s / P]);
-    for (int i = 0; i <= jj + 1; ++i) { q.dots1[i] = make_double2(0.0, 0.0); q.dots2[i] = q.dots1[i]; }
-    const double nb = q.nrm_b;
-    q.nrm_b = 0.0;
-    if (!isfinite(est) || !isfinite(hn)) { q.flags |= 1; q.state = ST_DONE; continue; }
-    if (est <= conv_threshold(q, tol, wn, anorm, s % P, P, backward) || jj + 1 == m ||
-        hn <= breakdown * sqrt(fmax(nb, 0.0)) || hn == 0.0) {
-      const int J = jj + 1;
-      for (int i = J - 1; i >= 0; --i) {
-        double2 acc = q.g[i];
-        for (int k2 = i + 1; k2 < J; ++k2) {
-          const double2 t2 = dmul(q.H[k2 * L + i], q.y[k2]);
-          acc.x -= t2.x; acc.y -= t2.y;
-        }
-        const double2 d = q.H[i * L + i];
-        const double dd = dabs2(d);
-        q.y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
-      }
-      q.jend = J;
-      q.enorm2 = 0.0;          // recomputed by the correction update
-      q.state = ST_CYCLE_END;
-    } else {
-      q.scale = 1.0 / hn;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+      hr += __shfl_down_sync(0xffffffffu, hr, o);
+      hi += __shfl_down_sync(0xffffffffu, hi, o);
+    }
+    if (tid == 0) {
+      const double r2 = a[j].x - s2;
+      ahb_s = make_double2(hr, hi);
+      rho_s = sqrt(fmax(r2, 0.0));
+      // 0: go on; 1: NaN; 2: the candidate vanished against the basis (breakdown at column j-1)
+      code_s = (!isfinite(r2) || !isfinite(hr) || !isfinite(hi) || !isfinite(nw_s)) ? 1 : (r2 > 0.0 ? 0 : 2);
     }
   }
+  __syncthreads();
+  if (code_s == 1) { if (tid == 0) { q.flags |= 1; q.state = ST_DONE; } return; }
+  if (code_s == 2) {   // columns 0..j-1 stand as they are (only a zero candidate gets here at j = 0)
+    if (j == 0) { if (tid == 0) { q.flags |= 1; q.state = ST_DONE; } return; }
+    stage_ls(q, j, -1, nullptr, j, nullptr, Rs, acc);
+    end_cycle_block(q, j, Rs, acc);
+    return;
+  }
+  const double rho = rho_s, ir = 1.0 / rho;
+  if (j >= 1) {
+    for (int i = tid; i <= j; i += blockDim.x) {
+      double2 h = i < j ? make_double2(hu[i].x + a[i].x, hu[i].y + a[i].y) : make_double2(rho, 0.0);
+      hu[i] = h;
+      col[i] = h;
+    }
+    __syncthreads();
+    if (tid == 0) {   // redo rotation j-1 on the final column
+      for (int i = 0; i + 1 < j; ++i) givens_apply(cs_s[i], sn_s[i], col[i], col[i + 1]);
+      double c; double2 sn;
+      givens_make(col[j - 1], col[j], c, sn);
+      cs_s[j - 1] = c; sn_s[j - 1] = sn;
+      const double2 gs = gsave_s;
+      gout[0] = make_double2(c * gs.x, c * gs.y);
+      const double2 t2 = dmul(dconj(sn), gs);
+      gout[1] = make_double2(-t2.x, -t2.y);
+    }
+    __syncthreads();
+    for (int i = tid; i <= j; i += blockDim.x) { q.H[i + (j - 1) * L] = col[i]; q.Hu[i + (j - 1) * L] = hu[i]; }
+    if (tid == 0) { q.cs[j - 1] = cs_s[j - 1]; q.sn[j - 1] = sn_s[j - 1]; q.g[j - 1] = gout[0]; q.g[j] = gout[1]; }
+  } else if (tid == 0) {
+    q.g[0] = make_double2(g0_s.x * rho, g0_s.y * rho);   // r = beta u_0 = beta rho q_0
+  }
+  for (int i = tid; i <= j; i += blockDim.x) {   // t = Hbar a over the final columns 0..j-1
+    double2 sum = make_double2(0.0, 0.0);
+    for (int k = i > 0 ? i - 1 : 0; k < j; ++k) {
+      const double2 h = (k == j - 1) ? hu[i] : q.Hu[i + k * L];
+      const double2 m2 = dmul(h, a[k]);
+      sum.x += m2.x; sum.y += m2.y;
+    }
+    t[i] = sum;
+  }
+  const double2 ahb = ahb_s, d = b[j];
+  const double2 gj = make_double2((d.x - ahb.x) * ir * ir, (d.y - ahb.y) * ir * ir);
+  for (int i = tid; i <= j; i += blockDim.x) {
+    double2 h;
+    if (i < j) {
+      h = make_double2((b[i].x - t[i].x) * ir, (b[i].y - t[i].y) * ir);
+      q.coef[i] = make_double2(b[i].x * ir, b[i].y * ir);
+      q.dots2[i] = a[i];
+    } else {
+      h = make_double2(gj.x - t[i].x * ir, gj.y - t[i].y * ir);
+      q.coef[i] = gj;
+    }
+    q.Hu[i + j * L] = h;
+  }
+  if (tid == 0) { q.scale = ir; q.nrm_b = nw_s * ir * ir; }
+}
+
+// After the update pass: h_{j+1,j} = ||u_{j+1}||, rotate column j with the
+// previous rotations, make rotation j, update g and the residual estimate
+// |g[j+1]|; end the cycle on convergence, breakdown or j+1 == m (the last
+// column stays as first projected: u_{j+1} is not needed).  The last block to
+// finish (ticket) then writes the state counts of k_count.
+__global__ void __launch_bounds__(64) k_dcgs_check(SysState* st, int nsys, int P, const double* bnorm2, double tol,
+                                                   int m, int jj, double breakdown, const double* anorm,
+                                                   int backward, double2* part, int* counts, int* ticket) {
+  constexpr int L = MMAX + 1;
+  __shared__ double2 col[MMAX + 2], sn_s[MMAX], xs[NSTRIPE], gout[2], gs_s;
+  __shared__ double2 Rs[RPACK], acc[MMAX + 1];
+  __shared__ double cs_s[MMAX], sc[8];
+  __shared__ int code_s, last_s;
+  const int s = blockIdx.x, j = jj, tid = threadIdx.x;
+  SysState& q = st[s];
+  const bool active = q.state == ST_ITER;
+  if (active) {
+    for (int i = tid; i <= j; i += blockDim.x) col[i] = q.Hu[i + j * L];
+    for (int i = tid; i < j; i += blockDim.x) { cs_s[i] = q.cs[i]; sn_s[i] = q.sn[i]; }
+    if (tid < NSTRIPE) { double2* p = part_at(part, s, 2, tid, 0); xs[tid] = *p; *p = make_double2(0.0, 0.0); }
+    const int k = s % P;
+    if (tid == 32) gs_s = q.g[j];
+    if (tid == 33) sc[2] = q.nrm_b;
+    if (tid == 34) sc[3] = sqrt(bnorm2[s / P]);
+    if (tid == 35) sc[4] = q.z0norm2;
+    if (tid == 36) sc[5] = q.enorm2;
+    if (tid == 37) sc[6] = anorm[k];
+    if (tid == 38) sc[7] = anorm[P + k];
+    __syncthreads();
+    if (tid == 0) {
+      double hn2 = 0.0;
+      for (int k2 = 0; k2 < NSTRIPE; ++k2) hn2 += xs[k2].x;
+      const double hn = sqrt(fmax(hn2, 0.0));
+      col[j + 1] = make_double2(hn, 0.0);
+      for (int i = 0; i < j; ++i) givens_apply(cs_s[i], sn_s[i], col[i], col[i + 1]);
+      double c; double2 sn;
+      givens_make(col[j], col[j + 1], c, sn);
+      cs_s[j] = c; sn_s[j] = sn;
+      const double2 gs = gs_s;
+      gout[0] = make_double2(c * gs.x, c * gs.y);
+      const double2 t2 = dmul(dconj(sn), gs);
+      gout[1] = make_double2(-t2.x, -t2.y);
+      const double est = sqrt(dabs2(gout[1]));
+      const double wn = sc[3];
+      // conv_threshold on the staged values
+      const double thr = backward ? tol * sc[7] * (wn + sc[6] * (sqrt(sc[4]) + sqrt(sc[5]))) : tol * wn;
+      if (!isfinite(est) || !isfinite(hn)) code_s = 1;
+      else if (est <= thr || j + 1 == m || hn <= breakdown * sqrt(fmax(sc[2], 0.0)) || hn == 0.0) code_s = 2;
+      else code_s = 0;
+      sc[0] = hn;
+    }
+    __syncthreads();
+    if (code_s == 1) {
+      if (tid == 0) { q.flags |= 1; q.state = ST_DONE; }
+    } else {
+      for (int i = tid; i <= j + 1; i += blockDim.x) q.H[i + j * L] = col[i];
+      if (tid == 0) {
+        q.Hu[j + 1 + j * L] = make_double2(sc[0], 0.0);
+        q.cs[j] = cs_s[j]; q.sn[j] = sn_s[j];
+        q.gsave = gs_s;
+        q.g[j] = gout[0]; q.g[j + 1] = gout[1];
+        q.iters += 1;
+        q.j = j + 1;
+      }
+      if (code_s == 2) {
+        stage_ls(q, j + 1, j, col, j, gout, Rs, acc);
+        end_cycle_block(q, j + 1, Rs, acc);
+      }
+    }
+  }
+  // last block: count the states (every block's writes are visible after its fence)
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last_s = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  __shared__ int c0, c1, c2;
+  if (tid == 0) { c0 = 0; c1 = 0; c2 = 0; }
+  __syncthreads();
+  for (int k = tid; k < nsys; k += blockDim.x) {
+    const volatile SysState* vs = st + k;
+    const int stt = vs->state, fl = vs->flags;
+    if (stt == ST_ITER) atomicAdd(&c0, 1);
+    if (stt == ST_CYCLE_END) atomicAdd(&c1, 1);
+    if (fl) atomicOr(&c2, fl);
+  }
+  __syncthreads();
+  if (tid == 0) { counts[0] = c0; counts[1] = c1; counts[2] = c2; *ticket = 0; }
 }
 
 // ---------------------------------------------------------------------------

@@ -49,11 +49,11 @@ constexpr int clamp_nt(int t) { return t < 64 ? 64 : (t > 256 ? 256 : t); }
 template <int N> constexpr int rows_nt() { return clamp_nt(rows_nr<N>() * N / 16); }
 template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * cols_per_cta<T>() / 16); }
 constexpr int NT_VEC = 256;
-constexpr int EPT_CGS = 8;
+constexpr int EPT_GS = 2;   // points per thread of the Gram-Schmidt sweeps
 constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host reads of the GMRES state
 
 struct Layout {
-  size_t V, Zb, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
+  size_t V, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
       rk, anorm, part, psi, Tmp2, poles, act0, act1, netout, stage, iters, cycles, resid, flags, end;
 };
 
@@ -111,7 +111,6 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
   size_t o = align_up(base);
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
   L.V = take(nsys * (m + 1) * C * npts * cs);
-  L.Zb = take(nsys * m * C * npts * cs);
   L.R0 = take(nsys * C * npts * cs);
   L.E = take(nsys * C * npts * 16);
   L.Tmp = take(nsys * C * npts * cs);
@@ -154,7 +153,7 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   GV<T> g;
   g.nx = G.nx; g.ny = G.ny; g.ncomp = h->C; g.P = h->P; g.m = h->m;
   g.nb = (int)G.beams.size(); g.nsys = g.nb * h->P; g.npts = G.npts;
-  g.V = (C*)(b + L.V); g.Zb = (C*)(b + L.Zb); g.R0 = (C*)(b + L.R0); g.E = (double2*)(b + L.E);
+  g.V = (C*)(b + L.V); g.R0 = (C*)(b + L.R0); g.E = (double2*)(b + L.E);
   g.Tmp = (C*)(b + L.Tmp);
   g.W64 = (double2*)(b + (G.cur == 0 ? L.W64a : L.W64b));
   g.What = (C*)(b + L.What); g.Btmp = (C*)(b + L.Btmp); g.delta = (C*)(b + L.delta);
@@ -207,9 +206,10 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
   using C = typename Cx<T>::t;
   constexpr int NR = rows_nr<N>(), NT = rows_nt<N>();
   const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
-  auto k = k_rows_inv<T, N, NR, NT>;
-  static bool attr = false;
-  cudaError_t e = set_smem_once(k, sm, attr);
+  const bool arn = ep.mode == EPI_ARNOLDI;
+  auto k = arn ? k_rows_inv<T, N, NR, NT, true> : k_rows_inv<T, N, NR, NT, false>;
+  static bool attr[2] = {false, false};
+  cudaError_t e = set_smem_once(k, sm, attr[arn ? 1 : 0]);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units * g.ncomp);
   k<<<grid, NT, sm, st>>>(g, src, dst, mask, skip, ep);
@@ -423,12 +423,12 @@ template <typename T> int upload_group_tables(prop* h, Group& G) {
 // ---------------------------------------------------------------------------
 // Launch accounting
 // ---------------------------------------------------------------------------
-enum Kind { K_ROWS_FWD, K_COLS, K_ROWS_INV, K_FIELD_IO, K_CGS, K_NORMALIZE, K_UPDATE_E, K_RESIDUE, K_MEDIUM,
+enum Kind { K_ROWS_FWD, K_COLS, K_ROWS_INV, K_FIELD_IO, K_GRAM, K_GS_UPDATE, K_COMBINE, K_RESIDUE, K_MEDIUM,
             K_CONTROL, K_INIT, K_SCALE, K_GUESS };
 const char* kind_name(int k) {
-  static const char* n[PROP_NKINDS] = {"rows_fwd", "cols", "rows_inv", "field_io", "cgs", "normalize",
-                                       "update_e", "residue_sum", "medium", "control", "init_systems",
-                                       "scale_v0", "guess_net"};
+  static const char* n[PROP_NKINDS] = {"rows_fwd", "cols", "rows_inv", "field_io", "gram", "gs_update", "combine",
+                                       "residue_sum", "medium", "control", "init_systems", "scale_v0",
+                                       "guess_net"};
   return n[k];
 }
 
@@ -493,7 +493,8 @@ template <typename T> int step_group(prop* h, Group& G) {
   double2* Wn = (double2*)(h->ws + (G.cur == 0 ? G.off.W64b : G.off.W64a));
   const int tb = 128, tg = (nsys + tb - 1) / tb;
   const int vb = vec_blocks(F);
-  const int cgs_blocks = (int)((F + NT_VEC * EPT_CGS - 1) / (NT_VEC * EPT_CGS));
+  const int gs_blocks = (int)((F + NT_VEC * EPT_GS - 1) / (NT_VEC * EPT_GS));
+  int* ticket = counts + 3 * (MMAX + 2) - 1;   // last-block ticket of k_dcgs_check (self-resetting)
 
   // which beams carry a non-zero delta (read back once per medium change)
   if (G.medium_dirty) {
@@ -660,15 +661,15 @@ template <typename T> int step_group(prop* h, Group& G) {
         { Prof p_(h, K_ROWS_INV, 0);
           CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
       }
-      { Prof p_(h, K_CGS, 0);
-        k_cgs<T, NT_VEC, EPT_CGS><<<dim3(cgs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
+      { Prof p_(h, K_GRAM, 0);
+        k_dcgs_gram<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CONTROL, 0);
-        k_arnoldi_finish<<<nsys, 64, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown, g.anorm, bw,
-                                               g.part); }
-      { Prof p_(h, K_NORMALIZE, 0);
-        k_normalize<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g, jj); }
+        k_dcgs_finish<<<nsys, 128, 0, st>>>(g.st, jj, g.part); }
+      { Prof p_(h, K_GS_UPDATE, 0);
+        k_dcgs_update<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
       { Prof p_(h, K_CONTROL, 0);
-        k_count<<<1, 256, 0, st>>>(g.st, nsys, counts + 3 * (jj - jj0 + 1)); }
+        k_dcgs_check<<<nsys, 64, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown, g.anorm, bw, g.part,
+                                          counts + 3 * (jj - jj0 + 1), ticket); }
       CK(cudaGetLastError());
       const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj + 1 == m;
       if (!sync_now) continue;
@@ -684,9 +685,10 @@ template <typename T> int step_group(prop* h, Group& G) {
         const double cont = (double)cnt[3 * (b2 + 1)] * Cn * pts;   // systems that continued after it
         h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
         h->k_bytes[K_COLS] += (Cn == 2 ? 3 : 2) * cs * act;
-        h->k_bytes[K_ROWS_INV] += (Cn == 2 ? (8.5 + j) : (5.0 + j)) * cs * act;
-        h->k_bytes[K_CGS] += (2.0 * (j + 1) + 2) * cs * act;
-        h->k_bytes[K_NORMALIZE] += (j + 3) * cs * cont;
+        h->k_bytes[K_ROWS_INV] += (Cn == 2 ? 6.5 : 4.0) * cs * act;
+        h->k_bytes[K_GRAM] += (j + 2.0) * cs * act;         // v_0..v_{j-1}, u, w read
+        h->k_bytes[K_GS_UPDATE] += (j + 4.0) * cs * act;   // v_0..v_{j-1}, u, w read; q_j, u_{j+1} written
+        (void)cont;
         h->total_iters += cnt[3 * b2];
       }
       c3[0] = cnt[3 * nb]; c3[1] = cnt[3 * nb + 1]; c3[2] = cnt[3 * nb + 2];
@@ -696,10 +698,17 @@ template <typename T> int step_group(prop* h, Group& G) {
       if (c3[0] == 0) break;
     }
     if (c3[1] == 0) break;
-    // cycle end: e += M^-1 V y (stored z_j); true residual r = R0 - (Z - p) e
+    // cycle end: e += M^-1 (V y) (Tmp = V y, then a free-space solve round trip
+    // accumulating into E); true residual r = R0 - (Z - p) e
     const double endp = (double)c3[1] * Cn * pts;
-    { Prof p_(h, K_UPDATE_E, (32 + m * cs) * endp);   // upper bound on the z_j read: J <= m
-      k_update_e<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    { Prof p_(h, K_COMBINE, (1 + m) * cs * endp);   // upper bound on the v_i read: J <= m
+      k_combine<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    { Prof p_(h, K_ROWS_FWD, 2 * cs * endp);
+      CK(rows_fwd<T, C>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
+    { Prof p_(h, K_COLS, 2 * cs * endp);
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
+    { Prof p_(h, K_ROWS_INV, (cs + 32) * endp);
+      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_ADD_E), nsys, st)); }
     if (Cn == 2) {   // (Z - Z_fs) e into v_0, from a derivative round trip of e
       { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
         CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
