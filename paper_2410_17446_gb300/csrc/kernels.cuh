@@ -33,22 +33,19 @@ struct SysState {
   double z0norm2, enorm2;                     // ||z_k||^2 (free-space solve), ||e_k||^2
   double2 r0r;                                // <R0, r> of the last true-residual pass
   double2 g[MMAX + 1];             // Givens-rotated right-hand side beta e_1
-  double2 gsave;                    // g[j] before rotation j (rotation j is redone when column j is final)
   double2 sn[MMAX];
   double cs[MMAX];
   double2 H[(MMAX + 1) * MMAX];     // rotated (upper-triangular) columns, H[i + j*(MMAX+1)]
   double2 Hu[(MMAX + 1) * MMAX];    // Hessenberg columns as built (same indexing)
   double2 y[MMAX];
-  double2 dots1[MMAX + 1];          // <v_i, w>
-  double2 dots2[MMAX + 1];          // <v_i, u_j>: the delayed re-orthogonalisation coefficients
-  double2 coef[MMAX + 1];           // projection coefficients of the next candidate
+  double2 coef[MMAX + 1];           // coef[0]: the learned guess's scale alpha
 };
 
 template <typename T> struct GV {
   using C = typename Cx<T>::t;
   int nx, ny, ncomp, P, m, nb, nsys;
   long npts;
-  C* V;          // [nsys][m+1][ncomp][npts]  Krylov basis
+  C* V;          // [nsys][m+2][ncomp][npts]  Krylov basis (slot j+1 takes w = B v_j up to j = m)
   C* R0;         // [nsys][ncomp][npts]       right-hand side of the correction system
   double2* E;    // [nsys][ncomp][npts]       correction e_k, FP64
   C* Tmp;        // [nsys][ncomp][npts]       FFT intermediate
@@ -69,8 +66,8 @@ template <typename T> struct GV {
   const double2* rk;    // [P] residues r_k
   const double* anorm;  // [2P]: bound on ||Z - p_k I|| over this grid (backward-error test), then the
                         //       per-pole tolerance factor mu_k >= 1 (error equidistribution)
-  double2* part;        // [nsys][3][NSTRIPE][MMAX+1] striped accumulators: <v_i, w>, <v_i, u_j>
-                        //   (slot MMAX: ||w||^2), plane 2 slot 0: ||u_{j+1}||^2
+  double2* part;        // [nsys][4][NSTRIPE][MMAX+1] striped accumulators of the Gram sweep,
+                        //   plane 2 (j % 2) + {0: <v_i, w>, 1: <v_i, u_j> (slot MMAX: ||w||^2)}
   // vector operator (ncomp = 2) only
   C* psi;        // [nb][5][npts]  coefficients of Z - Z_fs: D1 = delta + psit_xx, D2 = delta + psit_yy,
                  //                X = psit_xy, px = psit_x, py = psit_y (psit = psi/(k0 n0)^2, psi = Log n^2)
@@ -87,9 +84,10 @@ template <typename C, typename T> __device__ __forceinline__ C ik_factor(int i, 
   return f;
 }
 
-// striped accumulator slot: plane 0 = <v_i, w>, 1 = <v_i, u_j>, 2 = candidate norm
+// striped accumulator slot: plane 2 (j % 2) + 0 = <v_i, w>, + 1 = <v_i, u_j>
+constexpr int NPLANE = 4;
 __device__ __forceinline__ double2* part_at(double2* part, int s, int plane, int stripe, int i) {
-  return part + (((long)s * 3 + plane) * NSTRIPE + stripe) * (MMAX + 1) + i;
+  return part + (((long)s * NPLANE + plane) * NSTRIPE + stripe) * (MMAX + 1) + i;
 }
 
 // Which buffer a pass reads or writes: item (unit u, component c) lives at
@@ -389,7 +387,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     // Arnoldi step: u = v_j (the candidate left by the last update pass),
     // z = M^-1 u from this transform, w = u + delta z stored as v_{j+1}; the
     // inner products follow in k_dcgs_gram.
-    const long vj = (((long)u * (g.m + 1) + ep.jj) * g.ncomp + c) * g.npts + off;
+    const long vj = (((long)u * (g.m + 2) + ep.jj) * g.ncomp + c) * g.npts + off;
 #pragma unroll
     for (int e = threadIdx.x; e < NR * N; e += NT) {
       const C val = s[sidx<N, NR, false>(e / N, e % N)];
@@ -454,7 +452,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
       } break;
       case EPI_TRUERES: {
         const double2 r0 = to_d(g.R0[unit_off + e]);
-        const long vb = (((long)u * (g.m + 1)) * g.ncomp + c) * g.npts + off + e;
+        const long vb = (((long)u * (g.m + 2)) * g.ncomp + c) * g.npts + off + e;
         double2 r;
         if (g.ncomp == 2) {   // (Z - Z_fs) e was written into v_0 by the preceding pass
           const double2 a = to_d(g.V[vb]);
@@ -561,7 +559,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
     t = cmul(px, y1); d2.x += t.x; d2.y += t.y;
     t = cmul(py, y2); d2.x += t.x; d2.y += t.y;
     if (mode == VEPI_ARNOLDI) {   // w = u + (Z - Z_fs) M^-1 u, stored as v_{j+1}
-      const long vj = ((long)u * (g.m + 1) + jj) * F + off + e;
+      const long vj = ((long)u * (g.m + 2) + jj) * F + off + e;
       const C v1 = g.V[vj], v2 = g.V[vj + g.npts];
       C w1, w2;
       w1.x = v1.x + d1.x; w1.y = v1.y + d1.y;
@@ -606,7 +604,7 @@ __global__ void __launch_bounds__(NT) k_psi_combine(GV<T> g, int beam) {
 // contiguous chunk of the system's ncomp*npts points.
 // ---------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ typename Cx<T>::t* vslot(const GV<T>& g, int s, int jj) {
-  return g.V + ((long)s * (g.m + 1) + jj) * g.ncomp * g.npts;
+  return g.V + ((long)s * (g.m + 2) + jj) * g.ncomp * g.npts;
 }
 
 // Sum each of 32 per-lane values over the warp: on return v[0] of lane l holds
@@ -627,14 +625,16 @@ template <typename A> __device__ __forceinline__ void warp_transpose_reduce(A (&
 }
 
 // The inner products of iteration j of the delayed re-orthogonalisation (see
-// k_dcgs_finish): b_i = <v_i, w>, a_i = <v_i, u> (i < j), d = <u, w>, c = <u, u>
-// and ||w||^2, with u = v_j and w = v_{j+1}, for every iterating system.  Each
+// the scheme before dcgs_control): b_i = <v_i, w>, a_i = <v_i, u> (i < j), d = <u, w>, c = <u, u>
+// and ||w||^2, with u = v_j and w = v_{j+1} (w = 0 when with_w = 0: the last
+// step of a cycle needs only the products with u), for every iterating system.  Each
 // thread keeps EPT points of u and w in registers and takes the basis in
 // groups of 8 vectors (8*EPT loads in flight); a group's 32 partial sums leave
 // the warp in one transpose-reduce.  Per-warp totals are summed in FP64 and
-// added to the striped accumulators (planes 0 and 1; slot MMAX of plane 1 takes ||w||^2).
+// added to the striped accumulators (planes 2 (j % 2) + 0, 1; slot MMAX of the
+// second takes ||w||^2).
 template <typename T, int NT, int EPT>
-__global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj) {
+__global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   using C = typename Cx<T>::t;
   constexpr int NW = NT / 32;
   __shared__ T red[NW][4 * (MMAX + 1)];
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj) {
   for (int e = 0; e < EPT; ++e) {
     const long p = b0 + (long)e * NT;
     uv[e] = C{}; wv[e] = C{};
-    if (p < L) { uv[e] = up[p]; wv[e] = wpv[p]; }
+    if (p < L) { uv[e] = up[p]; if (with_w) wv[e] = wpv[p]; }
     uwr += uv[e].x * wv[e].x + uv[e].y * wv[e].y; uwi += uv[e].x * wv[e].y - uv[e].y * wv[e].x;
     uu += uv[e].x * uv[e].x + uv[e].y * uv[e].y;
     ww += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
@@ -684,8 +684,8 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj) {
     if (g0 + (lane >> 2) <= jj) red[wp][4 * g0 + lane] = acc[0];
   }
   __syncthreads();
-  double2* pb = part_at(g.part, s, 0, blockIdx.x % NSTRIPE, 0);
-  double2* pa = part_at(g.part, s, 1, blockIdx.x % NSTRIPE, 0);
+  double2* pb = part_at(g.part, s, 2 * (jj & 1), blockIdx.x % NSTRIPE, 0);
+  double2* pa = part_at(g.part, s, 2 * (jj & 1) + 1, blockIdx.x % NSTRIPE, 0);
   for (int t = threadIdx.x; t < 4 * (jj + 1); t += NT) {
     double v = 0.0;
 #pragma unroll
@@ -697,77 +697,6 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj) {
     else if (i < jj) atomicAdd(&pa[i].y, v);
     else atomicAdd(&pa[MMAX].x, v);   // ||w||^2
   }
-}
-
-// Update pass of the delayed re-orthogonalisation (see k_dcgs_finish):
-//   q_j     = (u - sum_{i<j} a_i v_i) / rho                  (written over u = v_j)
-//   u_{j+1} = w / rho - sum_{i<j} gamma_i v_i - gamma_j q_j  (written over w = v_{j+1})
-// with a_i = dots2[i], gamma_i = coef[i], 1/rho = scale; adds ||u_{j+1}||^2 to
-// the norm accumulator.  One sweep over v_0..v_{j-1} in groups of 8 vectors
-// (8*EPT loads in flight per thread); each CTA owns NT*EPT points.
-template <typename T, int NT, int EPT>
-__global__ void __launch_bounds__(NT) k_dcgs_update(GV<T> g, int jj) {
-  using C = typename Cx<T>::t;
-  __shared__ C ca[MMAX + 8], cg[MMAX + 8];
-  __shared__ double red[32];
-  const int s = blockIdx.y;
-  if (g.st[s].state != ST_ITER) return;
-  for (int i = threadIdx.x; i < jj + 8; i += NT) {
-    C a{}, c{};
-    if (i <= jj) { const double2 d = g.st[s].coef[i]; c.x = (T)d.x; c.y = (T)d.y; }
-    if (i < jj) { const double2 d = g.st[s].dots2[i]; a.x = (T)d.x; a.y = (T)d.y; }
-    ca[i] = a; cg[i] = c;
-  }
-  __syncthreads();
-  const T ir = (T)g.st[s].scale;
-  const long L = (long)g.ncomp * g.npts;
-  C* uj = vslot(g, s, jj);
-  C* wj = vslot(g, s, jj + 1);
-  const long b0 = (long)blockIdx.x * NT * EPT + threadIdx.x;
-  C qv[EPT], x[EPT];
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const long p = b0 + (long)e * NT;
-    qv[e] = C{}; x[e] = C{};
-    if (p < L) { qv[e] = uj[p]; const C w = wj[p]; x[e].x = w.x * ir; x[e].y = w.y * ir; }
-  }
-  for (int i0 = 0; i0 < jj; i0 += 8) {
-    C vv[8][EPT];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const C* v = vslot(g, s, i0 + k);
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const long p = b0 + (long)e * NT;
-        vv[k][e] = (i0 + k < jj && p < L) ? v[p] : C{};
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const C a = ca[i0 + k], gm = cg[i0 + k];   // vv is zero past v_{j-1}: padded terms vanish
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const C t1 = cmul(a, vv[k][e]), t2 = cmul(gm, vv[k][e]);
-        qv[e].x -= t1.x; qv[e].y -= t1.y;
-        x[e].x -= t2.x; x[e].y -= t2.y;
-      }
-    }
-  }
-  const C gj = cg[jj];
-  T nr = 0;
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const long p = b0 + (long)e * NT;
-    if (p < L) {
-      C q = qv[e]; q.x *= ir; q.y *= ir;
-      const C t = cmul(gj, q);
-      C xx = x[e]; xx.x -= t.x; xx.y -= t.y;
-      uj[p] = q; wj[p] = xx;
-      nr += xx.x * xx.x + xx.y * xx.y;
-    }
-  }
-  const double t = block_sum((double)nr, red);
-  if (threadIdx.x == 0) atomicAdd(&part_at(g.part, s, 2, blockIdx.x % NSTRIPE, 0)->x, t);
 }
 
 // v_0 *= scale (start of a cycle)
@@ -782,6 +711,8 @@ __global__ void __launch_bounds__(NT) k_scale_v0(GV<T> g) {
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < L; p += (long)gridDim.x * NT) {
     C x = w[p]; x.x *= sc; x.y *= sc; w[p] = x;
   }
+  if (blockIdx.x == 0)   // the cycle's Gram accumulators start from zero
+    for (int i = threadIdx.x; i < NPLANE * NSTRIPE * (MMAX + 1); i += NT) part_at(g.part, s, 0, 0, 0)[i] = make_double2(0.0, 0.0);
 }
 
 // v_0 = R0 and E = 0 for the systems that start iterating (the others keep E unused).
@@ -949,7 +880,7 @@ __global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm
     q.state = ST_ITER;
     q.j = 0;
     q.scale = 1.0 / beta;
-    for (int i = 0; i <= MMAX; ++i) { q.g[i] = make_double2(0.0, 0.0); q.dots1[i] = q.g[i]; q.dots2[i] = q.g[i]; }
+    for (int i = 0; i <= MMAX; ++i) q.g[i] = make_double2(0.0, 0.0);
     q.g[0] = make_double2(beta, 0.0);
     q.nrm_b = 0.0;
   }
@@ -1029,7 +960,7 @@ __device__ void stage_ls(const SysState& q, int J, int own, const double2* ownco
 // ---------------------------------------------------------------------------
 // Arnoldi with delayed re-orthogonalisation (the DCGS2 scheme of Swirydowicz,
 // Langou, Ananthan, Yang and Thomas, 2020, and Bielich et al., 2022), right-
-// preconditioned: B = (Z - p) M^-1.  At iteration j, v_0..v_{j-1} are final and
+// preconditioned: B = (Z - p) M^-1.  At step j, v_0..v_{j-1} are final and
 // orthonormal and u = v_j is the candidate, projected once.  The Arnoldi
 // epilogue forms w = B u; k_dcgs_gram the products a_i = <v_i, u>,
 // b_i = <v_i, w> (i < j), c = <u, u>, d = <u, w>.  Then, with rho^2 = c - sum |a_i|^2:
@@ -1039,55 +970,65 @@ __device__ void stage_ls(const SysState& q, int J, int own, const double2* ownco
 //     first projection of B q_j gives column j:
 //     h_{i,j} = (b_i - t_i)/rho (i < j),  h_{j,j} = (d - a^H b)/rho^2 - t_j/rho;
 //   u_{j+1} = (I - V_{j+1} V_{j+1}^H) w / rho
-//           = w/rho - sum_{i<j} (b_i/rho) v_i - ((d - a^H b)/rho^2) q_j,
-//     and h_{j+1,j} = ||u_{j+1}|| until the next iteration finalises it.
-// Per iteration the basis is swept twice (products, update) instead of four
-// times for classical Gram-Schmidt run twice.
+//           = w/rho - sum_{i<j} (b_i/rho) v_i - ((d - a^H b)/rho^2) q_j.
+// Column j-1 becomes final only at step j, so its Givens rotation and the
+// convergence test for the j-column solution happen there (one operator
+// application past the converged column, and at j = m only the products with
+// u are formed).  Per step the basis is swept twice (products, update) instead
+// of four times for classical Gram-Schmidt run twice.
 //
-// The control kernels below run one block per system.  GB300 issues FP64 at a
-// small fraction of its FP32 rate and a lone thread's global round trips are
-// long, so each kernel stages everything it reads into shared memory with
-// parallel loads, lets thread 0 run the serial Givens work there, and writes
-// back in parallel.
+// The FP64 control runs in one extra CTA of the update kernel, beside the
+// sweep: GB300 issues FP64 at a small fraction of its FP32 rate, so its serial
+// Givens chain would otherwise sit on the critical path.  It stages what it
+// reads in shared memory with parallel loads and writes back in parallel.
 // ---------------------------------------------------------------------------
 
-// Finish of the products: finalise column j-1 and redo its Givens rotation,
-// form column j's first projection and the update-pass coefficients.
-__global__ void __launch_bounds__(128) k_dcgs_finish(SysState* st, int jj, double2* part) {
+// Control of step j for one system (one block, FP64), concurrent with the
+// update sweep of the other CTAs: finalise Hessenberg column j-1 with the
+// re-orthogonalisation products, rotate it (rotations 0..j-2, then a new one),
+// update g and test |g[j]| -- the residual of the J = j column solution -- for
+// convergence; end the cycle then (or at j = m, or when u_j vanished); else
+// form column j's first projection.  Also clears the other parity's
+// accumulators (last read by step j-1, next written by the Gram sweep of j+1)
+// and adds this system to the iteration's counts.
+struct StepArgs {
+  int m, P, backward;
+  double tol, breakdown;
+  const double* bnorm2;
+  const double* anorm;
+  int* counts;   // this iteration's slot: [0] continuing, [1] ending the cycle, [2] flags
+};
+
+__device__ void dcgs_control(SysState& q, int s, int j, const double2* bs, const double2* as, double nw,
+                             double2* part, const StepArgs& A) {
   constexpr int L = MMAX + 1;
-  __shared__ double2 a[MMAX + 1], b[MMAX + 1], t[MMAX + 1], hu[MMAX + 1], col[MMAX + 1], sn_s[MMAX];
+  __shared__ double2 hu[MMAX + 1], col[MMAX + 1], tt[MMAX + 1], sn_s[MMAX], gout[2], gj_s, g0_s, ahb_s;
   __shared__ double2 Rs[RPACK], acc[MMAX + 1];
-  __shared__ double cs_s[MMAX];
-  __shared__ double rho_s, nw_s;
-  __shared__ double2 ahb_s, gsave_s, g0_s, gout[2];
+  __shared__ double cs_s[MMAX], sc[6], rho_s;
   __shared__ int code_s;
-  const int s = blockIdx.x, j = jj, tid = threadIdx.x;
-  SysState& q = st[s];
-  if (q.state != ST_ITER) return;
-  // fold the stripes: thread (plane, i) loads all NSTRIPE copies at once, then clears them
-  for (int t2 = tid; t2 < 2 * (j + 1) + 1; t2 += blockDim.x) {
-    const int plane = t2 < j + 1 ? 0 : 1;
-    const int i = t2 == 2 * (j + 1) ? MMAX : (plane == 0 ? t2 : t2 - (j + 1));
-    double2 x[NSTRIPE];
-#pragma unroll
-    for (int k = 0; k < NSTRIPE; ++k) x[k] = *part_at(part, s, plane, k, i);
-    double2 sum = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int k = 0; k < NSTRIPE; ++k) { sum.x += x[k].x; sum.y += x[k].y; *part_at(part, s, plane, k, i) = make_double2(0.0, 0.0); }
-    if (i == MMAX) nw_s = sum.x;
-    else if (plane == 0) b[i] = sum;
-    else a[i] = sum;
-  }
-  for (int i = tid; i + 1 < j; i += blockDim.x) { cs_s[i] = q.cs[i]; sn_s[i] = q.sn[i]; }
+  const int tid = threadIdx.x, par = j & 1;
   if (j >= 1) for (int i = tid; i < j; i += blockDim.x) hu[i] = q.Hu[i + (j - 1) * L];
-  if (tid == blockDim.x - 1) { gsave_s = q.gsave; g0_s = q.g[0]; }
-  __syncthreads();
+  for (int i = tid; i + 1 < j; i += blockDim.x) { cs_s[i] = q.cs[i]; sn_s[i] = q.sn[i]; }
+  const int k = s % A.P;
+  if (tid == 32) gj_s = j >= 1 ? q.g[j - 1] : q.g[0];
+  if (tid == 33) sc[0] = q.nrm_b;
+  if (tid == 34) sc[1] = sqrt(A.bnorm2[s / A.P]);
+  if (tid == 35) sc[2] = q.z0norm2;
+  if (tid == 36) sc[3] = q.enorm2;
+  if (tid == 37) sc[4] = A.anorm[k];
+  if (tid == 38) sc[5] = A.anorm[A.P + k];
+  // clear the other parity (slots 0..j-1 and MMAX were written by the Gram sweep of step j-1)
+  for (int t2 = tid; t2 < 2 * NSTRIPE * (j + 1); t2 += blockDim.x) {
+    const int pl = t2 / (NSTRIPE * (j + 1)), r = t2 % (NSTRIPE * (j + 1));
+    const int stripe = r / (j + 1), i0 = r % (j + 1);
+    *part_at(part, s, 2 * (1 - par) + pl, stripe, i0 < j ? i0 : MMAX) = make_double2(0.0, 0.0);
+  }
   if (tid < 32) {
     double s2 = 0.0, hr = 0.0, hi = 0.0;
     for (int i = tid; i < j; i += 32) {
-      s2 += dabs2(a[i]);
-      hr += a[i].x * b[i].x + a[i].y * b[i].y;
-      hi += a[i].x * b[i].y - a[i].y * b[i].x;
+      s2 += dabs2(as[i]);
+      hr += as[i].x * bs[i].x + as[i].y * bs[i].y;
+      hi += as[i].x * bs[i].y - as[i].y * bs[i].x;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1096,160 +1037,193 @@ __global__ void __launch_bounds__(128) k_dcgs_finish(SysState* st, int jj, doubl
       hi += __shfl_down_sync(0xffffffffu, hi, o);
     }
     if (tid == 0) {
-      const double r2 = a[j].x - s2;
+      const double r2 = as[j].x - s2;
       ahb_s = make_double2(hr, hi);
       rho_s = sqrt(fmax(r2, 0.0));
-      // 0: go on; 1: NaN; 2: the candidate vanished against the basis (breakdown at column j-1)
-      code_s = (!isfinite(r2) || !isfinite(hr) || !isfinite(hi) || !isfinite(nw_s)) ? 1 : (r2 > 0.0 ? 0 : 2);
+      // 0: go on; 1: NaN; 2: u_j vanished against the basis
+      code_s = (!isfinite(r2) || !isfinite(hr) || !isfinite(hi) || !isfinite(nw)) ? 1 : (r2 > 0.0 ? 0 : 2);
     }
   }
   __syncthreads();
-  if (code_s == 1) { if (tid == 0) { q.flags |= 1; q.state = ST_DONE; } return; }
-  if (code_s == 2) {   // columns 0..j-1 stand as they are (only a zero candidate gets here at j = 0)
-    if (j == 0) { if (tid == 0) { q.flags |= 1; q.state = ST_DONE; } return; }
-    stage_ls(q, j, -1, nullptr, j, nullptr, Rs, acc);
-    end_cycle_block(q, j, Rs, acc);
+  int code = code_s;
+  if (code == 1 || (code == 2 && j == 0)) {
+    if (tid == 0) { q.flags |= 1; q.state = ST_DONE; atomicOr(&A.counts[2], 1); }
     return;
   }
-  const double rho = rho_s, ir = 1.0 / rho;
+  const double rho = rho_s;
   if (j >= 1) {
     for (int i = tid; i <= j; i += blockDim.x) {
-      double2 h = i < j ? make_double2(hu[i].x + a[i].x, hu[i].y + a[i].y) : make_double2(rho, 0.0);
+      const double2 h = i < j ? make_double2(hu[i].x + as[i].x, hu[i].y + as[i].y) : make_double2(rho, 0.0);
       hu[i] = h;
       col[i] = h;
     }
     __syncthreads();
-    if (tid == 0) {   // redo rotation j-1 on the final column
+    if (tid == 0) {   // column j-1 is final: rotations 0..j-2, then rotation j-1
       for (int i = 0; i + 1 < j; ++i) givens_apply(cs_s[i], sn_s[i], col[i], col[i + 1]);
       double c; double2 sn;
       givens_make(col[j - 1], col[j], c, sn);
       cs_s[j - 1] = c; sn_s[j - 1] = sn;
-      const double2 gs = gsave_s;
-      gout[0] = make_double2(c * gs.x, c * gs.y);
-      const double2 t2 = dmul(dconj(sn), gs);
-      gout[1] = make_double2(-t2.x, -t2.y);
-    }
-    __syncthreads();
-    for (int i = tid; i <= j; i += blockDim.x) { q.H[i + (j - 1) * L] = col[i]; q.Hu[i + (j - 1) * L] = hu[i]; }
-    if (tid == 0) { q.cs[j - 1] = cs_s[j - 1]; q.sn[j - 1] = sn_s[j - 1]; q.g[j - 1] = gout[0]; q.g[j] = gout[1]; }
-  } else if (tid == 0) {
-    q.g[0] = make_double2(g0_s.x * rho, g0_s.y * rho);   // r = beta u_0 = beta rho q_0
-  }
-  for (int i = tid; i <= j; i += blockDim.x) {   // t = Hbar a over the final columns 0..j-1
-    double2 sum = make_double2(0.0, 0.0);
-    for (int k = i > 0 ? i - 1 : 0; k < j; ++k) {
-      const double2 h = (k == j - 1) ? hu[i] : q.Hu[i + k * L];
-      const double2 m2 = dmul(h, a[k]);
-      sum.x += m2.x; sum.y += m2.y;
-    }
-    t[i] = sum;
-  }
-  const double2 ahb = ahb_s, d = b[j];
-  const double2 gj = make_double2((d.x - ahb.x) * ir * ir, (d.y - ahb.y) * ir * ir);
-  for (int i = tid; i <= j; i += blockDim.x) {
-    double2 h;
-    if (i < j) {
-      h = make_double2((b[i].x - t[i].x) * ir, (b[i].y - t[i].y) * ir);
-      q.coef[i] = make_double2(b[i].x * ir, b[i].y * ir);
-      q.dots2[i] = a[i];
-    } else {
-      h = make_double2(gj.x - t[i].x * ir, gj.y - t[i].y * ir);
-      q.coef[i] = gj;
-    }
-    q.Hu[i + j * L] = h;
-  }
-  if (tid == 0) { q.scale = ir; q.nrm_b = nw_s * ir * ir; }
-}
-
-// After the update pass: h_{j+1,j} = ||u_{j+1}||, rotate column j with the
-// previous rotations, make rotation j, update g and the residual estimate
-// |g[j+1]|; end the cycle on convergence, breakdown or j+1 == m (the last
-// column stays as first projected: u_{j+1} is not needed).  The last block to
-// finish (ticket) then writes the state counts of k_count.
-__global__ void __launch_bounds__(64) k_dcgs_check(SysState* st, int nsys, int P, const double* bnorm2, double tol,
-                                                   int m, int jj, double breakdown, const double* anorm,
-                                                   int backward, double2* part, int* counts, int* ticket) {
-  constexpr int L = MMAX + 1;
-  __shared__ double2 col[MMAX + 2], sn_s[MMAX], xs[NSTRIPE], gout[2], gs_s;
-  __shared__ double2 Rs[RPACK], acc[MMAX + 1];
-  __shared__ double cs_s[MMAX], sc[8];
-  __shared__ int code_s, last_s;
-  const int s = blockIdx.x, j = jj, tid = threadIdx.x;
-  SysState& q = st[s];
-  const bool active = q.state == ST_ITER;
-  if (active) {
-    for (int i = tid; i <= j; i += blockDim.x) col[i] = q.Hu[i + j * L];
-    for (int i = tid; i < j; i += blockDim.x) { cs_s[i] = q.cs[i]; sn_s[i] = q.sn[i]; }
-    if (tid < NSTRIPE) { double2* p = part_at(part, s, 2, tid, 0); xs[tid] = *p; *p = make_double2(0.0, 0.0); }
-    const int k = s % P;
-    if (tid == 32) gs_s = q.g[j];
-    if (tid == 33) sc[2] = q.nrm_b;
-    if (tid == 34) sc[3] = sqrt(bnorm2[s / P]);
-    if (tid == 35) sc[4] = q.z0norm2;
-    if (tid == 36) sc[5] = q.enorm2;
-    if (tid == 37) sc[6] = anorm[k];
-    if (tid == 38) sc[7] = anorm[P + k];
-    __syncthreads();
-    if (tid == 0) {
-      double hn2 = 0.0;
-      for (int k2 = 0; k2 < NSTRIPE; ++k2) hn2 += xs[k2].x;
-      const double hn = sqrt(fmax(hn2, 0.0));
-      col[j + 1] = make_double2(hn, 0.0);
-      for (int i = 0; i < j; ++i) givens_apply(cs_s[i], sn_s[i], col[i], col[i + 1]);
-      double c; double2 sn;
-      givens_make(col[j], col[j + 1], c, sn);
-      cs_s[j] = c; sn_s[j] = sn;
-      const double2 gs = gs_s;
+      const double2 gs = gj_s;
       gout[0] = make_double2(c * gs.x, c * gs.y);
       const double2 t2 = dmul(dconj(sn), gs);
       gout[1] = make_double2(-t2.x, -t2.y);
       const double est = sqrt(dabs2(gout[1]));
-      const double wn = sc[3];
-      // conv_threshold on the staged values
-      const double thr = backward ? tol * sc[7] * (wn + sc[6] * (sqrt(sc[4]) + sqrt(sc[5]))) : tol * wn;
-      if (!isfinite(est) || !isfinite(hn)) code_s = 1;
-      else if (est <= thr || j + 1 == m || hn <= breakdown * sqrt(fmax(sc[2], 0.0)) || hn == 0.0) code_s = 2;
+      const double wn = sc[1];
+      const double thr = A.backward ? A.tol * sc[5] * (wn + sc[4] * (sqrt(sc[2]) + sqrt(sc[3]))) : A.tol * wn;
+      if (!isfinite(est)) code_s = 1;
+      else if (code == 2 || est <= thr || j == A.m || rho <= A.breakdown * sqrt(fmax(sc[0], 0.0))) code_s = 3;
       else code_s = 0;
-      sc[0] = hn;
     }
     __syncthreads();
-    if (code_s == 1) {
-      if (tid == 0) { q.flags |= 1; q.state = ST_DONE; }
-    } else {
-      for (int i = tid; i <= j + 1; i += blockDim.x) q.H[i + j * L] = col[i];
-      if (tid == 0) {
-        q.Hu[j + 1 + j * L] = make_double2(sc[0], 0.0);
-        q.cs[j] = cs_s[j]; q.sn[j] = sn_s[j];
-        q.gsave = gs_s;
-        q.g[j] = gout[0]; q.g[j + 1] = gout[1];
-        q.iters += 1;
-        q.j = j + 1;
+    code = code_s;
+    if (code == 1) {
+      if (tid == 0) { q.flags |= 1; q.state = ST_DONE; atomicOr(&A.counts[2], 1); }
+      return;
+    }
+    for (int i = tid; i <= j; i += blockDim.x) { q.H[i + (j - 1) * L] = col[i]; q.Hu[i + (j - 1) * L] = hu[i]; }
+    if (tid == 0) {
+      q.cs[j - 1] = cs_s[j - 1]; q.sn[j - 1] = sn_s[j - 1];
+      q.g[j - 1] = gout[0]; q.g[j] = gout[1];
+      q.iters += 1;
+      q.j = j;
+    }
+    if (code == 3) {
+      stage_ls(q, j, j - 1, col, j - 1, gout, Rs, acc);
+      end_cycle_block(q, j, Rs, acc);
+      if (tid == 0) atomicAdd(&A.counts[1], 1);
+      return;
+    }
+  } else if (tid == 0) {
+    q.g[0] = make_double2(gj_s.x * rho, gj_s.y * rho);   // r = beta u_0 = beta rho q_0
+  }
+  // first projection of B q_j: column j (rows 0..j; row j+1 comes with step j+1)
+  for (int i = tid; i <= j; i += blockDim.x) {   // t = Hbar a over the final columns 0..j-1
+    double2 sum = make_double2(0.0, 0.0);
+    for (int k2 = i > 0 ? i - 1 : 0; k2 < j; ++k2) {
+      const double2 h = (k2 == j - 1) ? hu[i] : q.Hu[i + k2 * L];
+      const double2 m2 = dmul(h, as[k2]);
+      sum.x += m2.x; sum.y += m2.y;
+    }
+    tt[i] = sum;
+  }
+  const double ir = 1.0 / rho;
+  const double2 ahb = ahb_s, d = bs[j];
+  const double2 gj = make_double2((d.x - ahb.x) * ir * ir, (d.y - ahb.y) * ir * ir);
+  for (int i = tid; i <= j; i += blockDim.x)
+    q.Hu[i + j * L] = i < j ? make_double2((bs[i].x - tt[i].x) * ir, (bs[i].y - tt[i].y) * ir)
+                            : make_double2(gj.x - tt[i].x * ir, gj.y - tt[i].y * ir);
+  if (tid == 0) { q.nrm_b = nw * ir * ir; atomicAdd(&A.counts[0], 1); }
+}
+
+// Step j after its Gram sweep.  grid = (chunks + 1, nsys): chunk CTAs apply
+//   q_j     = (u - sum_{i<j} a_i v_i) / rho                  (written over u = v_j)
+//   u_{j+1} = w / rho - sum_{i<j} gamma_i v_i - gamma_j q_j  (written over w = v_{j+1})
+// gamma_i = b_i / rho (i < j), gamma_j = (d - a^H b) / rho^2, with coefficients
+// each CTA derives from the folded sums; the last CTA runs dcgs_control.
+// The sweep takes the basis in groups of 8 vectors (8*EPT loads in flight).
+// If the control ends the cycle at this step the sweep's output goes unused.
+template <typename T, int NT, int EPT>
+__global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
+  using C = typename Cx<T>::t;
+  __shared__ double2 bs[MMAX + 1], as[MMAX + 1];
+  __shared__ double nw_s;
+  __shared__ C ca[MMAX + 8], cg[MMAX + 8];
+  __shared__ T ir_s;
+  const int s = blockIdx.y, j = jj, tid = threadIdx.x;
+  SysState& q = g.st[s];
+  if (q.state != ST_ITER) return;
+  const int par = j & 1;
+  for (int t2 = tid; t2 < 2 * (j + 1) + 1; t2 += NT) {   // fold the stripes (read only)
+    const int plane = t2 < j + 1 ? 0 : 1;
+    const int i = t2 == 2 * (j + 1) ? MMAX : (plane == 0 ? t2 : t2 - (j + 1));
+    double2 x[NSTRIPE];
+#pragma unroll
+    for (int k = 0; k < NSTRIPE; ++k) x[k] = *part_at(g.part, s, 2 * par + plane, k, i);
+    double2 sum = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < NSTRIPE; ++k) { sum.x += x[k].x; sum.y += x[k].y; }
+    if (i == MMAX) nw_s = sum.x;
+    else if (plane == 0) bs[i] = sum;
+    else as[i] = sum;
+  }
+  __syncthreads();
+  if (blockIdx.x == gridDim.x - 1) { dcgs_control(q, s, j, bs, as, nw_s, g.part, A); return; }
+  if (j == A.m) return;   // the cycle ends at this step: nothing to sweep
+  // coefficients, in the working precision (the sums themselves are FP64)
+  if (tid < 32) {
+    T s2 = 0, hr = 0, hi = 0;
+    for (int i = tid; i < j; i += 32) {
+      const T ax = (T)as[i].x, ay = (T)as[i].y, bx = (T)bs[i].x, by = (T)bs[i].y;
+      s2 += ax * ax + ay * ay; hr += ax * bx + ay * by; hi += ax * by - ay * bx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+      hr += __shfl_down_sync(0xffffffffu, hr, o);
+      hi += __shfl_down_sync(0xffffffffu, hi, o);
+    }
+    if (tid == 0) {
+      const T r2 = (T)as[j].x - s2;
+      const T ir = r2 > (T)0 ? (T)1 / sqrt(r2) : (T)0;
+      ir_s = ir;
+      cg[j].x = ((T)bs[j].x - hr) * ir * ir; cg[j].y = ((T)bs[j].y - hi) * ir * ir;
+    }
+  }
+  __syncthreads();
+  const T ir = ir_s;
+  if (!(ir > (T)0)) return;   // u_j vanished: the control ends the cycle
+  for (int i = tid; i < j + 8; i += NT) {
+    if (i == j) continue;
+    C a{}, c{};
+    if (i < j) { a.x = (T)as[i].x; a.y = (T)as[i].y; c.x = (T)bs[i].x * ir; c.y = (T)bs[i].y * ir; }
+    ca[i] = a; cg[i] = c;
+  }
+  if (tid == 0) { ca[j].x = 0; ca[j].y = 0; }
+  __syncthreads();
+  const long L = (long)g.ncomp * g.npts;
+  C* uj = vslot(g, s, jj);
+  C* wj = vslot(g, s, jj + 1);
+  const long b0 = (long)blockIdx.x * NT * EPT + tid;
+  C qv[EPT], x[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const long p = b0 + (long)e * NT;
+    qv[e] = C{}; x[e] = C{};
+    if (p < L) { qv[e] = uj[p]; const C w = wj[p]; x[e].x = w.x * ir; x[e].y = w.y * ir; }
+  }
+  for (int i0 = 0; i0 < jj; i0 += 8) {
+    C vv[8][EPT];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const C* v = vslot(g, s, i0 + k);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const long p = b0 + (long)e * NT;
+        vv[k][e] = (i0 + k < jj && p < L) ? v[p] : C{};
       }
-      if (code_s == 2) {
-        stage_ls(q, j + 1, j, col, j, gout, Rs, acc);
-        end_cycle_block(q, j + 1, Rs, acc);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const C a = ca[i0 + k], gm = cg[i0 + k];   // vv is zero past v_{j-1}: padded terms vanish
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const C t1 = cmul(a, vv[k][e]), t2 = cmul(gm, vv[k][e]);
+        qv[e].x -= t1.x; qv[e].y -= t1.y;
+        x[e].x -= t2.x; x[e].y -= t2.y;
       }
     }
   }
-  // last block: count the states (every block's writes are visible after its fence)
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) last_s = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
-  __syncthreads();
-  if (!last_s) return;
-  __threadfence();
-  __shared__ int c0, c1, c2;
-  if (tid == 0) { c0 = 0; c1 = 0; c2 = 0; }
-  __syncthreads();
-  for (int k = tid; k < nsys; k += blockDim.x) {
-    const volatile SysState* vs = st + k;
-    const int stt = vs->state, fl = vs->flags;
-    if (stt == ST_ITER) atomicAdd(&c0, 1);
-    if (stt == ST_CYCLE_END) atomicAdd(&c1, 1);
-    if (fl) atomicOr(&c2, fl);
+  const C gj = cg[jj];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const long p = b0 + (long)e * NT;
+    if (p < L) {
+      C qq = qv[e]; qq.x *= ir; qq.y *= ir;
+      const C t = cmul(gj, qq);
+      C xx = x[e]; xx.x -= t.x; xx.y -= t.y;
+      uj[p] = qq; wj[p] = xx;
+    }
   }
-  __syncthreads();
-  if (tid == 0) { counts[0] = c0; counts[1] = c1; counts[2] = c2; *ticket = 0; }
 }
 
 // ---------------------------------------------------------------------------
@@ -1348,7 +1322,7 @@ __global__ void __launch_bounds__(NT) k_guess_apply(GV<T> g) {
   if (q.state != ST_CYCLE_END) return;
   const double2 a = q.coef[0];
   const long L = (long)g.ncomp * g.npts;
-  C* v = g.V + (long)s * (g.m + 1) * L;
+  C* v = g.V + (long)s * (g.m + 2) * L;
   const C* r0 = g.R0 + (long)s * L;
   double2* e = g.E + (long)s * L;
   const T ax = (T)a.x, ay = (T)a.y, bx = (T)(1.0 - a.x), by = (T)(-a.y);

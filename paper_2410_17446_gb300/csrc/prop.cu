@@ -110,7 +110,7 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
   Layout& L = G.off;
   size_t o = align_up(base);
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
-  L.V = take(nsys * (m + 1) * C * npts * cs);
+  L.V = take(nsys * (m + 2) * C * npts * cs);
   L.R0 = take(nsys * C * npts * cs);
   L.E = take(nsys * C * npts * 16);
   L.Tmp = take(nsys * C * npts * cs);
@@ -130,7 +130,7 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
   L.nonhomog = take(nb * sizeof(int));
   L.rk = take(P * 16);
   L.anorm = take(2 * P * sizeof(double));
-  L.part = take(nsys * 3 * NSTRIPE * (MMAX + 1) * sizeof(double2));
+  L.part = take(nsys * NPLANE * NSTRIPE * (MMAX + 1) * sizeof(double2));
   L.psi = take(C == 2 ? nb * 5 * npts * cs : 0);
   L.Tmp2 = take(C == 2 ? nsys * C * npts * cs : 0);
   L.poles = take(P * 16);
@@ -494,7 +494,6 @@ template <typename T> int step_group(prop* h, Group& G) {
   const int tb = 128, tg = (nsys + tb - 1) / tb;
   const int vb = vec_blocks(F);
   const int gs_blocks = (int)((F + NT_VEC * EPT_GS - 1) / (NT_VEC * EPT_GS));
-  int* ticket = counts + 3 * (MMAX + 2) - 1;   // last-block ticket of k_dcgs_check (self-resetting)
 
   // which beams carry a non-zero delta (read back once per medium change)
   if (G.medium_dirty) {
@@ -605,7 +604,7 @@ template <typename T> int step_group(prop* h, Group& G) {
         CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
                    Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
       { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
-        CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 1) * F), ST_CYCLE_END, 0,
+        CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 2) * F), ST_CYCLE_END, 0,
                            VEPI_OPDIFF, 0, nsys, st)); }
     }
     { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
@@ -635,68 +634,74 @@ template <typename T> int step_group(prop* h, Group& G) {
   }
   const double breakdown = sizeof(T) == 4 ? 1e-6 : 1e-14;
   while (c3[0] > 0) {
-    // Iterations are launched in batches of SYNC_EVERY between host reads: every
+    // Steps are launched in batches of SYNC_EVERY between host reads: every
     // kernel skips systems that have left ST_ITER, so launches past a cycle end
-    // are empty.  k_count records the active count after each iteration in its own
-    // slot, from which the algorithmic bytes of each launch are charged exactly.
-    int slot_base = 0;                       // slot holding the count before iteration jj0
-    std::vector<int> cnt(3 * (m + 2));
-    int jj0 = 0;
-    cnt[0] = c3[0];
-    for (int jj = 0; jj < m; ++jj) {
-      C* Vj = g.V + (long)jj * F;
-      const long vs = (long)(m + 1) * F;
-      { Prof p_(h, K_ROWS_FWD, 0);
-        CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st)); }
-      if (Cn == 2) {
-        { Prof p_(h, K_COLS, 0);
-          CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st,
-                     Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
-        { Prof p_(h, K_ROWS_INV, 0);
-          CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, nsys,
-                             st)); }
-      } else {
-        { Prof p_(h, K_COLS, 0);
-          CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
-        { Prof p_(h, K_ROWS_INV, 0);
-          CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
+    // are empty.  Each step's control adds its system to the step's count slot
+    // (continuing, ending the cycle, flags), zeroed at the batch start; the
+    // algorithmic bytes of each launch are charged from these counts exactly.
+    // Step j = m only finalises column m-1: no operator application, and the
+    // Gram sweep forms the products with u alone.
+    std::vector<int> cnt(3 * (SYNC_EVERY + 1));
+    int jj0 = 0, ended = 0, flags = 0, act0 = c3[0];
+    for (int jj = 0; jj <= m; ++jj) {
+      if (jj == jj0) CK(cudaMemsetAsync(counts + 3, 0, 3 * SYNC_EVERY * sizeof(int), st));
+      const bool op = jj < m;
+      if (op) {
+        C* Vj = g.V + (long)jj * F;
+        const long vs = (long)(m + 2) * F;
+        { Prof p_(h, K_ROWS_FWD, 0);
+          CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st)); }
+        if (Cn == 2) {
+          { Prof p_(h, K_COLS, 0);
+            CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st,
+                       Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+          { Prof p_(h, K_ROWS_INV, 0);
+            CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, nsys,
+                               st)); }
+        } else {
+          { Prof p_(h, K_COLS, 0);
+            CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
+          { Prof p_(h, K_ROWS_INV, 0);
+            CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
+        }
       }
       { Prof p_(h, K_GRAM, 0);
-        k_dcgs_gram<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
-      { Prof p_(h, K_CONTROL, 0);
-        k_dcgs_finish<<<nsys, 128, 0, st>>>(g.st, jj, g.part); }
+        k_dcgs_gram<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, nsys), NT_VEC, 0, st>>>(g, jj, op ? 1 : 0); }
       { Prof p_(h, K_GS_UPDATE, 0);
-        k_dcgs_update<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, nsys), NT_VEC, 0, st>>>(g, jj); }
-      { Prof p_(h, K_CONTROL, 0);
-        k_dcgs_check<<<nsys, 64, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, m, jj, breakdown, g.anorm, bw, g.part,
-                                          counts + 3 * (jj - jj0 + 1), ticket); }
+        StepArgs sa;
+        sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
+        sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = counts + 3 * (jj - jj0 + 1);
+        k_dcgs_step<T, NT_VEC, EPT_GS><<<dim3(gs_blocks + 1, nsys), NT_VEC, 0, st>>>(g, jj, sa); }
       CK(cudaGetLastError());
-      const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj + 1 == m;
+      const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj == m;
       if (!sync_now) continue;
-      // read the slots of this batch; slot 0 already holds the count before jj0
       const int nb = jj + 1 - jj0;
       if (cudaMemcpyAsync(cnt.data() + 3, counts + 3, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess)
         return PROP_E_CUDA;
       if (!h->pending.empty()) resolve_pending(h);
+      int before = act0;                                   // systems iterating at step j
       for (int b2 = 0; b2 < nb; ++b2) {
         const int j = jj0 + b2;
-        const double act = (double)cnt[3 * b2] * Cn * pts;          // systems iterating in iteration j
-        const double cont = (double)cnt[3 * (b2 + 1)] * Cn * pts;   // systems that continued after it
-        h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
-        h->k_bytes[K_COLS] += (Cn == 2 ? 3 : 2) * cs * act;
-        h->k_bytes[K_ROWS_INV] += (Cn == 2 ? 6.5 : 4.0) * cs * act;
-        h->k_bytes[K_GRAM] += (j + 2.0) * cs * act;         // v_0..v_{j-1}, u, w read
-        h->k_bytes[K_GS_UPDATE] += (j + 4.0) * cs * act;   // v_0..v_{j-1}, u, w read; q_j, u_{j+1} written
-        (void)cont;
-        h->total_iters += cnt[3 * b2];
+        const double act = (double)before * Cn * pts;
+        if (j < m) {
+          h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
+          h->k_bytes[K_COLS] += (Cn == 2 ? 3 : 2) * cs * act;
+          h->k_bytes[K_ROWS_INV] += (Cn == 2 ? 6.5 : 4.0) * cs * act;
+          h->k_bytes[K_GS_UPDATE] += (j + 4.0) * cs * act;   // v_0..v_{j-1}, u, w read; q_j, u_{j+1} written
+        }
+        h->k_bytes[K_GRAM] += (j + (j < m ? 2.0 : 1.0)) * cs * act;   // v_0..v_{j-1}, u (and w) read
+        if (j >= 1) h->total_iters += before;               // column j-1 finalised for each of them
+        const int* sl = cnt.data() + 3 * (b2 + 1);
+        ended += sl[1];
+        flags |= sl[2];
+        before = sl[0];
       }
-      c3[0] = cnt[3 * nb]; c3[1] = cnt[3 * nb + 1]; c3[2] = cnt[3 * nb + 2];
-      cnt[0] = c3[0];
+      act0 = before;
       jj0 = jj + 1;
-      (void)slot_base;
-      if (c3[0] == 0) break;
+      if (act0 == 0) break;
     }
+    c3[0] = 0; c3[1] = ended; c3[2] = flags;
     if (c3[1] == 0) break;
     // cycle end: e += M^-1 (V y) (Tmp = V y, then a free-space solve round trip
     // accumulating into E); true residual r = R0 - (Z - p) e
@@ -716,7 +721,7 @@ template <typename T> int step_group(prop* h, Group& G) {
         CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
                    Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
       { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
-        CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 1) * F), ST_CYCLE_END, 0,
+        CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 2) * F), ST_CYCLE_END, 0,
                            VEPI_OPDIFF, 0, nsys, st)); }
     }
     { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
