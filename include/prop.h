@@ -51,7 +51,10 @@ enum prop_status {
   PROP_E_NOCONV = 4,       /* GMRES hit max_restarts without reaching tol         */
   PROP_E_NAN = 5,          /* a residual norm became NaN or Inf                   */
   PROP_E_UNSUPPORTED = 6,  /* grid size / mode not compiled into this library     */
-  PROP_E_SCRATCH = 7       /* request exceeds the fixed scratch of prop_fft2_noalloc */
+  PROP_E_SCRATCH = 7,      /* request exceeds the fixed scratch of prop_fft2_noalloc */
+  PROP_E_TIMEOUT = 8       /* an asynchronous tile copy did not complete within its
+                              bounded wait; the kernel skipped its work (results of
+                              the affected step are invalid)                        */
 };
 
 enum prop_precision {

@@ -12,7 +12,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 SRC = [os.path.join(PKG, "csrc", "prop.cu"), os.path.join(PKG, "csrc", "cnn.cu")]
-DEPS = SRC + [os.path.join(PKG, "csrc", f) for f in ("fft.cuh", "kernels.cuh")] + [
+DEPS = SRC + [os.path.join(PKG, "csrc", f) for f in ("fft.cuh", "kernels.cuh", "tma.cuh")] + [
     os.path.join(ROOT, "include", h) for h in ("prop.h", "prop_cnn.h")]
 LIB = os.path.join(PKG, "libprop.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

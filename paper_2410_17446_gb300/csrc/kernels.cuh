@@ -17,6 +17,7 @@
 #pragma once
 #include <cuda_bf16.h>
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace prop_dev {
 
@@ -73,6 +74,7 @@ template <typename T> struct GV {
                  //                X = psit_xy, px = psit_x, py = psit_y (psit = psi/(k0 n0)^2, psi = Log n^2)
   C* Tmp2;       // [nsys][ncomp][npts] second column-pass output (the d/dy branch)
   T kx0, ky0;    // 2 pi/(nx dx), 2 pi/(ny dy): wavenumber of FFT index 1
+  int* err;      // error word: 1 = a bounded wait for an asynchronous copy gave up, 2 = TMA alignment check failed
 };
 
 // Signed FFT frequency index of position i on an n-point grid.
@@ -326,6 +328,100 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
       const int n = e / NV, v = e % NV;
       o2[(long)n * g.nx + x0 + v] = s[n * W + NV + v];
     }
+  }
+}
+
+// The column pass with its tiles moved by TMA: one thread issues the tensor
+// loads of the whole NY x NV tile (and of the multiplier tile for MUL_TABLE)
+// at entry, so every byte a CTA needs is in flight at once; the result leaves
+// by TMA tensor stores.  Same arithmetic as k_cols (no d/dy branch).  Tensor
+// maps view a buffer as [items][ny][nx] elements, item = unit * ncomp + c.
+template <typename T, int NY, int NV, int NT>
+__global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant__ CUtensorMap msrc,
+                                                 const __grid_constant__ CUtensorMap mdst,
+                                                 const __grid_constant__ CUtensorMap mtab, int mask, int fwd, int mul,
+                                                 int inv, int skip_homog, int pole, T scale,
+                                                 Buf<typename Cx<T>::t> spec) {
+  using C = typename Cx<T>::t;
+  constexpr int EW = sizeof(C) / 8;           // 8-byte words per element (tensor-map element size)
+  constexpr int BR = tma_box_rows(NY);        // rows per TMA box
+  static_assert(NY % BR == 0 && BR <= 256, "TMA boxes must tile the column");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA writes shared memory at 128-byte aligned addresses: align the tile at
+  // run time (the launch reserves 128 bytes of slack)
+  const uint32_t pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
+  C* s = reinterpret_cast<C*>(smem_raw + pad);
+  C* tab = s + NY * NV;                       // multiplier tile (MUL_TABLE)
+  __shared__ __align__(8) uint64_t bar;
+  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  if (!unit_active(g.st, mask, u)) return;
+  if (skip_homog && !g.nonhomog[u / g.P]) return;
+  const int x0 = blockIdx.x * NV;
+  // self-check of the TMA alignment rules: 128-byte shared destinations, 64-byte
+  // tensor maps, 16-byte x offsets; on a violation record it and do nothing
+  if ((smem_u32(s) & 127u) || (smem_u32(tab) & 127u) || (reinterpret_cast<uintptr_t>(&msrc) & 63u) ||
+      (reinterpret_cast<uintptr_t>(&mdst) & 63u) || (reinterpret_cast<uintptr_t>(&mtab) & 63u) ||
+      ((x0 * (int)sizeof(C)) & 15) || ((BR * NV * (int)sizeof(C)) & 127)) {
+    if (threadIdx.x == 0) atomicExch(g.err, 2);
+    return;
+  }
+  if (threadIdx.x == 0) { mbar_init(&bar, 1); fence_mbar_init(); }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, (uint32_t)(NY * NV * sizeof(C) * (mul == MUL_TABLE ? 2 : 1)));
+    for (int r = 0; r < NY; r += BR) {
+      tma_load_3d(s + r * NV, &msrc, x0 * EW, r, item, &bar);
+      if (mul == MUL_TABLE) tma_load_3d(tab + r * NV, &mtab, x0 * EW, r, 0, &bar);
+    }
+  }
+  if (!mbar_wait(&bar, 0, g.err)) { mbar_wait(&bar, 0, g.err); return; }
+  if (fwd) fft_smem<C, NY, false, NV, NT, true>(s, g.twy, threadIdx.x);
+  if (spec.base) {   // keep the 2-D spectrum as well (read again by the pole solves)
+    C* sp = spec.at(u, c, g.npts);
+#pragma unroll 8
+    for (int e = threadIdx.x; e < NY * NV; e += NT) sp[(long)(e / NV) * g.nx + x0 + e % NV] = s[e];
+  }
+  if (mul != MUL_NONE) {
+    const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD);
+    const int k = pm ? (pole >= 0 ? pole : u % g.P) : 0;
+    const T* ax = pm ? g.ax + (long)k * g.nx * 2 : nullptr;
+    const T* ay = pm ? g.ay + (long)k * g.ny * 2 : nullptr;
+    const T pim = pm ? g.pim[k] : (T)0;
+    for (int e = threadIdx.x; e < NY * NV; e += NT) {
+      const int n = e / NV, v = e % NV, i = x0 + v;
+      C a = s[e];
+      if (mul == MUL_TABLE) {
+        a = cmul(a, tab[e]);
+      } else if (mul == MUL_SCALE) {
+        a.x *= scale; a.y *= scale;
+      } else if (mul == MUL_DY) {
+        a = cmul(a, ik_factor<C>(n, g.ny, g.ky0));
+        a.x *= scale; a.y *= scale;
+      } else if (mul == MUL_DYY) {
+        const T kk = (T)ffreq(n, g.ny) * g.ky0;
+        a.x *= -kk * kk * scale; a.y *= -kk * kk * scale;
+      } else {   // as in k_cols: Re(zeta_fs - p) from (hi, lo) pairs
+        const T re = (ax[2 * i] + ay[2 * n]) + (ax[2 * i + 1] + ay[2 * n + 1]);
+        C f;
+        if (mul == MUL_POLE_INV) {
+          const T d = scale / (re * re + pim * pim);
+          f.x = re * d; f.y = -pim * d;
+        } else {
+          f.x = re * scale; f.y = pim * scale;
+        }
+        a = cmul(a, f);
+      }
+      s[e] = a;
+    }
+    __syncthreads();
+  }
+  if (inv) fft_smem<C, NY, true, NV, NT, true>(s, g.twy, threadIdx.x);
+  fence_proxy_async_smem();   // this thread's tile writes, before the TMA store reads them
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < NY; r += BR) tma_store_3d(&mdst, x0 * EW, r, item, s + r * NV);
+    bulk_commit();
+    bulk_wait_read();
   }
 }
 

@@ -51,6 +51,7 @@ template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * col
 constexpr int NT_VEC = 256;
 constexpr int EPT_GS = 2;   // points per thread of the Gram-Schmidt sweeps
 constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host reads of the GMRES state
+constexpr int ERR_SLOT = 3 * (MMAX + 2) - 1;   // int in the counts area: the asynchronous-copy error word
 
 struct Layout {
   size_t V, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
@@ -68,6 +69,9 @@ struct Group {
   bool stats_zero;         // per-system statistics already record a homogeneous step
   bool carry;              // Btmp holds the forward row DFT of the current field (from the last step)
   std::vector<int> nonhomog_host;
+  // TMA tensor maps of the column pass: Btmp [nb*C][ny][nx], Tmp [nsys*C][ny][nx], basemul [1][ny][nx]
+  bool tma;
+  CUtensorMap tm_btmp, tm_tmp, tm_tab;
 };
 
 }  // namespace
@@ -166,12 +170,49 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   g.part = (double2*)(b + L.part);
   g.psi = (C*)(b + L.psi);
   g.Tmp2 = (C*)(b + L.Tmp2);
+  g.err = (int*)(b + h->counts_off) + ERR_SLOT;
   g.kx0 = (T)(2.0 * M_PI / ((double)G.nx * G.dx));
   g.ky0 = (T)(2.0 * M_PI / ((double)G.ny * G.dy));
   return g;
 }
 
 template <typename C> Buf<C> buf(C* base, long ustride, int div = 1) { Buf<C> b; b.base = base; b.ustride = ustride; b.div = div; return b; }
+
+// ---------------------------------------------------------------------------
+// TMA tensor maps (driver entry point looked up once; no link against libcuda)
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// [items][ny][nx] complex elements of csz bytes (8 or 16), seen as 8-byte words;
+// box = nv elements x tma_box_rows(ny) rows x 1 item, as k_cols_tma loads it.
+bool make_col_map(CUtensorMap* m, void* base, int nx, int ny, long items, int csz, int nv) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || (csz != 8 && csz != 16) || ((uintptr_t)base % 16) != 0 || ((long)nv * csz) % 16 != 0) return false;
+  const int ew = csz / 8;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx * ew, (cuuint64_t)ny, (cuuint64_t)items};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * csz, (cuuint64_t)nx * ny * csz};
+  const cuuint32_t box[3] = {(cuuint32_t)(nv * ew), (cuuint32_t)tma_box_rows(ny), 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
 
 // ---------------------------------------------------------------------------
 // Launch dispatch over the compiled sizes
@@ -216,11 +257,30 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
   return cudaGetLastError();
 }
 
+// Tensor maps for a column pass: source, destination and (MUL_TABLE) multiplier.
+struct ColMaps { const CUtensorMap* src; const CUtensorMap* dst; const CUtensorMap* tab; };
+
 template <typename T, int NY, bool DY>
 cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
                     int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
-                    Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
+                    Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy, ColMaps cm) {
   using C = typename Cx<T>::t;
+  if (!DY && cm.src && cm.dst && (mul != MUL_TABLE || cm.tab)) {
+    constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
+    const size_t sm = (size_t)NY * NV * sizeof(C) * (mul == MUL_TABLE ? 2 : 1) + 128;   // + alignment slack
+    auto k = k_cols_tma<T, NY, NV, NT>;
+    static bool attr = false;
+    if (!attr) {   // room for the table tile whatever this launch needs
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(2 * NY * NV * sizeof(C) + 128));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    dim3 grid(g.nx / NV, units * g.ncomp);
+    k<<<grid, NT, sm, st>>>(g, *cm.src, *cm.dst, cm.tab ? *cm.tab : *cm.src, mask, fwd, mul, inv, skip, pole, scale,
+                            spec);
+    return cudaGetLastError();
+  }
   constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>() * (DY ? 2 : 1) > 256 ? 256 : cols_nt<T, NY>() * (DY ? 2 : 1);
   const size_t sm = smem_elems<NY, DY ? 2 * NV : NV, true>() * sizeof(C);
   auto k = k_cols<T, NY, NV, NT, DY>;
@@ -234,9 +294,9 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
 template <typename T, int NY>
 cudaError_t cols_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
                    int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
-                   Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
-  if (dy.base) return cols_nd<T, NY, true>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy);
-  return cols_nd<T, NY, false>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy);
+                   Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy, ColMaps cm) {
+  if (dy.base) return cols_nd<T, NY, true>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy, cm);
+  return cols_nd<T, NY, false>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy, cm);
 }
 
 template <int N> constexpr int vrows_nr() { return rows_nr<N>() / 2; }
@@ -291,8 +351,9 @@ template <typename T>
 cudaError_t cols(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd, int mul,
                  int inv, int skip, int pole, T scale, int units, cudaStream_t st,
                  Buf<typename Cx<T>::t> spec = Buf<typename Cx<T>::t>{nullptr, 0, 1},
-                 Buf<typename Cx<T>::t> dy = Buf<typename Cx<T>::t>{nullptr, 0, 1}) {
-#define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy)
+                 Buf<typename Cx<T>::t> dy = Buf<typename Cx<T>::t>{nullptr, 0, 1},
+                 ColMaps cm = ColMaps{nullptr, nullptr, nullptr}) {
+#define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy, cm)
   PROP_SIZE_SWITCH(g.ny, CALL)
 #undef CALL
 }
@@ -473,12 +534,18 @@ struct Prof {
 // ---------------------------------------------------------------------------
 // The step
 // ---------------------------------------------------------------------------
+// Status of the asynchronous-copy error word: 1 = a bounded wait gave up,
+// 2 = a TMA kernel's alignment self-check failed (it skipped its work).
+int async_status(int e) { return e == 0 ? PROP_OK : (e == 2 ? PROP_E_WORKSPACE : PROP_E_TIMEOUT); }
+
 int read_counts(prop* h, int* c3) {
-  if (cudaMemcpyAsync(c3, h->ws + h->counts_off, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+  int buf[3 * (MMAX + 2)];
+  if (cudaMemcpyAsync(buf, h->ws + h->counts_off, sizeof(buf), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return PROP_E_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PROP_E_CUDA;
   if (!h->pending.empty()) resolve_pending(h);
-  return PROP_OK;
+  c3[0] = buf[0]; c3[1] = buf[1]; c3[2] = buf[2];
+  return async_status(buf[ERR_SLOT]);
 }
 
 template <typename T> int step_group(prop* h, Group& G) {
@@ -495,6 +562,9 @@ template <typename T> int step_group(prop* h, Group& G) {
   const int vb = vec_blocks(F);
   const int gs_blocks = (int)((F + NT_VEC * EPT_GS - 1) / (NT_VEC * EPT_GS));
 
+  const ColMaps bmaps = G.tma ? ColMaps{&G.tm_btmp, &G.tm_btmp, &G.tm_tab} : ColMaps{nullptr, nullptr, nullptr};
+  const ColMaps tmaps = G.tma ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr} : ColMaps{nullptr, nullptr, nullptr};
+  const Buf<C> none{nullptr, 0, 1};
   // which beams carry a non-zero delta (read back once per medium change)
   if (G.medium_dirty) {
     G.nonhomog_host.assign(nb, 0);
@@ -522,7 +592,7 @@ template <typename T> int step_group(prop* h, Group& G) {
   // Wn = w + IFFT2[(r - 1) w_hat] (Eq. approx_fs_prop), in one column pass
   { Prof p_(h, K_COLS, (n_inh ? 4 : 3) * cs * pts * nb * Cn);
     CK(cols<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 1, MUL_TABLE, 1, 0, -1, (T)1, nb, st,
-               n_inh ? buf(g.What, F) : Buf<C>{nullptr, 0, 1})); }
+               n_inh ? buf(g.What, F) : none, none, bmaps)); }
   if (n_inh == 0) {   // homogeneous: the new field is final, so its row DFT for the next step is formed here
     Prof p_(h, K_ROWS_INV, (2 * cs + 32) * pts * nb * Cn);   // increment, old field, new field, next row DFT
     CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0,
@@ -610,7 +680,8 @@ template <typename T> int step_group(prop* h, Group& G) {
     { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
       CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
     { Prof p_(h, K_COLS, 2 * cs * endp);
-      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st)); }
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st, none, none,
+                 tmaps)); }
     { Prof p_(h, K_ROWS_INV, (4 * cs + 16) * endp);
       CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st)); }
     { Prof p_(h, K_CONTROL, 0);
@@ -660,7 +731,8 @@ template <typename T> int step_group(prop* h, Group& G) {
                                st)); }
         } else {
           { Prof p_(h, K_COLS, 0);
-            CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
+            CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st, none,
+                     none, tmaps)); }
           { Prof p_(h, K_ROWS_INV, 0);
             CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
         }
@@ -711,7 +783,8 @@ template <typename T> int step_group(prop* h, Group& G) {
     { Prof p_(h, K_ROWS_FWD, 2 * cs * endp);
       CK(rows_fwd<T, C>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
     { Prof p_(h, K_COLS, 2 * cs * endp);
-      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st)); }
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st, none, none,
+                 tmaps)); }
     { Prof p_(h, K_ROWS_INV, (cs + 32) * endp);
       CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_ADD_E), nsys, st)); }
     if (Cn == 2) {   // (Z - Z_fs) e into v_0, from a derivative round trip of e
@@ -727,7 +800,8 @@ template <typename T> int step_group(prop* h, Group& G) {
     { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
       CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
     { Prof p_(h, K_COLS, 2 * cs * endp);
-      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st)); }
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st, none, none,
+                 tmaps)); }
     { Prof p_(h, K_ROWS_INV, (4 * cs + 16) * endp);
       CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st)); }
     { Prof p_(h, K_CONTROL, 0);
@@ -900,6 +974,12 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   for (Group& G : h->groups) {
     rc = h->prec == PROP_FP64 ? upload_group_tables<double>(h, G) : upload_group_tables<float>(h, G);
     if (rc) { delete h; return rc; }
+    const int csz = 2 * (int)elem_size(h->prec);   // bytes per complex element
+    const int nv = h->prec == PROP_FP64 ? cols_per_cta<double>() : cols_per_cta<float>();
+    const long nb = (long)G.beams.size();
+    G.tma = make_col_map(&G.tm_btmp, h->ws + G.off.Btmp, G.nx, G.ny, nb * h->C, csz, nv) &&
+            make_col_map(&G.tm_tmp, h->ws + G.off.Tmp, G.nx, G.ny, nb * h->P * h->C, csz, nv) &&
+            make_col_map(&G.tm_tab, h->ws + G.off.basemul, G.nx, G.ny, 1, csz, nv);
   }
   *out = h;
   return PROP_OK;
@@ -1069,6 +1149,7 @@ const char* prop_error_string(int status) {
     case PROP_E_NAN: return "NaN or Inf in a residual";
     case PROP_E_UNSUPPORTED: return "unsupported grid size or mode";
     case PROP_E_SCRATCH: return "request exceeds the fixed scratch of prop_fft2_noalloc";
+    case PROP_E_TIMEOUT: return "an asynchronous tile copy did not complete within its bounded wait";
     default: return "unknown status";
   }
 }

@@ -19,7 +19,8 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libprop.so")
 
-PROP_OK, PROP_E_ARG, PROP_E_WORKSPACE, PROP_E_CUDA, PROP_E_NOCONV, PROP_E_NAN, PROP_E_UNSUPPORTED, PROP_E_SCRATCH = range(8)
+(PROP_OK, PROP_E_ARG, PROP_E_WORKSPACE, PROP_E_CUDA, PROP_E_NOCONV, PROP_E_NAN, PROP_E_UNSUPPORTED, PROP_E_SCRATCH,
+ PROP_E_TIMEOUT) = range(9)
 PROP_FP64, PROP_FP32 = 0, 1
 
 
