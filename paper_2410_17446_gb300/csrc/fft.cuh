@@ -173,7 +173,7 @@ template <int N, int NV, bool COL> __host__ __device__ constexpr int smem_elems(
   return COL ? N * NV : NV * (N + N / 16);
 }
 
-template <typename C, int N, int R, int NS, bool INV, int NV, int NT, bool COL>
+template <typename C, int N, int R, int NS, bool INV, int NV, int NT, bool COL, bool TWS>
 __device__ __forceinline__ void fft_stage(C* s, const C* __restrict__ tw, int tid) {
   constexpr int M = N / R;
   constexpr int NTASK = NV * M;
@@ -191,7 +191,7 @@ __device__ __forceinline__ void fft_stage(C* s, const C* __restrict__ tw, int ti
         const int k = j % NS;
 #pragma unroll
         for (int t = 1; t < R; ++t) {
-          C w = __ldg(&tw[t * k * (N / (NS * R))]);
+          C w = TWS ? tw[t * k * (N / (NS * R))] : __ldg(&tw[t * k * (N / (NS * R))]);
           if (INV) w.y = -w.y;
           r[q][t] = cmul(r[q][t], w);
         }
@@ -216,12 +216,14 @@ __device__ __forceinline__ void fft_stage(C* s, const C* __restrict__ tw, int ti
 }
 
 // Full transform of the NV vectors held in s (caller synchronises before the call).
-template <typename C, int N, bool INV, int NV, int NT, bool COL>
+// TWS: the twiddle table tw is in shared memory (else global, read through the
+// read-only cache).
+template <typename C, int N, bool INV, int NV, int NT, bool COL, bool TWS = false>
 __device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, int tid) {
   using P = Plan<N>;
-  fft_stage<C, N, P::R0, 1, INV, NV, NT, COL>(s, tw, tid);
-  if constexpr (P::S >= 2) fft_stage<C, N, P::R1, P::R0, INV, NV, NT, COL>(s, tw, tid);
-  if constexpr (P::S >= 3) fft_stage<C, N, P::R2, P::R0 * P::R1, INV, NV, NT, COL>(s, tw, tid);
+  fft_stage<C, N, P::R0, 1, INV, NV, NT, COL, TWS>(s, tw, tid);
+  if constexpr (P::S >= 2) fft_stage<C, N, P::R1, P::R0, INV, NV, NT, COL, TWS>(s, tw, tid);
+  if constexpr (P::S >= 3) fft_stage<C, N, P::R2, P::R0 * P::R1, INV, NV, NT, COL, TWS>(s, tw, tid);
 }
 
 }  // namespace prop_dev

@@ -75,7 +75,14 @@ template <typename T> struct GV {
   C* Tmp2;       // [nsys][ncomp][npts] second column-pass output (the d/dy branch)
   T kx0, ky0;    // 2 pi/(nx dx), 2 pi/(ny dy): wavenumber of FFT index 1
   int* err;      // error word: 1 = a bounded wait for an asynchronous copy gave up, 2 = TMA alignment check failed
+  const int* ulist;   // optional: grid row y works on unit ulist[y] (the compacted iterating systems)
 };
+
+// Unit and (unit, component) item of grid row y, through the optional unit list.
+template <typename T> __device__ __forceinline__ int unit_of(const GV<T>& g, int y) { return g.ulist ? g.ulist[y] : y; }
+template <typename T> __device__ __forceinline__ int item_of(const GV<T>& g, int y) {
+  return g.ulist ? g.ulist[y / g.ncomp] * g.ncomp + y % g.ncomp : y;
+}
 
 // Signed FFT frequency index of position i on an n-point grid.
 __device__ __forceinline__ int ffreq(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   const int row0 = blockIdx.x * NR;
   const SRC* in = src.at(u, c, g.npts) + (long)row0 * N;
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
   constexpr int W = DY ? 2 * NV : NV;     // tile width in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   const int x0 = blockIdx.x * NV;
@@ -351,9 +358,10 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   // run time (the launch reserves 128 bytes of slack)
   const uint32_t pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
   C* s = reinterpret_cast<C*>(smem_raw + pad);
-  C* tab = s + NY * NV;                       // multiplier tile (MUL_TABLE)
+  C* tws = s + NY * NV;                       // twiddles
+  C* tab = tws + NY;                          // multiplier tile (MUL_TABLE)
   __shared__ __align__(8) uint64_t bar;
-  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   const int x0 = blockIdx.x * NV;
@@ -374,8 +382,10 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
       if (mul == MUL_TABLE) tma_load_3d(tab + r * NV, &mtab, x0 * EW, r, 0, &bar);
     }
   }
+  for (int i = threadIdx.x; i < NY; i += NT) tws[i] = g.twy[i];   // while the tiles are in flight
   if (!mbar_wait(&bar, 0, g.err)) { mbar_wait(&bar, 0, g.err); return; }
-  if (fwd) fft_smem<C, NY, false, NV, NT, true>(s, g.twy, threadIdx.x);
+  __syncthreads();
+  if (fwd) fft_smem<C, NY, false, NV, NT, true, true>(s, tws, threadIdx.x);
   if (spec.base) {   // keep the 2-D spectrum as well (read again by the pole solves)
     C* sp = spec.at(u, c, g.npts);
 #pragma unroll 8
@@ -415,7 +425,7 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
     }
     __syncthreads();
   }
-  if (inv) fft_smem<C, NY, true, NV, NT, true>(s, g.twy, threadIdx.x);
+  if (inv) fft_smem<C, NY, true, NV, NT, true, true>(s, tws, threadIdx.x);
   fence_proxy_async_smem();   // this thread's tile writes, before the TMA store reads them
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -447,7 +457,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int item = blockIdx.y, u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   const bool sys = (ep.mode == EPI_R0 || ep.mode == EPI_ARNOLDI || ep.mode == EPI_TRUERES || ep.mode == EPI_ADD_E);
   const int beam = sys ? u / g.P : u;
@@ -616,7 +626,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int u = blockIdx.y;
+  const int u = unit_of(g, (int)blockIdx.y);
   if (!unit_active(g.st, mask, u)) return;
   const int beam = (mode == VEPI_OPDIFF && mask < 0) ? u : u / g.P;
   if (skip_homog && !g.nonhomog[beam]) return;
@@ -734,7 +744,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   using C = typename Cx<T>::t;
   constexpr int NW = NT / 32;
   __shared__ T red[NW][4 * (MMAX + 1)];
-  const int s = blockIdx.y;
+  const int s = unit_of(g, (int)blockIdx.y);
   if (g.st[s].state != ST_ITER) return;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long L = (long)g.ncomp * g.npts;
@@ -1225,7 +1235,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   __shared__ double nw_s;
   __shared__ C ca[MMAX + 8], cg[MMAX + 8];
   __shared__ T ir_s;
-  const int s = blockIdx.y, j = jj, tid = threadIdx.x;
+  const int s = unit_of(g, (int)blockIdx.y), j = jj, tid = threadIdx.x;
   SysState& q = g.st[s];
   if (q.state != ST_ITER) return;
   const int par = j & 1;
@@ -1467,6 +1477,28 @@ __global__ void k_step_reset(SysState* st, int nsys) {
 __global__ void k_collect(const SysState* st, int nsys, int* iters, int* cycles, double* resid, int* flags) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     iters[s] = st[s].iters; cycles[s] = st[s].cycles; resid[s] = st[s].resid; flags[s] = st[s].flags;
+  }
+}
+
+// Compacted list of the systems in state ST_ITER, in index order (one block of
+// a multiple of 32 threads): the Arnoldi launches of a batch cover only these.
+__global__ void k_active_list(const SysState* st, int nsys, int* list) {
+  __shared__ int wsum[32], base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int s0 = 0; s0 < nsys; s0 += blockDim.x) {
+    const int s = s0 + threadIdx.x;
+    const bool a = s < nsys && st[s].state == ST_ITER;
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) wsum[w] = __popc(m);
+    __syncthreads();
+    int off = base;
+    for (int k = 0; k < w; ++k) off += wsum[k];
+    if (a) list[off + __popc(m & ((1u << lane) - 1u))] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) for (int k = 0; k < nw; ++k) base += wsum[k];
+    __syncthreads();
   }
 }
 

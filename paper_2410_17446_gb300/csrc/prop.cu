@@ -55,7 +55,7 @@ constexpr int ERR_SLOT = 3 * (MMAX + 2) - 1;   // int in the counts area: the as
 
 struct Layout {
   size_t V, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
-      rk, anorm, part, psi, Tmp2, poles, act0, act1, netout, stage, iters, cycles, resid, flags, end;
+      rk, anorm, part, psi, Tmp2, poles, act0, act1, netout, stage, iters, cycles, resid, flags, ulist, end;
 };
 
 struct Group {
@@ -146,6 +146,7 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
   L.cycles = take(nsys * sizeof(int));
   L.resid = take(nsys * sizeof(double));
   L.flags = take(nsys * sizeof(int));
+  L.ulist = take(nsys * sizeof(int));
   L.end = o;
   return o;
 }
@@ -171,6 +172,7 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   g.psi = (C*)(b + L.psi);
   g.Tmp2 = (C*)(b + L.Tmp2);
   g.err = (int*)(b + h->counts_off) + ERR_SLOT;
+  g.ulist = nullptr;
   g.kx0 = (T)(2.0 * M_PI / ((double)G.nx * G.dx));
   g.ky0 = (T)(2.0 * M_PI / ((double)G.ny * G.dy));
   return g;
@@ -267,12 +269,12 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
   using C = typename Cx<T>::t;
   if (!DY && cm.src && cm.dst && (mul != MUL_TABLE || cm.tab)) {
     constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
-    const size_t sm = (size_t)NY * NV * sizeof(C) * (mul == MUL_TABLE ? 2 : 1) + 128;   // + alignment slack
+    const size_t sm = ((size_t)NY * NV * (mul == MUL_TABLE ? 2 : 1) + NY) * sizeof(C) + 128;   // + twiddles, slack
     auto k = k_cols_tma<T, NY, NV, NT>;
     static bool attr = false;
     if (!attr) {   // room for the table tile whatever this launch needs
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(2 * NY * NV * sizeof(C) + 128));
+                                           (int)((2 * NY * NV + NY) * sizeof(C) + 128));
       if (e != cudaSuccess) return e;
       attr = true;
     }
@@ -565,6 +567,9 @@ template <typename T> int step_group(prop* h, Group& G) {
   const ColMaps bmaps = G.tma ? ColMaps{&G.tm_btmp, &G.tm_btmp, &G.tm_tab} : ColMaps{nullptr, nullptr, nullptr};
   const ColMaps tmaps = G.tma ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr} : ColMaps{nullptr, nullptr, nullptr};
   const Buf<C> none{nullptr, 0, 1};
+  int* ulist = (int*)(h->ws + G.off.ulist);
+  GV<T> ga = g;            // the Arnoldi launches of a batch: grid rows = the listed iterating systems
+  ga.ulist = ulist;
   // which beams carry a non-zero delta (read back once per medium change)
   if (G.medium_dirty) {
     G.nonhomog_host.assign(nb, 0);
@@ -715,35 +720,39 @@ template <typename T> int step_group(prop* h, Group& G) {
     std::vector<int> cnt(3 * (SYNC_EVERY + 1));
     int jj0 = 0, ended = 0, flags = 0, act0 = c3[0];
     for (int jj = 0; jj <= m; ++jj) {
-      if (jj == jj0) CK(cudaMemsetAsync(counts + 3, 0, 3 * SYNC_EVERY * sizeof(int), st));
+      if (jj == jj0) {   // batch start: zero the count slots, list the act0 iterating systems
+        CK(cudaMemsetAsync(counts + 3, 0, 3 * SYNC_EVERY * sizeof(int), st));
+        Prof p_(h, K_CONTROL, 0);
+        k_active_list<<<1, 256, 0, st>>>(g.st, nsys, ulist);
+      }
       const bool op = jj < m;
       if (op) {
         C* Vj = g.V + (long)jj * F;
         const long vs = (long)(m + 2) * F;
         { Prof p_(h, K_ROWS_FWD, 0);
-          CK(rows_fwd<T, C>(g, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, nsys, st)); }
+          CK(rows_fwd<T, C>(ga, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, act0, st)); }
         if (Cn == 2) {
           { Prof p_(h, K_COLS, 0);
-            CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st,
+            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, act0, st,
                        Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
           { Prof p_(h, K_ROWS_INV, 0);
-            CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, nsys,
+            CK(rows_inv_vec<T>(ga, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, act0,
                                st)); }
         } else {
           { Prof p_(h, K_COLS, 0);
-            CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st, none,
+            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, act0, st, none,
                      none, tmaps)); }
           { Prof p_(h, K_ROWS_INV, 0);
-            CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), nsys, st)); }
+            CK(rows_inv<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), act0, st)); }
         }
       }
       { Prof p_(h, K_GRAM, 0);
-        k_dcgs_gram<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, nsys), NT_VEC, 0, st>>>(g, jj, op ? 1 : 0); }
+        k_dcgs_gram<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, act0), NT_VEC, 0, st>>>(ga, jj, op ? 1 : 0); }
       { Prof p_(h, K_GS_UPDATE, 0);
         StepArgs sa;
         sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
         sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = counts + 3 * (jj - jj0 + 1);
-        k_dcgs_step<T, NT_VEC, EPT_GS><<<dim3(gs_blocks + 1, nsys), NT_VEC, 0, st>>>(g, jj, sa); }
+        k_dcgs_step<T, NT_VEC, EPT_GS><<<dim3(gs_blocks + 1, act0), NT_VEC, 0, st>>>(ga, jj, sa); }
       CK(cudaGetLastError());
       const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj == m;
       if (!sync_now) continue;
