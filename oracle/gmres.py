@@ -54,6 +54,23 @@ def _apply_P(u: np.ndarray, v: np.ndarray) -> np.ndarray:
     return v - 2.0 * u * np.vdot(u, v)
 
 
+def _lsq_qr(Hk: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """min ||g - Hk y|| by a Householder QR of Hk (full column rank)."""
+    Q, R = np.linalg.qr(Hk)
+    return np.linalg.solve(R, Q.conj().T @ g)
+
+
+def _lsq(Hk: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """The GMRES least-squares problem min ||beta e_1 - Hbar y|| (Saad & Schultz,
+    1986): LAPACK's SVD-based driver, or the QR solve when that driver reports
+    that its SVD did not converge (seen with some BLAS builds).  Hbar has full
+    column rank before a breakdown, where both give the same y."""
+    try:
+        return np.linalg.lstsq(Hk, g, rcond=None)[0]
+    except np.linalg.LinAlgError:
+        return _lsq_qr(Hk, g)
+
+
 def gmres(apply_A: Callable[[np.ndarray], np.ndarray],
           apply_Minv: Callable[[np.ndarray], np.ndarray],
           b: np.ndarray, x0: Optional[np.ndarray] = None, restart: int = 20,
@@ -91,7 +108,7 @@ def gmres(apply_A: Callable[[np.ndarray], np.ndarray],
                 k = j
                 g = np.zeros(k + 1, np.complex128)
                 g[0] = beta
-                y, *_ = np.linalg.lstsq(H[:k + 1, :k], g, rcond=None)
+                y = _lsq(H[:k + 1, :k], g)
                 est = np.linalg.norm(g - H[:k + 1, :k] @ y)
                 if est <= tol * bnorm or j == m or alpha == 0.0:
                     break

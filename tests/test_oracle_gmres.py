@@ -55,3 +55,17 @@ def test_homogeneous_medium_needs_one_iteration():
         r = pr.solve_shifted_gmres(med, w, pole, tol=1e-12)
         assert r.iterations == GOLD["gmres_homogeneous_iterations"]["iterations"]
         np.testing.assert_allclose(r.x, med.freespace_solve(w, pole), atol=1e-13)
+
+
+def test_least_squares_qr_branch_matches_lstsq():
+    """The QR fallback of the Hessenberg least-squares solve gives lstsq's y."""
+    import numpy as np
+    from oracle import gmres as gm
+    rng = np.random.default_rng(5)
+    for k in (1, 4, 19):
+        H = np.triu(rng.standard_normal((k + 1, k)) + 1j * rng.standard_normal((k + 1, k)), -1)
+        g = np.zeros(k + 1, complex)
+        g[0] = 2.5
+        y_ref = np.linalg.lstsq(H, g, rcond=None)[0]
+        assert np.allclose(gm._lsq_qr(H, g), y_ref, rtol=1e-12, atol=1e-12)
+        assert np.allclose(gm._lsq(H, g), y_ref, rtol=1e-12, atol=1e-12)
