@@ -40,7 +40,9 @@ def _reflector(z: np.ndarray, j: int):
     u = np.zeros_like(z)
     if nrm == 0.0:
         return u, 0.0 + 0.0j
-    phase = tail[0] / abs(tail[0]) if tail[0] != 0 else 1.0
+    # alpha = -exp(i arg z_j) ||tail|| (the sign that avoids cancellation); the
+    # phase from the angle stays exact when z_j is subnormal, where z_j/|z_j| overflows
+    phase = np.exp(1j * np.angle(tail[0])) if tail[0] != 0 else 1.0
     alpha = -phase * nrm
     u[j:] = tail
     u[j] -= alpha

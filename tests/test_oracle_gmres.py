@@ -69,3 +69,15 @@ def test_least_squares_qr_branch_matches_lstsq():
         y_ref = np.linalg.lstsq(H, g, rcond=None)[0]
         assert np.allclose(gm._lsq_qr(H, g), y_ref, rtol=1e-12, atol=1e-12)
         assert np.allclose(gm._lsq(H, g), y_ref, rtol=1e-12, atol=1e-12)
+
+
+def test_reflector_with_subnormal_leading_entry():
+    """A subnormal leading entry still gives a unit reflector mapping z to alpha e_j."""
+    import numpy as np
+    from oracle import gmres as gm
+    z = np.array([0.3 + 0.1j, 5e-320 + 3e-320j, 1.0 - 2.0j, 0.5j])
+    u, alpha = gm._reflector(z, 1)
+    assert np.isfinite(u).all() and abs(np.linalg.norm(u) - 1.0) < 1e-14
+    r = gm._apply_P(u, z)
+    assert np.allclose(r[2:], 0.0, atol=1e-14) and abs(r[1] - alpha) < 1e-14 and r[0] == z[0]
+    assert abs(abs(alpha) - np.linalg.norm(z[1:])) < 1e-14
