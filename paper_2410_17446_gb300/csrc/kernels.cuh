@@ -713,13 +713,15 @@ template <typename T> __device__ __forceinline__ typename Cx<T>::t* vslot(const 
   return g.V + ((long)s * (g.m + 2) + jj) * g.ncomp * g.npts;
 }
 
-// Sum each of 32 per-lane values over the warp: on return v[0] of lane l holds
-// the warp total of value l (a butterfly that halves the live values at each
-// of its five levels: 31 shuffles in all).
-template <typename A> __device__ __forceinline__ void warp_transpose_reduce(A (&v)[32]) {
+// Sum each of V per-lane values (V a power of two <= 32) over the warp: on
+// return v[0] of lane l holds the warp total of value l % V.  A butterfly halves
+// the live values at each of its first log2 V levels (lane pairs exchange the
+// halves they do not keep), then plain xor steps finish the sum: V - 1 + (5 -
+// log2 V) shuffles in all.
+template <int V, typename A> __device__ __forceinline__ void warp_transpose_reduce(A (&v)[V]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 16; k >= 1; k >>= 1) {
+  for (int k = V / 2; k >= 1; k >>= 1) {
     const bool up = (lane & k) != 0;
 #pragma unroll
     for (int i = 0; i < k; ++i) {
@@ -728,6 +730,8 @@ template <typename A> __device__ __forceinline__ void warp_transpose_reduce(A (&
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, k);
     }
   }
+#pragma unroll
+  for (int o = V; o < 32; o <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
 }
 
 // The inner products of iteration j of the delayed re-orthogonalisation (see
@@ -735,11 +739,11 @@ template <typename A> __device__ __forceinline__ void warp_transpose_reduce(A (&
 // and ||w||^2, with u = v_j and w = v_{j+1} (w = 0 when with_w = 0: the last
 // step of a cycle needs only the products with u), for every iterating system.  Each
 // thread keeps EPT points of u and w in registers and takes the basis in
-// groups of 8 vectors (8*EPT loads in flight); a group's 32 partial sums leave
-// the warp in one transpose-reduce.  Per-warp totals are summed in FP64 and
+// groups of GVEC vectors (GVEC*EPT loads in flight); a group's 4 GVEC partial
+// sums leave the warp in one transpose-reduce.  Per-warp totals are summed in FP64 and
 // added to the striped accumulators (planes 2 (j % 2) + 0, 1; slot MMAX of the
 // second takes ||w||^2).
-template <typename T, int NT, int EPT>
+template <typename T, int NT, int EPT, int GVEC>
 __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   using C = typename Cx<T>::t;
   constexpr int NW = NT / 32;
@@ -762,10 +766,10 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
     uu += uv[e].x * uv[e].x + uv[e].y * uv[e].y;
     ww += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
   }
-  for (int g0 = 0; g0 <= jj; g0 += 8) {   // slots g0..g0+7; slot jj carries (d, c, ||w||^2)
-    C vv[8][EPT];
+  for (int g0 = 0; g0 <= jj; g0 += GVEC) {   // slots g0..g0+GVEC-1; slot jj carries (d, c, ||w||^2)
+    C vv[GVEC][EPT];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < GVEC; ++k) {
       const C* vi = vslot(g, s, g0 + k);
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
@@ -773,9 +777,9 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
         vv[k][e] = (g0 + k < jj && p < L) ? vi[p] : C{};
       }
     }
-    T acc[32];
+    T acc[4 * GVEC];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < GVEC; ++k) {
       T br = 0, bi = 0, ar = 0, ai = 0;
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
@@ -786,8 +790,8 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
       if (g0 + k == jj) { br = uwr; bi = uwi; ar = uu; ai = ww; }
       acc[4 * k] = br; acc[4 * k + 1] = bi; acc[4 * k + 2] = ar; acc[4 * k + 3] = ai;
     }
-    warp_transpose_reduce(acc);
-    if (g0 + (lane >> 2) <= jj) red[wp][4 * g0 + lane] = acc[0];
+    warp_transpose_reduce<4 * GVEC>(acc);
+    if (lane < 4 * GVEC && g0 + (lane >> 2) <= jj) red[wp][4 * g0 + lane] = acc[0];
   }
   __syncthreads();
   double2* pb = part_at(g.part, s, 2 * (jj & 1), blockIdx.x % NSTRIPE, 0);
@@ -1028,24 +1032,30 @@ __device__ __forceinline__ int rp(int row, int col) { return col * (col + 1) / 2
 // shared-memory copy of R; ends the cycle.  Rs must hold columns 0..J-1 packed
 // and acc the right-hand side g[0..J-1].
 __device__ void end_cycle_block(SysState& q, int J, double2* Rs, double2* acc) {
-  const int tid = threadIdx.x;
+  // One warp, no block barriers: lane l holds rows l and l + 32 (J <= MMAX = 64)
+  // and the reciprocals of their diagonal entries; at row i the owner lane forms
+  // y_i and broadcasts it, every lane updates its rows above i.
   __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int l = threadIdx.x;
+  const double2 zero = make_double2(0.0, 0.0);
+  auto rcp = [](double2 d) { const double dd = dabs2(d); return make_double2(d.x / dd, -d.y / dd); };
+  double2 a0 = l < J ? acc[l] : zero, a1 = l + 32 < J ? acc[l + 32] : zero;
+  const double2 r0 = l < J ? rcp(Rs[rp(l, l)]) : zero, r1 = l + 32 < J ? rcp(Rs[rp(l + 32, l + 32)]) : zero;
   for (int i = J - 1; i >= 0; --i) {
-    if (tid == 0) {
-      const double2 d = Rs[rp(i, i)], a = acc[i];
-      const double dd = dabs2(d);
-      acc[i] = make_double2((a.x * d.x + a.y * d.y) / dd, (a.y * d.x - a.x * d.y) / dd);
-    }
-    __syncthreads();
-    const double2 y = acc[i];
-    for (int k = tid; k < i; k += blockDim.x) {
-      const double2 t = dmul(Rs[rp(k, i)], y);
-      acc[k].x -= t.x; acc[k].y -= t.y;
-    }
-    __syncthreads();
+    const int owner = i & 31;
+    const bool hi = i >= 32;
+    const double2 mine = hi ? dmul(a1, r1) : dmul(a0, r0);   // meaningful in the owner lane
+    double2 y;
+    y.x = __shfl_sync(0xffffffffu, mine.x, owner);
+    y.y = __shfl_sync(0xffffffffu, mine.y, owner);
+    if (l == owner) { if (hi) a1 = y; else a0 = y; }
+    if (l < i) { const double2 t = dmul(Rs[rp(l, i)], y); a0.x -= t.x; a0.y -= t.y; }
+    if (l + 32 < i) { const double2 t = dmul(Rs[rp(l + 32, i)], y); a1.x -= t.x; a1.y -= t.y; }
   }
-  for (int i = tid; i < J; i += blockDim.x) q.y[i] = acc[i];
-  if (tid == 0) {
+  if (l < J) q.y[l] = a0;
+  if (l + 32 < J) q.y[l + 32] = a1;
+  if (l == 0) {
     q.jend = J;
     q.enorm2 = 0.0;          // recomputed by the correction update
     q.state = ST_CYCLE_END;
@@ -1228,6 +1238,7 @@ __device__ void dcgs_control(SysState& q, int s, int j, const double2* bs, const
 // each CTA derives from the folded sums; the last CTA runs dcgs_control.
 // The sweep takes the basis in groups of 8 vectors (8*EPT loads in flight).
 // If the control ends the cycle at this step the sweep's output goes unused.
+// grid.x = chunks + 1: CTA 0 is the control, CTA x > 0 sweeps chunk x - 1.
 template <typename T, int NT, int EPT>
 __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   using C = typename Cx<T>::t;
@@ -1253,7 +1264,8 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
     else as[i] = sum;
   }
   __syncthreads();
-  if (blockIdx.x == gridDim.x - 1) { dcgs_control(q, s, j, bs, as, nw_s, g.part, A); return; }
+  // the control goes first in dispatch order, so its FP64 chain overlaps the sweep
+  if (blockIdx.x == 0) { dcgs_control(q, s, j, bs, as, nw_s, g.part, A); return; }
   if (j == A.m) return;   // the cycle ends at this step: nothing to sweep
   // coefficients, in the working precision (the sums themselves are FP64)
   if (tid < 32) {
@@ -1289,7 +1301,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   const long L = (long)g.ncomp * g.npts;
   C* uj = vslot(g, s, jj);
   C* wj = vslot(g, s, jj + 1);
-  const long b0 = (long)blockIdx.x * NT * EPT + tid;
+  const long b0 = (long)(blockIdx.x - 1) * NT * EPT + tid;
   C qv[EPT], x[EPT];
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {

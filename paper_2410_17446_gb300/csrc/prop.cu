@@ -49,7 +49,9 @@ constexpr int clamp_nt(int t) { return t < 64 ? 64 : (t > 256 ? 256 : t); }
 template <int N> constexpr int rows_nt() { return clamp_nt(rows_nr<N>() * N / 16); }
 template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * cols_per_cta<T>() / 16); }
 constexpr int NT_VEC = 256;
-constexpr int EPT_GS = 2;   // points per thread of the Gram-Schmidt sweeps
+constexpr int EPT_GS = 2;     // points per thread of the update sweep
+constexpr int EPT_GRAM = 4;   // points per thread of the Gram sweep
+constexpr int GVEC_GRAM = 4;  // basis vectors per transpose-reduce of the Gram sweep
 constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host reads of the GMRES state
 constexpr int ERR_SLOT = 3 * (MMAX + 2) - 1;   // int in the counts area: the asynchronous-copy error word
 
@@ -563,6 +565,7 @@ template <typename T> int step_group(prop* h, Group& G) {
   const int tb = 128, tg = (nsys + tb - 1) / tb;
   const int vb = vec_blocks(F);
   const int gs_blocks = (int)((F + NT_VEC * EPT_GS - 1) / (NT_VEC * EPT_GS));
+  const int gram_blocks = (int)((F + NT_VEC * EPT_GRAM - 1) / (NT_VEC * EPT_GRAM));
 
   const ColMaps bmaps = G.tma ? ColMaps{&G.tm_btmp, &G.tm_btmp, &G.tm_tab} : ColMaps{nullptr, nullptr, nullptr};
   const ColMaps tmaps = G.tma ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr} : ColMaps{nullptr, nullptr, nullptr};
@@ -747,7 +750,7 @@ template <typename T> int step_group(prop* h, Group& G) {
         }
       }
       { Prof p_(h, K_GRAM, 0);
-        k_dcgs_gram<T, NT_VEC, EPT_GS><<<dim3(gs_blocks, act0), NT_VEC, 0, st>>>(ga, jj, op ? 1 : 0); }
+        k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM><<<dim3(gram_blocks, act0), NT_VEC, 0, st>>>(ga, jj, op ? 1 : 0); }
       { Prof p_(h, K_GS_UPDATE, 0);
         StepArgs sa;
         sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
