@@ -740,21 +740,25 @@ template <int V, typename A> __device__ __forceinline__ void warp_transpose_redu
 // step of a cycle needs only the products with u), for every iterating system.  Each
 // thread keeps EPT points of u and w in registers and takes the basis in
 // groups of GVEC vectors (GVEC*EPT loads in flight); a group's 4 GVEC partial
-// sums leave the warp in one transpose-reduce.  Per-warp totals are summed in FP64 and
+// sums leave the warp in one transpose-reduce.  CTAs loop over chunks (about
+// one wave of them); per-warp totals are kept in FP64, summed and
 // added to the striped accumulators (planes 2 (j % 2) + 0, 1; slot MMAX of the
 // second takes ||w||^2).
 template <typename T, int NT, int EPT, int GVEC>
 __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   using C = typename Cx<T>::t;
   constexpr int NW = NT / 32;
-  __shared__ T red[NW][4 * (MMAX + 1)];
+  __shared__ double red[NW][4 * (MMAX + 1)];
   const int s = unit_of(g, (int)blockIdx.y);
   if (g.st[s].state != ST_ITER) return;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long L = (long)g.ncomp * g.npts;
   const C* up = vslot(g, s, jj);
   const C* wpv = vslot(g, s, jj + 1);
-  const long b0 = (long)blockIdx.x * NT * EPT + threadIdx.x;
+  for (int t = lane; t < 4 * (jj + 1); t += 32) red[wp][t] = 0.0;   // each warp owns its row
+  const long nchunks = (L + NT * EPT - 1) / (NT * EPT);
+  for (long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {   // persistent over chunks
+  const long b0 = chunk * NT * EPT + threadIdx.x;
   C uv[EPT], wv[EPT];
   T uwr = 0, uwi = 0, uu = 0, ww = 0;
 #pragma unroll
@@ -791,7 +795,8 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
       acc[4 * k] = br; acc[4 * k + 1] = bi; acc[4 * k + 2] = ar; acc[4 * k + 3] = ai;
     }
     warp_transpose_reduce<4 * GVEC>(acc);
-    if (lane < 4 * GVEC && g0 + (lane >> 2) <= jj) red[wp][4 * g0 + lane] = acc[0];
+    if (lane < 4 * GVEC && g0 + (lane >> 2) <= jj) red[wp][4 * g0 + lane] += (double)acc[0];
+  }
   }
   __syncthreads();
   double2* pb = part_at(g.part, s, 2 * (jj & 1), blockIdx.x % NSTRIPE, 0);
@@ -799,7 +804,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   for (int t = threadIdx.x; t < 4 * (jj + 1); t += NT) {
     double v = 0.0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) v += (double)red[w][t];
+    for (int w = 0; w < NW; ++w) v += red[w][t];
     const int i = t >> 2, comp = t & 3;
     if (comp == 0) atomicAdd(&pb[i].x, v);
     else if (comp == 1) atomicAdd(&pb[i].y, v);
@@ -1238,7 +1243,8 @@ __device__ void dcgs_control(SysState& q, int s, int j, const double2* bs, const
 // each CTA derives from the folded sums; the last CTA runs dcgs_control.
 // The sweep takes the basis in groups of 8 vectors (8*EPT loads in flight).
 // If the control ends the cycle at this step the sweep's output goes unused.
-// grid.x = chunks + 1: CTA 0 is the control, CTA x > 0 sweeps chunk x - 1.
+// grid.x = 1 + sweep CTAs: CTA 0 is the control, CTA x > 0 sweeps chunks
+// x - 1, x - 1 + (gridDim.x - 1), ... (one coefficient prologue per CTA).
 template <typename T, int NT, int EPT>
 __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   using C = typename Cx<T>::t;
@@ -1301,7 +1307,9 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   const long L = (long)g.ncomp * g.npts;
   C* uj = vslot(g, s, jj);
   C* wj = vslot(g, s, jj + 1);
-  const long b0 = (long)(blockIdx.x - 1) * NT * EPT + tid;
+  const long nchunks = (L + NT * EPT - 1) / (NT * EPT);
+  for (long chunk = blockIdx.x - 1; chunk < nchunks; chunk += gridDim.x - 1) {   // persistent over chunks
+  const long b0 = chunk * NT * EPT + tid;
   C qv[EPT], x[EPT];
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
@@ -1341,6 +1349,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
       C xx = x[e]; xx.x -= t.x; xx.y -= t.y;
       uj[p] = qq; wj[p] = xx;
     }
+  }
   }
 }
 

@@ -41,6 +41,17 @@ bool supported_n(int n) {
   }
 }
 
+int sm_count() {   // SMs of the current device (looked up once)
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    cudaGetLastError();
+  }
+  return n > 0 ? n : 1;
+}
+
 // Launch geometry of the FFT passes: small CTAs, so that one 1024^2 field still
 // spreads over several CTAs per SM and their load / transform / store phases overlap.
 template <typename T> constexpr int cols_per_cta() { return sizeof(T) == 4 ? 4 : 2; }   // 32-byte row segments
@@ -750,12 +761,16 @@ template <typename T> int step_group(prop* h, Group& G) {
         }
       }
       { Prof p_(h, K_GRAM, 0);
-        k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM><<<dim3(gram_blocks, act0), NT_VEC, 0, st>>>(ga, jj, op ? 1 : 0); }
+        // sweeps: about one wave of CTAs (4 resident per SM) shared by the act0 systems
+        const int cap = std::max(1, 4 * sm_count() / std::max(act0, 1));
+        k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>
+            <<<dim3(std::min(gram_blocks, cap), act0), NT_VEC, 0, st>>>(ga, jj, op ? 1 : 0); }
       { Prof p_(h, K_GS_UPDATE, 0);
         StepArgs sa;
         sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
         sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = counts + 3 * (jj - jj0 + 1);
-        k_dcgs_step<T, NT_VEC, EPT_GS><<<dim3(gs_blocks + 1, act0), NT_VEC, 0, st>>>(ga, jj, sa); }
+        const int cap = std::max(1, 4 * sm_count() / std::max(act0, 1));
+        k_dcgs_step<T, NT_VEC, EPT_GS><<<dim3(std::min(gs_blocks, cap) + 1, act0), NT_VEC, 0, st>>>(ga, jj, sa); }
       CK(cudaGetLastError());
       const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj == m;
       if (!sync_now) continue;
