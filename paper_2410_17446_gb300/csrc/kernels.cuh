@@ -478,12 +478,30 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
       for (int e = threadIdx.x * 8; e < NR * N; e += NT * 8) prefetch_l2(w0 + (uo + e) * 16);
     }
   }
+  const bool in16 = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+  if (sizeof(T) == 4 && in16) {   // 16-byte loads: two points (same row, N even) per access
 #pragma unroll
-  for (int e = threadIdx.x; e < NR * N; e += NT) {
-    C a = in[e];
-    if (ep.kxsel == 1) a = cmul(a, ik_factor<C>(e % N, N, g.kx0));
-    else if (ep.kxsel == 2) { const T k = (T)ffreq(e % N, N) * g.kx0; a.x *= -k * k; a.y *= -k * k; }
-    s[sidx<N, NR, false>(e / N, e % N)] = a;
+    for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {
+      const float4 q = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(in))[e2];
+      const int e = 2 * e2;
+      C a, b;
+      a.x = (T)q.x; a.y = (T)q.y; b.x = (T)q.z; b.y = (T)q.w;
+      if (ep.kxsel == 1) { a = cmul(a, ik_factor<C>(e % N, N, g.kx0)); b = cmul(b, ik_factor<C>((e + 1) % N, N, g.kx0)); }
+      else if (ep.kxsel == 2) {
+        const T k0 = (T)ffreq(e % N, N) * g.kx0, k1 = (T)ffreq((e + 1) % N, N) * g.kx0;
+        a.x *= -k0 * k0; a.y *= -k0 * k0; b.x *= -k1 * k1; b.y *= -k1 * k1;
+      }
+      s[sidx<N, NR, false>(e / N, e % N)] = a;
+      s[sidx<N, NR, false>(e / N, e % N + 1)] = b;
+    }
+  } else {
+#pragma unroll
+    for (int e = threadIdx.x; e < NR * N; e += NT) {
+      C a = in[e];
+      if (ep.kxsel == 1) a = cmul(a, ik_factor<C>(e % N, N, g.kx0));
+      else if (ep.kxsel == 2) { const T k = (T)ffreq(e % N, N) * g.kx0; a.x *= -k * k; a.y *= -k * k; }
+      s[sidx<N, NR, false>(e / N, e % N)] = a;
+    }
   }
   __syncthreads();
   fft_smem<C, N, true, NR, NT, false>(s, g.twx, threadIdx.x);
@@ -504,7 +522,32 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     }
   } else {
   double acc = 0.0, acc2 = 0.0, accr = 0.0, acci = 0.0;
+  bool acc16 = false;   // the FP32 accumulate ran vectorised below
+  if constexpr (sizeof(T) == 4) {
+    const long plane = (long)g.nb * g.ncomp * g.npts;
+    acc16 = ep.mode == EPI_ACCUM64 &&
+            ((reinterpret_cast<uintptr_t>(reinterpret_cast<const float2*>(g.W64) + unit_off) |
+              reinterpret_cast<uintptr_t>(reinterpret_cast<const float2*>(g.W64) + plane + unit_off) |
+              reinterpret_cast<uintptr_t>(reinterpret_cast<float2*>(ep.out64) + unit_off) |
+              reinterpret_cast<uintptr_t>(reinterpret_cast<float2*>(ep.out64) + plane + unit_off)) & 15) == 0;
+    if (acc16) {   // double-float accumulate with 16-byte accesses (two points each)
+      const float4* ohi = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(g.W64) + unit_off);
+      const float4* olo = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(g.W64) + plane + unit_off);
+      float4* nhi = reinterpret_cast<float4*>(reinterpret_cast<float2*>(ep.out64) + unit_off);
+      float4* nlo = reinterpret_cast<float4*>(reinterpret_cast<float2*>(ep.out64) + plane + unit_off);
+      for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {
+        const int e = 2 * e2, i0 = sidx<N, NR, false>(e / N, e % N), i1 = sidx<N, NR, false>(e / N, e % N + 1);
+        const C v0 = s[i0], v1 = s[i1];
+        float4 h = ohi[e2], l = olo[e2];
+        df_add(h.x, l.x, v0.x); df_add(h.y, l.y, v0.y);
+        df_add(h.z, l.z, v1.x); df_add(h.w, l.w, v1.y);
+        nhi[e2] = h; nlo[e2] = l;
+        if (ep.fwd_out) { s[i0] = make_float2(h.x, h.y); s[i1] = make_float2(h.z, h.w); }
+      }
+    }
+  }
   for (int e = threadIdx.x; e < NR * N; e += NT) {
+    if (acc16) break;   // done above
     const C val = s[sidx<N, NR, false>(e / N, e % N)];
     switch (ep.mode) {
       case EPI_STORE: dst.at(u, c, g.npts)[off + e] = val; break;
@@ -581,8 +624,16 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     __syncthreads();
     fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
     C* o = reinterpret_cast<C*>(ep.fwd_out) + unit_off;
+    if (sizeof(T) == 4 && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+      for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {
+        const int e = 2 * e2;
+        const C a = s[sidx<N, NR, false>(e / N, e % N)], b = s[sidx<N, NR, false>(e / N, e % N + 1)];
+        reinterpret_cast<float4*>(reinterpret_cast<float*>(o))[e2] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+      }
+    } else {
 #pragma unroll
-    for (int e = threadIdx.x; e < NR * N; e += NT) o[e] = s[sidx<N, NR, false>(e / N, e % N)];
+      for (int e = threadIdx.x; e < NR * N; e += NT) o[e] = s[sidx<N, NR, false>(e / N, e % N)];
+    }
   }
   if (ep.mode == EPI_R0 || ep.mode == EPI_TRUERES) {
     const double t = block_sum(acc, red);
