@@ -212,6 +212,24 @@ __device__ __forceinline__ void flush_slots(const S* red, int nwarps, int n, dou
   }
 }
 
+// Points p, p+1 (p even, 16-byte aligned) in one access: a float4 for complex
+// FP32, two 16-byte accesses for complex FP64.
+template <typename C> __device__ __forceinline__ void ld2(const C* base, long p, C& a, C& b) {
+  if constexpr (sizeof(C) == 8) {
+    const float4 q = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(base + p));
+    a.x = q.x; a.y = q.y; b.x = q.z; b.y = q.w;
+  } else {
+    a = base[p]; b = base[p + 1];
+  }
+}
+template <typename C> __device__ __forceinline__ void st2(C* base, long p, const C& a, const C& b) {
+  if constexpr (sizeof(C) == 8) {
+    *reinterpret_cast<float4*>(reinterpret_cast<float*>(base + p)) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    base[p] = a; base[p + 1] = b;
+  }
+}
+
 __device__ __forceinline__ bool unit_active(const SysState* st, int mask, int u) {
   return mask < 0 || st[u].state == mask;
 }
@@ -231,18 +249,41 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
   const int row0 = blockIdx.x * NR;
   const SRC* in = src.at(u, c, g.npts) + (long)row0 * N;
   T acc = 0;
+  C* out = dst.at(u, c, g.npts) + (long)row0 * N;
+  // 16-byte accesses (two points, same row) for complex FP32 in and out
+  constexpr bool V4 = sizeof(T) == 4 && sizeof(SRC) == 8;
+  const bool vec = V4 && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+  if (vec) {
 #pragma unroll
-  for (int e = threadIdx.x; e < NR * N; e += NT) {
-    const int r = e / N, n = e % N;
-    const C v = to_c(in[e], T());
-    if (norm_acc) acc += v.x * v.x + v.y * v.y;
-    s[sidx<N, NR, false>(r, n)] = v;
+    for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {
+      const int e = 2 * e2;
+      C a, b;
+      ld2(reinterpret_cast<const C*>(in), e, a, b);
+      if (norm_acc) acc += a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
+      s[sidx<N, NR, false>(e / N, e % N)] = a;
+      s[sidx<N, NR, false>(e / N, e % N + 1)] = b;
+    }
+  } else {
+#pragma unroll
+    for (int e = threadIdx.x; e < NR * N; e += NT) {
+      const int r = e / N, n = e % N;
+      const C v = to_c(in[e], T());
+      if (norm_acc) acc += v.x * v.x + v.y * v.y;
+      s[sidx<N, NR, false>(r, n)] = v;
+    }
   }
   __syncthreads();
   fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
-  C* out = dst.at(u, c, g.npts) + (long)row0 * N;
+  if (vec) {
 #pragma unroll
-  for (int e = threadIdx.x; e < NR * N; e += NT) out[e] = s[sidx<N, NR, false>(e / N, e % N)];
+    for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {
+      const int e = 2 * e2;
+      st2(out, e, s[sidx<N, NR, false>(e / N, e % N)], s[sidx<N, NR, false>(e / N, e % N + 1)]);
+    }
+  } else {
+#pragma unroll
+    for (int e = threadIdx.x; e < NR * N; e += NT) out[e] = s[sidx<N, NR, false>(e / N, e % N)];
+  }
   if (norm_acc) {
     const double t = block_sum((double)acc, red);
     if (threadIdx.x == 0) atomicAdd(&norm_acc[u], t);
@@ -512,13 +553,16 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     // z = M^-1 u from this transform, w = u + delta z stored as v_{j+1}; the
     // inner products follow in k_dcgs_gram.
     const long vj = (((long)u * (g.m + 2) + ep.jj) * g.ncomp + c) * g.npts + off;
+    C* wout = g.V + vj + (long)g.ncomp * g.npts;
 #pragma unroll
-    for (int e = threadIdx.x; e < NR * N; e += NT) {
-      const C val = s[sidx<N, NR, false>(e / N, e % N)];
-      const C v = g.V[vj + e];
-      const C dz = cmul(dl[e], val);
-      C w; w.x = v.x + dz.x; w.y = v.y + dz.y;
-      g.V[vj + (long)g.ncomp * g.npts + e] = w;
+    for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {   // pairs: 16-byte accesses in FP32
+      const int e = 2 * e2;
+      C v0, v1, d0, d1, w0, w1;
+      ld2(g.V + vj, e, v0, v1);
+      ld2(dl, e, d0, d1);
+      const C z0 = cmul(d0, s[sidx<N, NR, false>(e / N, e % N)]), z1 = cmul(d1, s[sidx<N, NR, false>(e / N, e % N + 1)]);
+      w0.x = v0.x + z0.x; w0.y = v0.y + z0.y; w1.x = v1.x + z1.x; w1.y = v1.y + z1.y;
+      st2(wout, e, w0, w1);
     }
   } else {
   double acc = 0.0, acc2 = 0.0, accr = 0.0, acci = 0.0;
@@ -763,6 +807,7 @@ __global__ void __launch_bounds__(NT) k_psi_combine(GV<T> g, int beam) {
 template <typename T> __device__ __forceinline__ typename Cx<T>::t* vslot(const GV<T>& g, int s, int jj) {
   return g.V + ((long)s * (g.m + 2) + jj) * g.ncomp * g.npts;
 }
+
 
 // Sum each of V per-lane values (V a power of two <= 32) over the warp: on
 // return v[0] of lane l holds the warp total of value l % V.  A butterfly halves
