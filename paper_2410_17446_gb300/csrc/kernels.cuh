@@ -731,12 +731,17 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   for (int c = 0; c < 2; ++c) {
     const C* a = A.at(u, c, g.npts) + off;
     const C* b = B.at(u, c, g.npts) + off;
-    for (int e = threadIdx.x; e < NR * N; e += NT) {
-      const int r = e / N, n = e % N;
-      const C x = a[e];
-      s[sidx<N, NVV, false>((c * 3 + 0) * NR + r, n)] = x;
-      s[sidx<N, NVV, false>((c * 3 + 1) * NR + r, n)] = cmul(x, ik_factor<C>(n, N, g.kx0));
-      s[sidx<N, NVV, false>((c * 3 + 2) * NR + r, n)] = b[e];
+    for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {   // point pairs: 16-byte accesses in FP32
+      const int e = 2 * e2, r = e / N, n = e % N;
+      C x[2], y[2];
+      ld2(a, e, x[0], x[1]);
+      ld2(b, e, y[0], y[1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        s[sidx<N, NVV, false>((c * 3 + 0) * NR + r, n + h)] = x[h];
+        s[sidx<N, NVV, false>((c * 3 + 1) * NR + r, n + h)] = cmul(x[h], ik_factor<C>(n + h, N, g.kx0));
+        s[sidx<N, NVV, false>((c * 3 + 2) * NR + r, n + h)] = y[h];
+      }
     }
   }
   __syncthreads();
@@ -744,37 +749,59 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   const C* cf = g.psi + (long)beam * 5 * g.npts + off;    // D1, D2, X, px, py planes
   const long F = 2 * g.npts;
   double acc = 0.0, acc2 = 0.0;
+  for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {   // point pairs: 16-byte accesses in FP32
+    const int e = 2 * e2, r = e / N, n0 = e % N;
+    C cD1[2], cD2[2], cX[2], cpx[2], cpy[2], d1v[2], d2v[2], z1v[2], z2v[2];
+    ld2(cf, e, cD1[0], cD1[1]);
+    ld2(cf + g.npts, e, cD2[0], cD2[1]);
+    ld2(cf + 2 * g.npts, e, cX[0], cX[1]);
+    ld2(cf + 3 * g.npts, e, cpx[0], cpx[1]);
+    ld2(cf + 4 * g.npts, e, cpy[0], cpy[1]);
 #pragma unroll
-  for (int q = 0; q < TPT; ++q) {
-    const int e = threadIdx.x + q * NT, r = e / N, n = e % N;
-    const C z1 = s[sidx<N, NVV, false>(0 * NR + r, n)], x1 = s[sidx<N, NVV, false>(1 * NR + r, n)],
-            y1 = s[sidx<N, NVV, false>(2 * NR + r, n)];
-    const C z2 = s[sidx<N, NVV, false>(3 * NR + r, n)], x2 = s[sidx<N, NVV, false>(4 * NR + r, n)],
-            y2 = s[sidx<N, NVV, false>(5 * NR + r, n)];
-    const C D1 = cf[e], D2 = cf[g.npts + e], X = cf[2 * g.npts + e], px = cf[3 * g.npts + e], py = cf[4 * g.npts + e];
-    C d1 = cmul(D1, z1), d2 = cmul(X, z1), t;
-    t = cmul(X, z2);  d1.x += t.x; d1.y += t.y;
-    t = cmul(px, x1); d1.x += t.x; d1.y += t.y;
-    t = cmul(py, x2); d1.x += t.x; d1.y += t.y;
-    t = cmul(D2, z2); d2.x += t.x; d2.y += t.y;
-    t = cmul(px, y1); d2.x += t.x; d2.y += t.y;
-    t = cmul(py, y2); d2.x += t.x; d2.y += t.y;
+    for (int h = 0; h < 2; ++h) {
+      const int n = n0 + h;
+      const C z1 = s[sidx<N, NVV, false>(0 * NR + r, n)], x1 = s[sidx<N, NVV, false>(1 * NR + r, n)],
+              y1 = s[sidx<N, NVV, false>(2 * NR + r, n)];
+      const C z2 = s[sidx<N, NVV, false>(3 * NR + r, n)], x2 = s[sidx<N, NVV, false>(4 * NR + r, n)],
+              y2 = s[sidx<N, NVV, false>(5 * NR + r, n)];
+      const C D1 = cD1[h], D2 = cD2[h], X = cX[h], px = cpx[h], py = cpy[h];
+      C d1 = cmul(D1, z1), d2 = cmul(X, z1), t;
+      t = cmul(X, z2);  d1.x += t.x; d1.y += t.y;
+      t = cmul(px, x1); d1.x += t.x; d1.y += t.y;
+      t = cmul(py, x2); d1.x += t.x; d1.y += t.y;
+      t = cmul(D2, z2); d2.x += t.x; d2.y += t.y;
+      t = cmul(px, y1); d2.x += t.x; d2.y += t.y;
+      t = cmul(py, y2); d2.x += t.x; d2.y += t.y;
+      d1v[h] = d1; d2v[h] = d2; z1v[h] = z1; z2v[h] = z2;
+    }
     if (mode == VEPI_ARNOLDI) {   // w = u + (Z - Z_fs) M^-1 u, stored as v_{j+1}
-      const long vj = ((long)u * (g.m + 2) + jj) * F + off + e;
-      const C v1 = g.V[vj], v2 = g.V[vj + g.npts];
-      C w1, w2;
-      w1.x = v1.x + d1.x; w1.y = v1.y + d1.y;
-      w2.x = v2.x + d2.x; w2.y = v2.y + d2.y;
-      g.V[vj + F] = w1; g.V[vj + F + g.npts] = w2;
+      const long vj = ((long)u * (g.m + 2) + jj) * F + off;
+      C v1[2], v2[2], w1[2], w2[2];
+      ld2(g.V + vj, e, v1[0], v1[1]);
+      ld2(g.V + vj + g.npts, e, v2[0], v2[1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        w1[h].x = v1[h].x + d1v[h].x; w1[h].y = v1[h].y + d1v[h].y;
+        w2[h].x = v2[h].x + d2v[h].x; w2[h].y = v2[h].y + d2v[h].y;
+      }
+      st2(g.V + vj + F, e, w1[0], w1[1]);
+      st2(g.V + vj + F + g.npts, e, w2[0], w2[1]);
     } else if (mode == VEPI_R0) {
-      const long rb = (long)u * F + off + e;
-      C m1, m2; m1.x = -d1.x; m1.y = -d1.y; m2.x = -d2.x; m2.y = -d2.y;
-      g.R0[rb] = m1; g.R0[rb + g.npts] = m2;
-      acc += (double)m1.x * m1.x + (double)m1.y * m1.y + (double)m2.x * m2.x + (double)m2.y * m2.y;
-      acc2 += (double)z1.x * z1.x + (double)z1.y * z1.y + (double)z2.x * z2.x + (double)z2.y * z2.y;
+      const long rb = (long)u * F + off;
+      C m1[2], m2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        m1[h].x = -d1v[h].x; m1[h].y = -d1v[h].y; m2[h].x = -d2v[h].x; m2[h].y = -d2v[h].y;
+        acc += (double)m1[h].x * m1[h].x + (double)m1[h].y * m1[h].y + (double)m2[h].x * m2[h].x +
+               (double)m2[h].y * m2[h].y;
+        acc2 += (double)z1v[h].x * z1v[h].x + (double)z1v[h].y * z1v[h].y + (double)z2v[h].x * z2v[h].x +
+                (double)z2v[h].y * z2v[h].y;
+      }
+      st2(g.R0 + rb, e, m1[0], m1[1]);
+      st2(g.R0 + rb + g.npts, e, m2[0], m2[1]);
     } else {
-      out.at(u, 0, g.npts)[off + e] = d1;
-      out.at(u, 1, g.npts)[off + e] = d2;
+      st2(out.at(u, 0, g.npts) + off, e, d1v[0], d1v[1]);
+      st2(out.at(u, 1, g.npts) + off, e, d2v[0], d2v[1]);
     }
   }
   if (mode == VEPI_R0) {
