@@ -384,10 +384,14 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
 // at entry, so every byte a CTA needs is in flight at once; the result leaves
 // by TMA tensor stores.  Same arithmetic as k_cols (no d/dy branch).  Tensor
 // maps view a buffer as [items][ny][nx] elements, item = unit * ncomp + c.
-template <typename T, int NY, int NV, int NT>
+// DY: also the d/dy branch (i ky times the multiplied spectrum) into a second
+// tile, stored through mdy; it uses the multiplier tile's room (no DY pass
+// multiplies by the table).
+template <typename T, int NY, int NV, int NT, bool DY>
 __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant__ CUtensorMap msrc,
                                                  const __grid_constant__ CUtensorMap mdst,
-                                                 const __grid_constant__ CUtensorMap mtab, int mask, int fwd, int mul,
+                                                 const __grid_constant__ CUtensorMap mtab,
+                                                 const __grid_constant__ CUtensorMap mdy, int mask, int fwd, int mul,
                                                  int inv, int skip_homog, int pole, T scale,
                                                  Buf<typename Cx<T>::t> spec) {
   using C = typename Cx<T>::t;
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   const uint32_t pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
   C* s = reinterpret_cast<C*>(smem_raw + pad);
   C* tws = s + NY * NV;                       // twiddles
-  C* tab = tws + NY;                          // multiplier tile (MUL_TABLE)
+  C* tab = tws + NY;                          // multiplier tile (MUL_TABLE), or the d/dy tile (DY)
   __shared__ __align__(8) uint64_t bar;
   const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
@@ -410,6 +414,7 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   // tensor maps, 16-byte x offsets; on a violation record it and do nothing
   if ((smem_u32(s) & 127u) || (smem_u32(tab) & 127u) || (reinterpret_cast<uintptr_t>(&msrc) & 63u) ||
       (reinterpret_cast<uintptr_t>(&mdst) & 63u) || (reinterpret_cast<uintptr_t>(&mtab) & 63u) ||
+      (reinterpret_cast<uintptr_t>(&mdy) & 63u) ||
       ((x0 * (int)sizeof(C)) & 15) || ((BR * NV * (int)sizeof(C)) & 127)) {
     if (threadIdx.x == 0) atomicExch(g.err, 2);
     return;
@@ -463,14 +468,21 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
         a = cmul(a, f);
       }
       s[e] = a;
+      if constexpr (DY) tab[e] = cmul(a, ik_factor<C>(n, g.ny, g.ky0));
     }
     __syncthreads();
   }
-  if (inv) fft_smem<C, NY, true, NV, NT, true, true>(s, tws, threadIdx.x);
+  if (inv) {
+    fft_smem<C, NY, true, NV, NT, true, true>(s, tws, threadIdx.x);
+    if constexpr (DY) fft_smem<C, NY, true, NV, NT, true, true>(tab, tws, threadIdx.x);
+  }
   fence_proxy_async_smem();   // this thread's tile writes, before the TMA store reads them
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int r = 0; r < NY; r += BR) tma_store_3d(&mdst, x0 * EW, r, item, s + r * NV);
+    for (int r = 0; r < NY; r += BR) {
+      tma_store_3d(&mdst, x0 * EW, r, item, s + r * NV);
+      if constexpr (DY) tma_store_3d(&mdy, x0 * EW, r, item, tab + r * NV);
+    }
     bulk_commit();
     bulk_wait_read();
   }

@@ -82,9 +82,9 @@ struct Group {
   bool stats_zero;         // per-system statistics already record a homogeneous step
   bool carry;              // Btmp holds the forward row DFT of the current field (from the last step)
   std::vector<int> nonhomog_host;
-  // TMA tensor maps of the column pass: Btmp [nb*C][ny][nx], Tmp [nsys*C][ny][nx], basemul [1][ny][nx]
-  bool tma;
-  CUtensorMap tm_btmp, tm_tmp, tm_tab;
+  // TMA tensor maps of the column pass: Btmp [nb*C][ny][nx], Tmp and Tmp2 [nsys*C][ny][nx], basemul [1][ny][nx]
+  bool tma, tma_dy;
+  CUtensorMap tm_btmp, tm_tmp, tm_tab, tm_tmp2;
 };
 
 }  // namespace
@@ -273,17 +273,17 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
 }
 
 // Tensor maps for a column pass: source, destination and (MUL_TABLE) multiplier.
-struct ColMaps { const CUtensorMap* src; const CUtensorMap* dst; const CUtensorMap* tab; };
+struct ColMaps { const CUtensorMap* src; const CUtensorMap* dst; const CUtensorMap* tab; const CUtensorMap* dy; };
 
 template <typename T, int NY, bool DY>
 cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
                     int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
                     Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy, ColMaps cm) {
   using C = typename Cx<T>::t;
-  if (!DY && cm.src && cm.dst && (mul != MUL_TABLE || cm.tab)) {
+  if (cm.src && cm.dst && (mul != MUL_TABLE || cm.tab) && (!DY || (cm.dy && mul != MUL_TABLE))) {
     constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
-    const size_t sm = ((size_t)NY * NV * (mul == MUL_TABLE ? 2 : 1) + NY) * sizeof(C) + 128;   // + twiddles, slack
-    auto k = k_cols_tma<T, NY, NV, NT>;
+    const size_t sm = ((size_t)NY * NV * (mul == MUL_TABLE || DY ? 2 : 1) + NY) * sizeof(C) + 128;   // + twiddles, slack
+    auto k = k_cols_tma<T, NY, NV, NT, DY>;
     static bool attr = false;
     if (!attr) {   // room for the table tile whatever this launch needs
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -292,8 +292,8 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
       attr = true;
     }
     dim3 grid(g.nx / NV, units * g.ncomp);
-    k<<<grid, NT, sm, st>>>(g, *cm.src, *cm.dst, cm.tab ? *cm.tab : *cm.src, mask, fwd, mul, inv, skip, pole, scale,
-                            spec);
+    k<<<grid, NT, sm, st>>>(g, *cm.src, *cm.dst, cm.tab ? *cm.tab : *cm.src, cm.dy ? *cm.dy : *cm.src, mask, fwd, mul,
+                            inv, skip, pole, scale, spec);
     return cudaGetLastError();
   }
   constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>() * (DY ? 2 : 1) > 256 ? 256 : cols_nt<T, NY>() * (DY ? 2 : 1);
@@ -367,7 +367,7 @@ cudaError_t cols(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>:
                  int inv, int skip, int pole, T scale, int units, cudaStream_t st,
                  Buf<typename Cx<T>::t> spec = Buf<typename Cx<T>::t>{nullptr, 0, 1},
                  Buf<typename Cx<T>::t> dy = Buf<typename Cx<T>::t>{nullptr, 0, 1},
-                 ColMaps cm = ColMaps{nullptr, nullptr, nullptr}) {
+                 ColMaps cm = ColMaps{nullptr, nullptr, nullptr, nullptr}) {
 #define CALL(N) cols_n<T, N>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, units, st, spec, dy, cm)
   PROP_SIZE_SWITCH(g.ny, CALL)
 #undef CALL
@@ -578,8 +578,9 @@ template <typename T> int step_group(prop* h, Group& G) {
   const int gs_blocks = (int)((F + NT_VEC * EPT_GS - 1) / (NT_VEC * EPT_GS));
   const int gram_blocks = (int)((F + NT_VEC * EPT_GRAM - 1) / (NT_VEC * EPT_GRAM));
 
-  const ColMaps bmaps = G.tma ? ColMaps{&G.tm_btmp, &G.tm_btmp, &G.tm_tab} : ColMaps{nullptr, nullptr, nullptr};
-  const ColMaps tmaps = G.tma ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr} : ColMaps{nullptr, nullptr, nullptr};
+  const ColMaps bmaps = G.tma ? ColMaps{&G.tm_btmp, &G.tm_btmp, &G.tm_tab, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
+  const ColMaps tmaps = G.tma ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
+  const ColMaps dmaps = G.tma_dy ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr, &G.tm_tmp2} : ColMaps{nullptr, nullptr, nullptr, nullptr};
   const Buf<C> none{nullptr, 0, 1};
   int* ulist = (int*)(h->ws + G.off.ulist);
   GV<T> ga = g;            // the Arnoldi launches of a batch: grid rows = the listed iterating systems
@@ -691,7 +692,7 @@ template <typename T> int step_group(prop* h, Group& G) {
         CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
       { Prof p_(h, K_COLS, 3 * cs * endp);
         CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
-                   Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+                   Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
       { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
         CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 2) * F), ST_CYCLE_END, 0,
                            VEPI_OPDIFF, 0, nsys, st)); }
@@ -748,7 +749,7 @@ template <typename T> int step_group(prop* h, Group& G) {
         if (Cn == 2) {
           { Prof p_(h, K_COLS, 0);
             CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, act0, st,
-                       Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+                       Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
           { Prof p_(h, K_ROWS_INV, 0);
             CK(rows_inv_vec<T>(ga, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, act0,
                                st)); }
@@ -819,7 +820,7 @@ template <typename T> int step_group(prop* h, Group& G) {
         CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
       { Prof p_(h, K_COLS, 3 * cs * endp);
         CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
-                   Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F))); }
+                   Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
       { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
         CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 2) * F), ST_CYCLE_END, 0,
                            VEPI_OPDIFF, 0, nsys, st)); }
@@ -1007,6 +1008,8 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
     G.tma = make_col_map(&G.tm_btmp, h->ws + G.off.Btmp, G.nx, G.ny, nb * h->C, csz, nv) &&
             make_col_map(&G.tm_tmp, h->ws + G.off.Tmp, G.nx, G.ny, nb * h->P * h->C, csz, nv) &&
             make_col_map(&G.tm_tab, h->ws + G.off.basemul, G.nx, G.ny, 1, csz, nv);
+    G.tma_dy = G.tma && h->C == 2 &&
+               make_col_map(&G.tm_tmp2, h->ws + G.off.Tmp2, G.nx, G.ny, nb * h->P * h->C, csz, nv);
   }
   *out = h;
   return PROP_OK;
