@@ -164,6 +164,15 @@ int prop_get_profile(prop* h, prop_kernel_profile* out);
 
 const char* prop_error_string(int status);
 
+/* Self-test of the failure path of the asynchronous tile copies (the paper has
+ * no counterpart).  Launches one CTA that waits on an mbarrier whose copy never
+ * comes; the bounded wait gives up after about one second and sets an error
+ * word.  Returns PROP_E_TIMEOUT when the bound works (the expected result),
+ * PROP_OK if the wait somehow completed, PROP_E_CUDA on a runtime error.  No
+ * copy is ever in flight and the CUDA context stays usable.  Synchronises the
+ * stream; stream may be NULL (the default stream). */
+int prop_selftest_wait_timeout(void* stream);
+
 /* Release the handle (host memory only; the workspace stays the caller's). */
 void prop_destroy(prop* h);
 

@@ -1636,6 +1636,17 @@ __global__ void k_collect(const SysState* st, int nsys, int* iters, int* cycles,
   }
 }
 
+// Self-test of the bounded wait: one thread announces 16 bytes of transaction
+// that no copy will deliver, every thread waits, the wait gives up after its
+// time limit and records the failure in *err.  No copy is ever in flight.
+__global__ void k_selftest_wait(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) { mbar_init(&bar, 1); fence_mbar_init(); }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+  mbar_wait(&bar, 0, err);
+}
+
 // Compacted list of the systems in state ST_ITER, in index order (one block of
 // a multiple of 32 threads): the Arnoldi launches of a batch cover only these.
 __global__ void k_active_list(const SysState* st, int nsys, int* list) {

@@ -937,6 +937,9 @@ size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, i
 
 }  // namespace
 
+// error word of prop_selftest_wait_timeout
+static __device__ int g_selftest_err;
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1167,6 +1170,20 @@ int prop_get_iterations(prop* h, int32_t* iters) {
   if (rc) return rc;
   std::memcpy(iters, it.data(), it.size() * sizeof(int));
   return PROP_OK;
+}
+
+int prop_selftest_wait_timeout(void* stream) {
+  static int* flag = nullptr;   // device address of g_selftest_err (current device at first call)
+  if (!flag && cudaGetSymbolAddress((void**)&flag, g_selftest_err) != cudaSuccess) { flag = nullptr; return PROP_E_CUDA; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int e = 0;
+  if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return PROP_E_CUDA;
+  k_selftest_wait<<<1, 64, 0, st>>>(flag);
+  if (cudaGetLastError() != cudaSuccess) return PROP_E_CUDA;
+  if (cudaMemcpyAsync(&e, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PROP_E_CUDA;
+  return async_status(e);
 }
 
 const char* prop_error_string(int status) {

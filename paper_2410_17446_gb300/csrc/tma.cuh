@@ -1,8 +1,9 @@
 // Asynchronous tile movement for the FFT passes (sm_100-family PTX): mbarrier
 // completion tracking and TMA tensor copies for strided column tiles.
 //
-// Every wait on an mbarrier is bounded: after MBAR_SPIN_LIMIT polls the
-// waiting thread records the failure in the workspace error word and gives up,
+// Every wait on an mbarrier is bounded: after MBAR_TIMEOUT_NS of the global
+// timer (or MBAR_SPIN_LIMIT polls) the waiting thread records the failure in
+// the workspace error word and gives up,
 // so a copy that never lands ends as an error status on the host instead of a
 // hung kernel.
 #pragma once
@@ -12,6 +13,7 @@
 namespace prop_dev {
 
 constexpr int MBAR_SPIN_LIMIT = 1 << 22;
+constexpr unsigned long long MBAR_TIMEOUT_NS = 1000000000ull;   // one second
 
 // Rows per TMA box of a column tile: a divisor of ny no larger than 256 (the
 // box limit), so the boxes tile the column exactly (384 -> 192, 768 -> 256).
@@ -45,10 +47,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // Bounded wait for phase `parity` of the barrier; false (and *err set) on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  for (int it = 0; it < MBAR_SPIN_LIMIT; ++it)
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < MBAR_SPIN_LIMIT; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && global_ns() - t0 > MBAR_TIMEOUT_NS) break;
+  }
   atomicExch(err, 1);
   return false;
 }

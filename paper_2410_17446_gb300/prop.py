@@ -85,6 +85,7 @@ _SIGS = {
     "prop_get_net_io": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p]),
     "prop_fft2_noalloc": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
                                      ct.c_void_p]),
+    "prop_selftest_wait_timeout": (ct.c_int, [ct.c_void_p]),
     # learned initial guess (include/prop_cnn.h)
     "prop_cnn_conv": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                  ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int32,
