@@ -1376,11 +1376,11 @@ __device__ void dcgs_control(SysState& q, int s, int j, const double2* bs, const
 //   u_{j+1} = w / rho - sum_{i<j} gamma_i v_i - gamma_j q_j  (written over w = v_{j+1})
 // gamma_i = b_i / rho (i < j), gamma_j = (d - a^H b) / rho^2, with coefficients
 // each CTA derives from the folded sums; the last CTA runs dcgs_control.
-// The sweep takes the basis in groups of 8 vectors (8*EPT loads in flight).
+// The sweep takes the basis in groups of GVEC vectors (GVEC*EPT loads in flight).
 // If the control ends the cycle at this step the sweep's output goes unused.
 // grid.x = 1 + sweep CTAs: CTA 0 is the control, CTA x > 0 sweeps chunks
 // x - 1, x - 1 + (gridDim.x - 1), ... (one coefficient prologue per CTA).
-template <typename T, int NT, int EPT>
+template <typename T, int NT, int EPT, int GVEC>
 __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   using C = typename Cx<T>::t;
   __shared__ double2 bs[MMAX + 1], as[MMAX + 1];
@@ -1452,10 +1452,10 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
     qv[e] = C{}; x[e] = C{};
     if (p < L) { qv[e] = uj[p]; const C w = wj[p]; x[e].x = w.x * ir; x[e].y = w.y * ir; }
   }
-  for (int i0 = 0; i0 < jj; i0 += 8) {
-    C vv[8][EPT];
+  for (int i0 = 0; i0 < jj; i0 += GVEC) {
+    C vv[GVEC][EPT];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < GVEC; ++k) {
       const C* v = vslot(g, s, i0 + k);
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
@@ -1464,7 +1464,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
       }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < GVEC; ++k) {
       const C a = ca[i0 + k], gm = cg[i0 + k];   // vv is zero past v_{j-1}: padded terms vanish
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {

@@ -60,7 +60,8 @@ constexpr int clamp_nt(int t) { return t < 64 ? 64 : (t > 256 ? 256 : t); }
 template <int N> constexpr int rows_nt() { return clamp_nt(rows_nr<N>() * N / 16); }
 template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * cols_per_cta<T>() / 16); }
 constexpr int NT_VEC = 256;
-constexpr int EPT_GS = 2;     // points per thread of the update sweep
+constexpr int EPT_GS = 4;     // points per thread of the update sweep
+constexpr int GVEC_GS = 4;    // basis vectors per load group of the update sweep
 constexpr int EPT_GRAM = 4;   // points per thread of the Gram sweep
 constexpr int GVEC_GRAM = 4;  // basis vectors per transpose-reduce of the Gram sweep
 constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host reads of the GMRES state
@@ -771,7 +772,7 @@ template <typename T> int step_group(prop* h, Group& G) {
         sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
         sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = counts + 3 * (jj - jj0 + 1);
         const int cap = std::max(1, 4 * sm_count() / std::max(act0, 1));
-        k_dcgs_step<T, NT_VEC, EPT_GS><<<dim3(std::min(gs_blocks, cap) + 1, act0), NT_VEC, 0, st>>>(ga, jj, sa); }
+        k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS><<<dim3(std::min(gs_blocks, cap) + 1, act0), NT_VEC, 0, st>>>(ga, jj, sa); }
       CK(cudaGetLastError());
       const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj == m;
       if (!sync_now) continue;
