@@ -160,58 +160,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
-// Sum a complex value over the warp in its own precision A (float on the FP32
-// path: GB300's FP64 pipe is a small fraction of its FP32 rate), then lane 0
-// adds it, widened to double, into a shared-memory slot.
-template <typename A> __device__ __forceinline__ void warp_add(A re, A im, double2* slot) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    re += __shfl_down_sync(0xffffffffu, re, o);
-    im += __shfl_down_sync(0xffffffffu, im, o);
-  }
-  if ((threadIdx.x & 31) == 0) { slot->x += (double)re; slot->y += (double)im; }
-}
-
-// After every warp has added its partials to red[w * (MMAX+1) + i], i <= n:
-// sum over warps and add the block total to acc[i] (one atomic per i).
-// acc points at stripe 0 of the target plane; this CTA adds to stripe blockIdx.x % NSTRIPE.
-__device__ __forceinline__ void flush_partials(double2* red, int nwarps, int n, double2* acc) {
-  __syncthreads();
-  double2* a = acc + (blockIdx.x % NSTRIPE) * (MMAX + 1);
-  for (int i = threadIdx.x; i <= n; i += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int w = 0; w < nwarps; ++w) { re += red[w * (MMAX + 1) + i].x; im += red[w * (MMAX + 1) + i].y; }
-    atomicAdd(&a[i].x, re);
-    atomicAdd(&a[i].y, im);
-  }
-}
-
-// warp_add into a slot of the working precision (per-warp partials of the FP32
-// path are float sums already; the cross-warp and cross-CTA sums are FP64).
-template <typename A, typename S> __device__ __forceinline__ void warp_acc(A re, A im, S* slot) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    re += __shfl_down_sync(0xffffffffu, re, o);
-    im += __shfl_down_sync(0xffffffffu, im, o);
-  }
-  if ((threadIdx.x & 31) == 0) { slot->x += re; slot->y += im; }
-}
-
-// flush_partials for per-warp slots red[w * (MMAX+1) + i] of type S: slots
-// 0..n-1 and, when extra >= 0, slot extra.  Caller synchronises first.
-template <typename S>
-__device__ __forceinline__ void flush_slots(const S* red, int nwarps, int n, double2* acc, int extra = -1) {
-  double2* a = acc + (blockIdx.x % NSTRIPE) * (MMAX + 1);
-  for (int t = threadIdx.x; t <= n; t += blockDim.x) {
-    const int i = (t == n) ? extra : t;
-    if (i < 0) continue;
-    double re = 0.0, im = 0.0;
-    for (int w = 0; w < nwarps; ++w) { re += (double)red[w * (MMAX + 1) + i].x; im += (double)red[w * (MMAX + 1) + i].y; }
-    atomicAdd(&a[i].x, re);
-    if (im != 0.0) atomicAdd(&a[i].y, im);
-  }
-}
-
 // Points p, p+1 (p even, 16-byte aligned) in one access: a float4 for complex
 // FP32, two 16-byte accesses for complex FP64.
 template <typename C> __device__ __forceinline__ void ld2(const C* base, long p, C& a, C& b) {
@@ -840,8 +788,9 @@ __global__ void __launch_bounds__(NT) k_psi_combine(GV<T> g, int beam) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched Krylov vector kernels.  grid = (chunks, nsys); each CTA owns a
-// contiguous chunk of the system's ncomp*npts points.
+// Batched Krylov vector kernels.  grid = (chunks, systems): a CTA works on
+// contiguous chunks of its system's ncomp*npts points (the Gram and update
+// sweeps loop over several chunks; the grid rows may come from the unit list).
 // ---------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ typename Cx<T>::t* vslot(const GV<T>& g, int s, int jj) {
   return g.V + ((long)s * (g.m + 2) + jj) * g.ncomp * g.npts;
@@ -1091,7 +1040,8 @@ __global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2*
 }
 
 // ---------------------------------------------------------------------------
-// GMRES control (one thread per system; tiny).
+// GMRES cycle control (one thread per system; tiny).  The per-step control
+// runs in the update kernel (dcgs_control).
 // ---------------------------------------------------------------------------
 
 // Begin a cycle for systems in state `from` (ST_DONE-initialised systems at a
