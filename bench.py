@@ -172,6 +172,21 @@ def run_oracle_sample(name: str, budget_s: float, max_steps: int) -> dict:
     return d
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest x over the ranks (the job's time is its slowest replica's)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ws: int, points: int, steps: int, seconds: float) -> float:
+    """Mpoint·steps/s of ws replicas that each advance `points` points by `steps` steps in `seconds`."""
+    return ws * points * steps / seconds / 1e6
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -301,23 +316,15 @@ def ours(args) -> None:
             for i, b in enumerate(W.beams):
                 prl.set_field(i, np.ascontiguousarray(b.w0))
         rl = timed(prl, clocks_on=False)
-        ml = rl["dev_ms"]
-        if ws > 1:
-            t = torch.tensor([ml], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ml = float(t.item())
-        learned = {"value": ws * W.points * args.steps / (ml / 1e3) / 1e6, "ms_per_step": ml / args.steps,
+        ml = max_over_ranks(rl["dev_ms"], ws, dev)
+        learned = {"value": whole_job_value(ws, W.points, args.steps, ml / 1e3), "ms_per_step": ml / args.steps,
                    "arnoldi_steps_total": int(rl["st"].total_iters), "net": net["meta"],
                    "guess_net_ms": round(rl["prof"]["guess_net"]["total_ms"], 3)}
         prl.close()
 
-    ms = dev_ms
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dev_ms, ws, dev)
     pts = W.points
-    value = ws * pts * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_value(ws, pts, args.steps, ms / 1e3)
 
     # accuracy over the configuration's own run length, where a closed form exists
     acc = None
@@ -363,11 +370,8 @@ def ours(args) -> None:
                     d2h += host_out[i].numel() * 16
             torch.cuda.synchronize(dev)
             e2e_s = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": ws * pts * args.steps / e2e_s / 1e6, "unit": UNIT,
+        e2e_s = max_over_ranks(e2e_s, ws, dev)
+        e2e = {"value": whole_job_value(ws, pts, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
 
     # roofline of the dominant kernel (largest device time in the timed region)
