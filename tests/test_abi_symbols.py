@@ -62,3 +62,24 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert P.lib().prop_create(1, good, -1.0, 1.0, 0.5, 1, d, d, d, ct.byref(o), None, 0, None,
                                ct.byref(h)) == P.PROP_E_ARG
     assert P.lib().prop_step(None) == P.PROP_E_ARG
+
+
+def test_workspace_holds_m_plus_2_basis_slots(lib):
+    """The Krylov basis keeps m + 2 vectors per system (slot j+1 takes w up to
+    step j = m): one more restart step adds exactly one vector per system."""
+    P = lib
+    grids = (P.prop_grid * 2)(P.prop_grid(256, 256, 0.25, 0.25), P.prop_grid(256, 256, 0.25, 0.25))
+    npoles = 12
+    sizes = {}
+    for prec, cs in ((P.PROP_FP32, 8), (P.PROP_FP64, 16)):
+        for m in (20, 21):
+            o = P.prop_default_opts(1, prec)
+            o.restart = m
+            n = ct.c_size_t()
+            assert P.lib().prop_workspace_size(2, grids, npoles, ct.byref(o), ct.byref(n)) == P.PROP_OK
+            sizes[(prec, m)] = n.value
+        assert sizes[(prec, 21)] - sizes[(prec, 20)] == 2 * npoles * 256 * 256 * cs
+    o = P.prop_default_opts(1, P.PROP_FP32)
+    o.restart = 65                                    # above the compiled maximum restart length
+    n = ct.c_size_t()
+    assert P.lib().prop_workspace_size(2, grids, npoles, ct.byref(o), ct.byref(n)) == P.PROP_E_ARG
