@@ -79,7 +79,16 @@ typedef struct prop_opts {
                               with mu_k >= 1 equalising each pole's share of the field error */
   int32_t guess;           /* PROP_GUESS_ZERO (x0 = 0) or PROP_GUESS_LEARNED (x0 from the network
                               installed by prop_set_guess_net; reserves activation memory)      */
+  int32_t precond;         /* GMRES right preconditioner (Sec. 4.2; the answer does not depend on it):
+                              PROP_PRECOND_FREESPACE: (Z_fs - p_k I)^-1, the n = n0 problem of
+                              Eq. Z_bar_fs_def; PROP_PRECOND_MEAN (default): (Z_fs + dbar - p_k I)^-1,
+                              the constant-index problem with n^2 = mean of n^2 over the beam's grid
+                              (dbar = mean delta), which carries the absorbing border's mean loss,
+                              as the paper's preconditioner carries its PML.  Both are diagonal in
+                              Fourier space. */
 } prop_opts;
+
+enum prop_precond { PROP_PRECOND_FREESPACE = 0, PROP_PRECOND_MEAN = 1 };
 
 enum prop_guess { PROP_GUESS_ZERO = 0, PROP_GUESS_LEARNED = 1 };
 #define PROP_GUESS_CHANNELS 16   /* padded input / output width of the guess network */
@@ -109,7 +118,8 @@ typedef struct prop_kernel_profile {
 
 typedef struct prop prop; /* opaque handle */
 
-/* Fill *o with the defaults for `precision` (tol 1e-12 FP64, 1e-7 FP32). */
+/* Fill *o with the defaults for `precision` (tol 1e-12 FP64, 1e-7 FP32; restart 20;
+ * PROP_GUESS_ZERO; PROP_PRECOND_MEAN). */
 int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision);
 
 /* Bytes of device workspace prop_create needs for these beams and options.

@@ -23,7 +23,21 @@ derivatives of an even-length grid; the Laplacian keeps -kx^2 at Nyquist.
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft
 import scipy.linalg
+
+# Threads of the 2-D transforms (scipy.fft's ``workers``); 1 unless a caller
+# that times the oracle on all host cores sets it.  Results do not depend on it
+# beyond rounding order.
+FFT_WORKERS = 1
+
+
+def fft2(v: np.ndarray) -> np.ndarray:
+    return scipy.fft.fft2(v, workers=FFT_WORKERS)
+
+
+def ifft2(v: np.ndarray) -> np.ndarray:
+    return scipy.fft.ifft2(v, workers=FFT_WORKERS)
 
 
 def wavenumbers(n: int, d: float) -> np.ndarray:
@@ -58,18 +72,18 @@ def psi_terms(n2: np.ndarray, dx: float, dy: float, k0n0: float) -> dict:
     """
     ny, nx = n2.shape
     psi = np.log(n2.astype(np.complex128))
-    P = np.fft.fft2(psi)
+    P = fft2(psi)
     ikx = first_derivative_symbol(nx, dx)[None, :]
     iky = first_derivative_symbol(ny, dy)[:, None]
     kx = wavenumbers(nx, dx)[None, :]
     ky = wavenumbers(ny, dy)[:, None]
     s = 1.0 / k0n0 ** 2
     return {
-        "x": s * np.fft.ifft2(ikx * P),
-        "y": s * np.fft.ifft2(iky * P),
-        "xx": s * np.fft.ifft2(-(kx ** 2) * P),
-        "yy": s * np.fft.ifft2(-(ky ** 2) * P),
-        "xy": s * np.fft.ifft2(ikx * iky * P),
+        "x": s * ifft2(ikx * P),
+        "y": s * ifft2(iky * P),
+        "xx": s * ifft2(-(kx ** 2) * P),
+        "yy": s * ifft2(-(ky ** 2) * P),
+        "xy": s * ifft2(ikx * iky * P),
     }
 
 
@@ -90,14 +104,14 @@ class Medium:
 
     # --- derivative helpers (spectral) ---
     def dxf(self, v):
-        return np.fft.ifft2(self.ikx * np.fft.fft2(v))
+        return ifft2(self.ikx * fft2(v))
 
     def dyf(self, v):
-        return np.fft.ifft2(self.iky * np.fft.fft2(v))
+        return ifft2(self.iky * fft2(v))
 
     def lap_t(self, v):
         """Scaled transverse Laplacian Dt v."""
-        return np.fft.ifft2(self.zfs * np.fft.fft2(v))
+        return ifft2(self.zfs * fft2(v))
 
     def apply_Z(self, v: np.ndarray) -> np.ndarray:
         """Z v for v of shape (ncomp, ny, nx), Eq. (Z_bar_eq)."""
@@ -125,7 +139,7 @@ class Medium:
         """
         out = np.empty_like(v, dtype=np.complex128)
         for c in range(v.shape[0]):
-            out[c] = np.fft.ifft2(np.fft.fft2(v[c]) / (self.zfs - pole))
+            out[c] = ifft2(fft2(v[c]) / (self.zfs - pole))
         return out
 
 

@@ -42,18 +42,38 @@ def solve_shifted_dense(med: ops.Medium, w: np.ndarray, pole: complex) -> np.nda
     return x.reshape(w.shape)
 
 
+def preconditioner_shift(med: ops.Medium, precond: str) -> complex:
+    """Constant medium of the preconditioner, as delta = (n^2 - n0^2)/n0^2.
+
+    "freespace": the n = n0 problem of Eq. Z_bar_fs_def (delta = 0).
+    "mean": the constant-index problem whose n^2 is the mean of the slab's n^2
+    over the grid, so delta = mean(delta).  Sec. 4.2 builds its free-space
+    preconditioner from the same difference matrices as Z, PML included; on the
+    periodic grid the absorber lives in Im n^2, and the mean carries its
+    average loss while keeping the solve diagonal in Fourier space.
+    """
+    if precond == "freespace":
+        return 0.0
+    if precond == "mean":
+        return complex(med.delta.mean())
+    raise ValueError(precond)
+
+
 def solve_shifted_gmres(med: ops.Medium, w: np.ndarray, pole: complex, restart: int = 20,
                         tol: float = 1e-12, max_cycles: int = 50,
-                        x0: Optional[np.ndarray] = None) -> gm.GmresResult:
-    """x = (Z - p I)^-1 w by GMRES right-preconditioned with (Z_fs - p I)."""
+                        x0: Optional[np.ndarray] = None, precond: str = "freespace") -> gm.GmresResult:
+    """x = (Z - p I)^-1 w by GMRES right-preconditioned with (Z_fs + dbar - p I),
+    dbar = preconditioner_shift(med, precond) (0 for the paper's free-space solve)."""
+    dbar = preconditioner_shift(med, precond)
     return gm.gmres(lambda v: med.apply_shifted(v, pole),
-                    lambda v: med.freespace_solve(v, pole),
+                    lambda v: med.freespace_solve(v, pole - dbar),
                     w, x0=x0, restart=restart, tol=tol, max_cycles=max_cycles)
 
 
 def step(med: ops.Medium, w: np.ndarray, table: aaa_lawson.PoleTable, solver: str = "gmres",
-         restart: int = 20, tol: float = 1e-12, max_cycles: int = 50):
-    """w(z+dz) = r0 w + sum_k r_k (Z - p_k)^-1 w  (Eq. approx_prop).  w: (ncomp, ny, nx)."""
+         restart: int = 20, tol: float = 1e-12, max_cycles: int = 50, precond: str = "freespace"):
+    """w(z+dz) = r0 w + sum_k r_k (Z - p_k)^-1 w  (Eq. approx_prop).  w: (ncomp, ny, nx).
+    ``precond`` only changes how GMRES reaches each (Z - p_k)^-1 w."""
     out = table.r0 * w
     its, rels = [], []
     for p, r in zip(table.poles, table.residues):
@@ -62,7 +82,7 @@ def step(med: ops.Medium, w: np.ndarray, table: aaa_lawson.PoleTable, solver: st
             its.append(0)
             rels.append(float(np.linalg.norm(med.apply_shifted(x, p) - w) / np.linalg.norm(w)))
         else:
-            res = solve_shifted_gmres(med, w, p, restart, tol, max_cycles)
+            res = solve_shifted_gmres(med, w, p, restart, tol, max_cycles, precond=precond)
             if not res.converged:
                 raise RuntimeError(f"GMRES did not converge for pole {p}: {res.rel_residual:.3e}")
             x = res.x
@@ -94,7 +114,7 @@ def homogeneous_rational_step(w: np.ndarray, dx: float, dy: float, k0n0: float,
     ny, nx = w.shape[-2:]
     z = ops.zeta_fs(nx, ny, dx, dy, k0n0)
     R = table(z) ** nsteps
-    return np.stack([np.fft.ifft2(R * np.fft.fft2(c)) for c in w.reshape(-1, ny, nx)]).reshape(w.shape)
+    return np.stack([ops.ifft2(R * ops.fft2(c)) for c in w.reshape(-1, ny, nx)]).reshape(w.shape)
 
 
 def angular_spectrum(w: np.ndarray, dx: float, dy: float, k0: float, n0: float, dz: float,
@@ -107,4 +127,4 @@ def angular_spectrum(w: np.ndarray, dx: float, dy: float, k0: float, n0: float, 
     ky = ops.wavenumbers(ny, dy)[:, None]
     kz = np.sqrt((k0 * n0) ** 2 - kx ** 2 - ky ** 2 + 0j)
     G = np.exp(1j * (kz - k0 * n0) * dz * nsteps)
-    return np.stack([np.fft.ifft2(G * np.fft.fft2(c)) for c in w.reshape(-1, ny, nx)]).reshape(w.shape)
+    return np.stack([ops.ifft2(G * ops.fft2(c)) for c in w.reshape(-1, ny, nx)]).reshape(w.shape)

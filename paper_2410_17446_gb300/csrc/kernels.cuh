@@ -64,6 +64,8 @@ template <typename T> struct GV {
   SysState* st;  // [nsys]
   double* bnorm2;       // [nb] ||w||^2 of the step's right-hand side
   int* nonhomog;        // [nb] 1 if delta != 0 somewhere
+  double2* dsum;        // [nb] sum of delta over the grid: the preconditioner's constant medium is
+                        //   its mean (the constant-index problem with n^2 = mean n^2)
   const double2* rk;    // [P] residues r_k
   const double* anorm;  // [2P]: bound on ||Z - p_k I|| over this grid (backward-error test), then the
                         //       per-pole tolerance factor mu_k >= 1 (error equidistribution)
@@ -110,8 +112,11 @@ template <typename C> struct Buf {
   }
 };
 
+// MUL_PREC_INV: the GMRES preconditioner (Z_fs + dbar - p)^-1, dbar = the beam's mean delta;
+// MUL_POLE_INV: the free-space solve (Z_fs - p)^-1 itself.
 enum MulMode { MUL_NONE = 0, MUL_TABLE = 1, MUL_POLE_INV = 2, MUL_POLE_FWD = 3, MUL_SCALE = 4,
-               MUL_DY = 5, MUL_DYY = 6 };   // scale * i ky,  scale * (-ky^2)
+               MUL_DY = 5, MUL_DYY = 6,   // scale * i ky,  scale * (-ky^2)
+               MUL_PREC_INV = 7 };
 enum EpiMode { EPI_STORE = 0, EPI_STORE64 = 1, EPI_ACCUM64 = 2, EPI_R0 = 3, EPI_ARNOLDI = 4,
                EPI_TRUERES = 5, EPI_OPERATOR = 6, EPI_ADD_E = 7 };
 
@@ -180,6 +185,13 @@ template <typename C> __device__ __forceinline__ void st2(C* base, long p, const
 
 __device__ __forceinline__ bool unit_active(const SysState* st, int mask, int u) {
   return mask < 0 || st[u].state == mask;
+}
+
+// Mean delta of a beam (the constant medium of its preconditioner), rounded to T.
+template <typename T> __device__ __forceinline__ typename Cx<T>::t dbar_of(const GV<T>& g, int beam) {
+  const double2 a = g.dsum[beam];
+  const double inv = 1.0 / (double)g.npts;
+  return to_c(make_double2(a.x * inv, a.y * inv), T());
 }
 
 // ---------------------------------------------------------------------------
@@ -274,11 +286,14 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
     for (int e = threadIdx.x; e < NY * NV; e += NT) sp[(long)(e / NV) * g.nx + x0 + e % NV] = s[(e / NV) * W + e % NV];
   }
   if (mul != MUL_NONE) {
-    const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD);
+    const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD || mul == MUL_PREC_INV);
     const int k = pm ? (pole >= 0 ? pole : u % g.P) : 0;
     const T* ax = pm ? g.ax + (long)k * g.nx * 2 : nullptr;
     const T* ay = pm ? g.ay + (long)k * g.ny * 2 : nullptr;
-    const T pim = pm ? g.pim[k] : (T)0;
+    // the preconditioner's pole is p - dbar: Re shifted by +Re dbar, -Im p by +Im dbar
+    C sh; sh.x = 0; sh.y = 0;
+    if (mul == MUL_PREC_INV) sh = dbar_of(g, u / g.P);
+    const T pim = pm ? g.pim[k] + sh.y : (T)0;
     for (int e = threadIdx.x; e < NY * NV; e += NT) {
       const int n = e / NV, v = e % NV, i = x0 + v;
       C a = s[n * W + v];
@@ -295,9 +310,9 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
       } else {
         // Re(zeta_fs - p) = ax + ay from (hi, lo) pairs: the hi parts cancel
         // exactly near the pole (Sterbenz), the lo parts restore the rest.
-        const T re = (ax[2 * i] + ay[2 * n]) + (ax[2 * i + 1] + ay[2 * n + 1]);
+        const T re = ((ax[2 * i] + ay[2 * n]) + (ax[2 * i + 1] + ay[2 * n + 1])) + sh.x;
         C f;
-        if (mul == MUL_POLE_INV) {
+        if (mul != MUL_POLE_FWD) {
           const T d = scale / (re * re + pim * pim);
           f.x = re * d; f.y = -pim * d;
         } else {
@@ -386,11 +401,14 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
     for (int e = threadIdx.x; e < NY * NV; e += NT) sp[(long)(e / NV) * g.nx + x0 + e % NV] = s[e];
   }
   if (mul != MUL_NONE) {
-    const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD);
+    const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD || mul == MUL_PREC_INV);
     const int k = pm ? (pole >= 0 ? pole : u % g.P) : 0;
     const T* ax = pm ? g.ax + (long)k * g.nx * 2 : nullptr;
     const T* ay = pm ? g.ay + (long)k * g.ny * 2 : nullptr;
-    const T pim = pm ? g.pim[k] : (T)0;
+    // the preconditioner's pole is p - dbar: Re shifted by +Re dbar, -Im p by +Im dbar
+    C sh; sh.x = 0; sh.y = 0;
+    if (mul == MUL_PREC_INV) sh = dbar_of(g, u / g.P);
+    const T pim = pm ? g.pim[k] + sh.y : (T)0;
     for (int e = threadIdx.x; e < NY * NV; e += NT) {
       const int n = e / NV, v = e % NV, i = x0 + v;
       C a = s[e];
@@ -405,9 +423,9 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
         const T kk = (T)ffreq(n, g.ny) * g.ky0;
         a.x *= -kk * kk * scale; a.y *= -kk * kk * scale;
       } else {   // as in k_cols: Re(zeta_fs - p) from (hi, lo) pairs
-        const T re = (ax[2 * i] + ay[2 * n]) + (ax[2 * i + 1] + ay[2 * n + 1]);
+        const T re = ((ax[2 * i] + ay[2 * n]) + (ax[2 * i + 1] + ay[2 * n + 1])) + sh.x;
         C f;
-        if (mul == MUL_POLE_INV) {
+        if (mul != MUL_POLE_FWD) {
           const T d = scale / (re * re + pim * pim);
           f.x = re * d; f.y = -pim * d;
         } else {
@@ -510,16 +528,19 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   const long unit_off = ((long)u * g.ncomp + c) * g.npts + off;   // [unit][c][pt] arrays
   if constexpr (ARN) {
     // Arnoldi step: u = v_j (the candidate left by the last update pass),
-    // z = M^-1 u from this transform, w = u + delta z stored as v_{j+1}; the
-    // inner products follow in k_dcgs_gram.
+    // z = M^-1 u from this transform with M = Z_fs + dbar - p, and
+    // w = (Z - p) z = u + (delta - dbar) z stored as v_{j+1}; the inner products
+    // follow in k_dcgs_gram.
     const long vj = (((long)u * (g.m + 2) + ep.jj) * g.ncomp + c) * g.npts + off;
     C* wout = g.V + vj + (long)g.ncomp * g.npts;
+    const C db = dbar_of(g, beam);
 #pragma unroll
     for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {   // pairs: 16-byte accesses in FP32
       const int e = 2 * e2;
       C v0, v1, d0, d1, w0, w1;
       ld2(g.V + vj, e, v0, v1);
       ld2(dl, e, d0, d1);
+      d0.x -= db.x; d0.y -= db.y; d1.x -= db.x; d1.y -= db.y;
       const C z0 = cmul(d0, s[sidx<N, NR, false>(e / N, e % N)]), z1 = cmul(d1, s[sidx<N, NR, false>(e / N, e % N + 1)]);
       w0.x = v0.x + z0.x; w0.y = v0.y + z0.y; w1.x = v1.x + z1.x; w1.y = v1.y + z1.y;
       st2(wout, e, w0, w1);
@@ -734,15 +755,17 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
       t = cmul(py, y2); d2.x += t.x; d2.y += t.y;
       d1v[h] = d1; d2v[h] = d2; z1v[h] = z1; z2v[h] = z2;
     }
-    if (mode == VEPI_ARNOLDI) {   // w = u + (Z - Z_fs) M^-1 u, stored as v_{j+1}
+    if (mode == VEPI_ARNOLDI) {   // w = u + (Z - Z_fs - dbar) z, z = M^-1 u, stored as v_{j+1}
       const long vj = ((long)u * (g.m + 2) + jj) * F + off;
+      const C db = dbar_of(g, beam);
       C v1[2], v2[2], w1[2], w2[2];
       ld2(g.V + vj, e, v1[0], v1[1]);
       ld2(g.V + vj + g.npts, e, v2[0], v2[1]);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        w1[h].x = v1[h].x + d1v[h].x; w1[h].y = v1[h].y + d1v[h].y;
-        w2[h].x = v2[h].x + d2v[h].x; w2[h].y = v2[h].y + d2v[h].y;
+        const C t1 = cmul(db, z1v[h]), t2 = cmul(db, z2v[h]);
+        w1[h].x = v1[h].x + d1v[h].x - t1.x; w1[h].y = v1[h].y + d1v[h].y - t1.y;
+        w2[h].x = v2[h].x + d2v[h].x - t2.x; w2[h].y = v2[h].y + d2v[h].y - t2.y;
       }
       st2(g.V + vj + F, e, w1[0], w1[1]);
       st2(g.V + vj + F + g.npts, e, w2[0], w2[1]);
@@ -1017,25 +1040,32 @@ __global__ void __launch_bounds__(NT) k_field_io(GV<T> g, int slot, double2* sta
   }
 }
 
-// delta = (n^2 - n0^2)/n0^2 from a complex128 slab; flags a non-zero delta;
+// delta = (n^2 - n0^2)/n0^2 from a complex128 slab; flags a non-zero delta and
+// adds its sum (of the values as rounded to T) into dsum[beam];
 // with psi_out also writes psi = Log n^2 (principal branch) for the vector operator.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2* n2, double n0sq,
                                                typename Cx<T>::t* psi_out) {
   using C = typename Cx<T>::t;
   C* d = g.delta + (long)beam * g.npts;
+  __shared__ double red[32];
   int nz = 0;
+  double sr = 0.0, si = 0.0;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < g.npts; p += (long)gridDim.x * NT) {
     const double2 a = n2[p];
     double2 v; v.x = (a.x - n0sq) / n0sq; v.y = a.y / n0sq;
     const C t = to_c(v, T());
     d[p] = t;
+    sr += (double)t.x; si += (double)t.y;   // the mean of the delta the kernels use
     if (psi_out) {
       const double2 lg = make_double2(0.5 * log(a.x * a.x + a.y * a.y), atan2(a.y, a.x));
       psi_out[p] = to_c(lg, T());
     }
     nz |= (t.x != (T)0 || t.y != (T)0);
   }
+  const double tr = block_sum(sr, red);
+  const double ti = block_sum(si, red);
+  if (threadIdx.x == 0) { atomicAdd(&g.dsum[beam].x, tr); atomicAdd(&g.dsum[beam].y, ti); }
   if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&g.nonhomog[beam], 1);
 }
 

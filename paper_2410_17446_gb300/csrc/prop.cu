@@ -68,7 +68,7 @@ constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host read
 constexpr int ERR_SLOT = 3 * (MMAX + 2) - 1;   // int in the counts area: the asynchronous-copy error word
 
 struct Layout {
-  size_t V, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog,
+  size_t V, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog, dsum,
       rk, anorm, part, psi, Tmp2, poles, act0, act1, netout, stage, iters, cycles, resid, flags, ulist, end;
 };
 
@@ -91,7 +91,7 @@ struct Group {
 }  // namespace
 
 struct prop {
-  int nbeams, P, C, prec, m, max_restarts;
+  int nbeams, P, C, prec, m, max_restarts, precond;
   double tol, k0, n0, dz;
   std::vector<cplx> poles, res;
   cplx r0;
@@ -146,6 +146,7 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
   L.st = take(nsys * sizeof(SysState));
   L.bnorm2 = take(nb * sizeof(double));
   L.nonhomog = take(nb * sizeof(int));
+  L.dsum = take(nb * sizeof(double2));
   L.rk = take(P * 16);
   L.anorm = take(2 * P * sizeof(double));
   L.part = take(nsys * NPLANE * NSTRIPE * (MMAX + 1) * sizeof(double2));
@@ -180,6 +181,7 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   g.ax = (const T*)(b + L.ax); g.ay = (const T*)(b + L.ay); g.pim = (const T*)(b + L.pim);
   g.twx = (const C*)(b + L.twx); g.twy = (const C*)(b + L.twy);
   g.st = (SysState*)(b + L.st); g.bnorm2 = (double*)(b + L.bnorm2); g.nonhomog = (int*)(b + L.nonhomog);
+  g.dsum = (double2*)(b + L.dsum);
   g.rk = (const double2*)(b + L.rk);
   g.anorm = (const double*)(b + L.anorm);
   g.part = (double2*)(b + L.part);
@@ -749,14 +751,14 @@ template <typename T> int step_group(prop* h, Group& G) {
           CK(rows_fwd<T, C>(ga, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, act0, st)); }
         if (Cn == 2) {
           { Prof p_(h, K_COLS, 0);
-            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, act0, st,
+            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act0, st,
                        Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
           { Prof p_(h, K_ROWS_INV, 0);
             CK(rows_inv_vec<T>(ga, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, act0,
                                st)); }
         } else {
           { Prof p_(h, K_COLS, 0);
-            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_POLE_INV, 1, 0, -1, scale, act0, st, none,
+            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act0, st, none,
                      none, tmaps)); }
           { Prof p_(h, K_ROWS_INV, 0);
             CK(rows_inv<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), act0, st)); }
@@ -812,7 +814,7 @@ template <typename T> int step_group(prop* h, Group& G) {
     { Prof p_(h, K_ROWS_FWD, 2 * cs * endp);
       CK(rows_fwd<T, C>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
     { Prof p_(h, K_COLS, 2 * cs * endp);
-      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_INV, 1, 0, -1, scale, nsys, st, none, none,
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_PREC_INV, 1, 0, -1, scale, nsys, st, none, none,
                  tmaps)); }
     { Prof p_(h, K_ROWS_INV, (cs + 32) * endp);
       CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_ADD_E), nsys, st)); }
@@ -896,6 +898,7 @@ int validate_opts(const prop_opts* o) {
   if (o->max_restarts < 1) return PROP_E_ARG;
   if (!(o->tol > 0.0)) return PROP_E_ARG;
   if (o->guess != PROP_GUESS_ZERO && o->guess != PROP_GUESS_LEARNED) return PROP_E_ARG;
+  if (o->precond != PROP_PRECOND_FREESPACE && o->precond != PROP_PRECOND_MEAN) return PROP_E_ARG;
   return PROP_OK;
 }
 
@@ -954,6 +957,7 @@ int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision) {
   o->max_restarts = precision == PROP_FP64 ? 50 : 200;
   o->tol = precision == PROP_FP64 ? 1e-12 : 1e-7;
   o->guess = PROP_GUESS_ZERO;
+  o->precond = PROP_PRECOND_MEAN;
   return PROP_OK;
 }
 
@@ -983,7 +987,7 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   prop* h = new (std::nothrow) prop();
   if (!h) return PROP_E_ARG;
   h->nbeams = nbeams; h->P = npoles; h->C = opts->ncomp; h->prec = opts->precision; h->m = opts->restart;
-  h->max_restarts = opts->max_restarts; h->tol = opts->tol; h->k0 = k0; h->n0 = n0; h->dz = dz;
+  h->max_restarts = opts->max_restarts; h->tol = opts->tol; h->precond = opts->precond; h->k0 = k0; h->n0 = n0; h->dz = dz;
   h->poles.resize(npoles); h->res.resize(npoles);
   for (int k = 0; k < npoles; ++k) {
     h->poles[k] = cplx(poles[2 * k], poles[2 * k + 1]);
@@ -1027,6 +1031,8 @@ int prop_set_medium(prop* h, int32_t beam, const void* n2) {
   CK(cudaMemcpyAsync(stage, n2, G.npts * 16, cudaMemcpyDefault, h->stream));
   int* nh = (int*)(h->ws + G.off.nonhomog) + slot;
   CK(cudaMemsetAsync(nh, 0, sizeof(int), h->stream));
+  double2* ds = (double2*)(h->ws + G.off.dsum) + slot;
+  CK(cudaMemsetAsync(ds, 0, sizeof(double2), h->stream));
   const int blocks = (int)std::min<long>(1024, (G.npts + 255) / 256);
   const double n0sq = h->n0 * h->n0;
   {
@@ -1042,6 +1048,7 @@ int prop_set_medium(prop* h, int32_t beam, const void* n2) {
     }
   }
   CK(cudaGetLastError());
+  if (h->precond == PROP_PRECOND_FREESPACE) CK(cudaMemsetAsync(ds, 0, sizeof(double2), h->stream));   // dbar = 0
   if (h->C == 2) {
     const int rc = h->prec == PROP_FP64 ? psi_derivatives<double>(h, G, slot) : psi_derivatives<float>(h, G, slot);
     if (rc) return rc;
