@@ -1,16 +1,25 @@
-"""Benchmark of the GB300 propagator: Mpoint*steps/s on one workload.
+"""Benchmark of the GB300 propagator: Mpoint*steps/s, learned vs plain.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--extra NAMES]
+                [--guess plain|both] [--impl ours|reference]
 
-A step is one z-step of the exponential propagator (Eq. approx_prop) for
-every beam of the workload: medium refresh (when the workload's n^2 changes),
-the free-space part, the shifted GMRES solves and the residue sum.  Each rank
-runs its own replica of the workload (the path has no exchange step), so
-``value`` is the total over ranks (weak scaling).  Time is taken with CUDA
-events on the library's stream around each step; an L2 flush (a 256 MiB
-write) runs between steps outside the timed intervals.  ``--impl reference``
-times the CPU oracle (complex128 NumPy) on a bounded sample of the same
-workload instead.
+A step is one z-step of the exponential propagator (Eq. approx_prop) for every
+beam of the workload: medium refresh (when the workload's n^2 changes), the
+free-space part, the shifted GMRES solves and the residue sum.  The default
+workload is the 1024^2 batched scalar one (16 poles, z-varying sine-product
+n^2, absorbing border); the 512^2 vector workload (14 poles, random n^2,
+cross-polarisation) is measured beside it, each with x0 = 0 (plain) and with
+the learned initial guess.  Each rank runs its own replica (the path has no
+exchange step), so ``value`` is the total over ranks (weak scaling).  Time is
+taken with CUDA events on the library's stream around each step; an L2 flush
+(a 256 MiB write) runs between steps outside the timed intervals.
+
+The CPU baseline (rank 0, one GPU only) times the complex128 oracle on all host
+cores on a bounded sample of each workload: the same recipe (spacing, border
+fraction, medium, beam, pole table) on a reduced grid, one z-step.  The GPU
+then runs the same sample from the same inputs, and the relative L2 difference
+of the two fields is reported with each leg.  ``--impl reference`` times the
+oracle alone on such samples.
 """
 from __future__ import annotations
 
@@ -21,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -31,17 +41,23 @@ import numpy as np  # noqa: E402
 
 METRIC = "Mpoint·steps/s at 1024² scalar & 512² vector, learned vs plain, at 1e-5 L2 err"
 UNIT = "Mpoint·steps/s"
-DEFAULT_WORKLOAD = "homogeneous_aperture_1024"
+DEFAULT_WORKLOAD = "batched_scalar_1024"
+DEFAULT_EXTRA = "vector_random_512"
 CONFIG_STEPS = {"homogeneous_aperture_1024": 100, "batched_scalar_1024": 200, "plain_scalar_64": 16,
                 "vector_random_512": 150, "uneven_batch": 64}
+DEFAULT_STEPS = {"homogeneous_aperture_1024": 20000, "plain_scalar_64": 2000, "uneven_batch": 6}
 GATE_CYCLES = 400_000      # ~0.2 ms of GPU sleep before each timed step (outside the interval)
 TABLE_OF = {"homogeneous_aperture_1024": "homogeneous_aperture_1024", "batched_scalar_1024": "batched_scalar_1024",
             "plain_scalar_64": "plain_scalar_64", "vector_random_512": "vector_random_512",
             "uneven_batch": "uneven_batch"}
+# grid of the CPU sample of each workload (same recipe, reduced grid; None: the workload itself)
+SAMPLE_N = {"batched_scalar_1024": 256, "vector_random_512": 128, "homogeneous_aperture_1024": 256,
+            "plain_scalar_64": None, "uneven_batch": 128}
+FP32_BAR = 1e-5
 
 
 def make_workload(name: str, nsteps: int, n: int = 0):
-    """The named workload; n > 0 shrinks a single-grid workload to n x n (profiling only)."""
+    """The named workload; n > 0 shrinks a single-grid workload to n x n (same spacing, border fraction)."""
     from paper_2410_17446_gb300 import workloads as wl
     if name == "homogeneous_aperture_1024":
         return wl.homogeneous_aperture_1024(nsteps, **({"n": n} if n else {}))
@@ -50,9 +66,9 @@ def make_workload(name: str, nsteps: int, n: int = 0):
     if name == "plain_scalar_64":
         return wl.plain_scalar_64(nsteps)
     if name == "vector_random_512":
-        return wl.vector_random_512(nsteps)
+        return wl.vector_random_512(nsteps, **({"n": n} if n else {}))
     if name == "uneven_batch":
-        return wl.uneven_batch(nsteps=nsteps)
+        return wl.uneven_batch(nsteps=nsteps) if not n else wl.uneven_batch(nbeams=4, nsteps=nsteps, sizes=(n,))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -121,54 +137,73 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# reference arm / CPU baseline: the oracle on the host cores
+# CPU baseline / reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 ORACLE_SNIPPET = r"""
 import json, sys, time, os
 sys.path.insert(0, {root!r})
 import numpy as np
 from oracle import aaa_lawson as al, propagator as pr, operators as ops
-from paper_2410_17446_gb300 import workloads as wl
+ops.FFT_WORKERS = {workers}
 import bench
-W = bench.make_workload({name!r}, 64)
+W = bench.make_workload({name!r}, {nsteps}, {n})
 T = al.PoleTable.from_json(bench.load_table({name!r}))
-budget = {budget}
-t0 = time.perf_counter(); steps = 0; pts = 0
-beams = W.beams
-w = [b.w0.copy() for b in beams]
-med = [None] * len(beams)
-its = []
-while True:
-    for i, b in enumerate(beams):
-        if med[i] is None or b.medium_changes(steps):
-            med[i] = ops.Medium(b.medium(steps), b.grid.dx, b.grid.dy, W.k0, W.n0, W.ncomp)
-        w[i], st = pr.step(med[i], w[i], T, tol=1e-12)
+fields = []
+t0 = time.perf_counter(); pts = 0; its = []
+for i, b in enumerate(W.beams):
+    med = ops.Medium(b.medium(0), b.grid.dx, b.grid.dy, W.k0, W.n0, W.ncomp)
+    w = b.w0.copy()
+    for s in range({nsteps}):
+        if s > 0 and b.medium_changes(s):
+            med = ops.Medium(b.medium(s), b.grid.dx, b.grid.dy, W.k0, W.n0, W.ncomp)
+        w, st = pr.step(med, w, T, tol=1e-12)
         its += st.iterations
         pts += b.grid.nx * b.grid.ny
-        if time.perf_counter() - t0 > budget and i + 1 < len(beams):
-            break
-    steps += 1
-    el = time.perf_counter() - t0
-    if el > budget or steps >= {max_steps}:
-        break
-print(json.dumps({{"seconds": el, "steps": steps, "point_steps": pts, "mean_iters": float(np.mean(its))}}))
+    fields.append(w)
+el = time.perf_counter() - t0
+if {out!r}:
+    np.savez({out!r}, *fields)
+print(json.dumps({{"seconds": el, "point_steps": pts, "mean_iters": float(np.mean(its))}}))
 """
 
 
-def run_oracle_sample(name: str, budget_s: float, max_steps: int) -> dict:
+def cpu_info() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "CPU part", "Hardware"):
+            for ln in txt.splitlines():
+                if ln.lower().startswith(key.lower()):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_oracle_sample(name: str, nsteps: int = 1, out: str = "") -> dict:
+    """The oracle (complex128) on the CPU sample of `name`: its recipe on the SAMPLE_N grid,
+    `nsteps` z-steps from the initial field, all host cores (scipy.fft workers and BLAS threads)."""
+    cores = os.cpu_count() or 1
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, name=name, budget=budget_s, max_steps=max_steps)
+        env[v] = str(cores)
+    n = SAMPLE_N.get(name) or 0
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, nsteps=nsteps, n=n, workers=cores, out=out)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT,
-                       timeout=max(600, 20 * budget_s))
+                       timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
     d["value"] = d["point_steps"] / d["seconds"] / 1e6
-    d["cores"] = 1
-    d["sample"] = (f"{d['steps']} step(s) of {name} by the complex128 oracle (GMRES tol 1e-12, "
-                   f"numpy.fft single-threaded, BLAS threads = 1), {d['seconds']:.1f} s")
+    d["cores"] = cores
+    W = make_workload(name, 1, n)
+    grid = f"{W.beams[0].grid.nx}x{W.beams[0].grid.ny}"
+    d["grid"] = grid
+    d["sample"] = (f"{nsteps} z-step(s) of {name}'s recipe on a {grid} grid ({len(W.beams)} beam(s), "
+                   f"{W.npoles} poles sequential, GMRES tol 1e-12, mean {d['mean_iters']:.1f} Arnoldi steps per "
+                   f"pole) by the complex128 oracle, scipy.fft workers = BLAS threads = {cores} on "
+                   f"{cpu_info()}, {d['seconds']:.1f} s")
     return d
 
 
@@ -195,26 +230,194 @@ def dist_setup():
 
 
 def reference_arm(args) -> None:
+    """The oracle, as it stands, on the host cores: K samples (one z-step of the
+    workload's recipe on its reduced grid each), rank 0 only."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return
-    budget = 20.0
-    d = run_oracle_sample(args.workload, budget, 10 ** 6)
+    steps = max(1, int(getattr(args, "steps", 1) or 1))
+    secs, pts, its, d = 0.0, 0, [], None
+    for _ in range(steps):
+        d = run_oracle_sample(args.workload, 1)
+        secs += d["seconds"]
+        pts += d["point_steps"]
+        its.append(d["mean_iters"])
+    value = pts / secs / 1e6
     W = make_workload(args.workload, 1)
-    line = {"impl": "reference", "metric": METRIC, "value": d["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": d["steps"], "warmup": 0, "ms_per_step": 1e3 * d["seconds"] / max(1, d["steps"]),
+    sample = f"{steps} x [{d['sample']}]"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * secs / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "points_per_step": W.points,
-                                            "poles": W.npoles},
-            "cpu_baseline": {"value": d["value"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
-                             "sample": d["sample"]},
-            "e2e": {"value": d["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                                            "poles": W.npoles, "sample_grid": d["grid"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f).get("hbm_gbs")
+    except OSError:
+        pk = None
+    return (pk, "measured") if pk else (6800.0, "fallback")
+
+
+def roofline_of(name: str, prof: dict, ms_total: float) -> dict:
+    """HBM roofline of the kernel kind with the largest device time in the timed region:
+    summed algorithmic bytes / summed CUDA-event durations of its launches."""
+    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    peak, src = _peak()
+    achieved = dom[1]["alg_bytes"] / (dom[1]["total_ms"] / 1e3) / 1e9 if dom[1]["total_ms"] > 0 else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get(dom[0])
+    return {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+            "alg_bytes_per_launch": dom[1]["alg_bytes"] / max(1, dom[1]["launches"]),
+            "launches": dom[1]["launches"], "share_of_step": dom[1]["total_ms"] / ms_total if ms_total else None}
+
+
+class Runner:
+    """One workload on this rank's GPU: media resident on the device, timed legs."""
+
+    def __init__(self, args, name, P, torch, dev, stream, ws, local):
+        self.args, self.name, self.P, self.torch, self.dev, self.stream = args, name, P, torch, dev, stream
+        self.ws, self.local = ws, local
+        total = args.warmup + args.steps
+        self.W = make_workload(name, max(total, 1), args.n)
+        self.tab = load_table(name)
+        self.grids = [(b.grid.nx, b.grid.ny, b.grid.dx, b.grid.dy) for b in self.W.beams]
+        self.media = {}
+        for s in range(total):
+            for i, b in enumerate(self.W.beams):
+                if s == 0 or b.medium_changes(s):
+                    self.media[(s, i)] = torch.tensor(b.medium(s), dtype=torch.complex128, device=dev)
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        self.net = None
+
+    def propagator(self, guess: str, W=None):
+        P = self.P
+        W = W or self.W
+        grids = [(b.grid.nx, b.grid.ny, b.grid.dx, b.grid.dy) for b in W.beams]
+        with self.torch.cuda.stream(self.stream):
+            pr = P.Propagator.from_table(grids, W.k0, W.n0, W.dz, self.tab, ncomp=W.ncomp, precision=P.PROP_FP32,
+                                         restart=W.restart, stream=self.stream,
+                                         guess=P.PROP_GUESS_LEARNED if guess == "learned" else P.PROP_GUESS_ZERO)
+            if guess == "learned":
+                net = self.load_net()
+                pr.set_guess_net(net["channels"], net["weights"], net["biases"])
+            for i, b in enumerate(W.beams):
+                pr.set_field(i, np.ascontiguousarray(b.w0))
+        return pr
+
+    def load_net(self):
+        if self.net is None:
+            from paper_2410_17446_gb300 import guess_train as GT
+            fam = "vector" if self.W.ncomp == 2 else "scalar"
+            self.net = GT.load(os.path.join(ROOT, "paper_2410_17446_gb300", "nets", f"guess_{fam}.npz"))
+        return self.net
+
+    def timed(self, prx, clocks_on: bool) -> dict:
+        """W warm-up steps, then K steps each timed by events on the library stream."""
+        torch, args, stream, dev = self.torch, self.args, self.stream, self.dev
+
+        def step_of(s):
+            for i in range(len(self.W.beams)):
+                m = self.media.get((s, i))
+                if m is not None:
+                    prx.set_medium(i, m)
+            prx.step()
+        with torch.cuda.stream(stream):
+            for s in range(args.warmup):
+                step_of(s)
+            torch.cuda.synchronize(dev)
+            l0 = prx.stats().kernel_launches
+            it0 = prx.stats().total_iters
+            prx.set_profiling(True)
+            st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            clocks = ClockSampler(self.local) if clocks_on else None
+            if self.ws > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize(dev)
+            if clocks:
+                clocks.start()
+                time.sleep(0.3)
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                self.flush.zero_()
+                # keep the GPU busy while the host enqueues the step, so that the
+                # timed interval holds device work, not host launch latency
+                torch.cuda._sleep(GATE_CYCLES)
+                st_ev[k].record(stream)
+                step_of(args.warmup + k)
+                en_ev[k].record(stream)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            clk = None
+            if clocks:
+                time.sleep(0.3)
+                clk = clocks.stop(t0, t1)
+            if self.ws > 1:
+                torch.distributed.barrier()
+            dms = sum(a.elapsed_time(b) for a, b in zip(st_ev, en_ev))
+            prof = prx.profile()
+            prx.set_profiling(False)
+            stx = prx.stats()
+        ms = max_over_ranks(dms, self.ws, dev)
+        return {"dev_ms": ms, "wall": t1 - t0, "clk": clk, "prof": prof, "launches": stx.kernel_launches - l0,
+                "arnoldi": int(stx.total_iters - it0), "iters": prx.iterations()}
+
+    def leg(self, guess: str, clocks_on: bool = False) -> dict:
+        pr = self.propagator(guess)
+        r = self.timed(pr, clocks_on)
+        ms = r["dev_ms"]
+        prof = r["prof"]
+        d = {"value": whole_job_value(self.ws, self.W.points, self.args.steps, ms / 1e3),
+             "ms_per_step": ms / self.args.steps,
+             "roofline": roofline_of(self.name, prof, ms),
+             "arnoldi_steps_total": r["arnoldi"],
+             "arnoldi_steps_per_solve": r["arnoldi"] / (self.args.steps * len(self.W.beams) * self.W.npoles),
+             "gmres_last_step": {"sum": int(r["iters"].sum()), "max": int(r["iters"].max())},
+             "gpu_launches": r["launches"],
+             "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
+                             "GBps": (v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9) if v["total_ms"] > 0 else None}
+                         for k, v in prof.items() if v["launches"]}}
+        if guess == "learned":
+            d["guess_net_ms"] = round(prof["guess_net"]["total_ms"], 3)
+            d["net"] = {k: v for k, v in self.load_net()["meta"].items()
+                        if k in ("family", "n", "train_media_seeds", "solves", "adam_iterations")}
+        self._last = (pr, r)
+        return d
+
+    def sample_error(self, guess: str, oracle_npz: str, nsteps: int = 1) -> dict:
+        """GPU run of the CPU sample (reduced grid, same inputs) against the oracle's fields."""
+        n = SAMPLE_N.get(self.name) or 0
+        W = make_workload(self.name, nsteps, n)
+        pr = self.propagator(guess, W)
+        with self.torch.cuda.stream(self.stream):
+            for s in range(nsteps):
+                for i, b in enumerate(W.beams):
+                    if s == 0 or b.medium_changes(s):
+                        pr.set_medium(i, np.ascontiguousarray(b.medium(s)))
+                pr.step()
+            got = [pr.get_field(i) for i in range(len(W.beams))]
+        pr.close()
+        z = np.load(oracle_npz)
+        ref = [z[f"arr_{i}"] for i in range(len(W.beams))]
+        errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(got, ref)]
+        return {"value": max(errs), "bar": FP32_BAR, "grid": f"{W.beams[0].grid.nx}x{W.beams[0].grid.ny}",
+                "steps": nsteps, "against": "complex128 oracle (the cpu_baseline sample: same recipe, reduced grid)"}
+
+
 def ours(args) -> None:
     import torch
     ws, rank, local = dist_setup()
@@ -230,101 +433,35 @@ def ours(args) -> None:
         torch.distributed.barrier()
     from paper_2410_17446_gb300 import prop as P
 
-    cpu = None
+    names = [args.workload] + [x for x in args.extra.split(",") if x and x != "none" and x != args.workload]
+    guesses = ["plain", "learned"] if args.guess == "both" else ["plain"]
+
+    # CPU samples first (all host cores; nothing on the GPU runs meanwhile)
+    tmpdir = tempfile.mkdtemp(prefix="bench_oracle_")
+    cpu = {}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = run_oracle_sample(args.workload, args.cpu_seconds, 10 ** 6)
+        for nm in names:
+            cpu[nm] = run_oracle_sample(nm, 1, os.path.join(tmpdir, nm + ".npz"))
 
-    total = args.warmup + args.steps
-    W = make_workload(args.workload, max(total, 1), args.n)
-    tab = load_table(args.workload)
-    grids = [(b.grid.nx, b.grid.ny, b.grid.dx, b.grid.dy) for b in W.beams]
     stream = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream):
-        pr = P.Propagator.from_table(grids, W.k0, W.n0, W.dz, tab, ncomp=W.ncomp, precision=P.PROP_FP32,
-                                     restart=W.restart, stream=stream)
-    for i, b in enumerate(W.beams):
-        pr.set_field(i, np.ascontiguousarray(b.w0))
-    # media for every step, resident on the device before timing
-    media = {}
-    for s in range(total):
-        for i, b in enumerate(W.beams):
-            if s == 0 or b.medium_changes(s):
-                media[(s, i)] = torch.tensor(b.medium(s), dtype=torch.complex128, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    def timed(prx, clocks_on=True):
-        """W warm-up steps, then K steps each timed by events on the library stream."""
-        def step_of(s):
-            for i in range(len(W.beams)):
-                m = media.get((s, i))
-                if m is not None:
-                    prx.set_medium(i, m)
-            prx.step()
-        with torch.cuda.stream(stream):
-            for s in range(args.warmup):
-                step_of(s)
-            torch.cuda.synchronize(dev)
-            l0 = prx.stats().kernel_launches
-            prx.set_profiling(True)
-            st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            clocks = ClockSampler(local) if clocks_on else None
-            if ws > 1:
-                torch.distributed.barrier()
-            torch.cuda.synchronize(dev)
-            if clocks:
-                clocks.start()
-                time.sleep(0.3)
-            t0 = time.perf_counter()
-            its_total = 0
-            for k in range(args.steps):
-                flush.zero_()
-                # keep the GPU busy while the host enqueues the step, so that the
-                # timed interval holds device work, not host launch latency
-                torch.cuda._sleep(GATE_CYCLES)
-                st_ev[k].record(stream)
-                step_of(args.warmup + k)
-                en_ev[k].record(stream)
-            torch.cuda.synchronize(dev)
-            t1 = time.perf_counter()
-            clk = None
-            if clocks:
-                time.sleep(0.3)
-                clk = clocks.stop(t0, t1)
-            if ws > 1:
-                torch.distributed.barrier()
-            dms = sum(a.elapsed_time(b) for a, b in zip(st_ev, en_ev))
-            prof = prx.profile()
-            prx.set_profiling(False)
-            stx = prx.stats()
-            return {"dev_ms": dms, "wall": t1 - t0, "clk": clk, "prof": prof,
-                    "launches": stx.kernel_launches - l0, "st": stx, "iters": prx.iterations()}
-
-    res = timed(pr)
-    dev_ms, wall, clk, prof = res["dev_ms"], res["wall"], res["clk"], res["prof"]
-    launches, st, iters = res["launches"], res["st"], res["iters"]
-
-    learned = None
-    if args.guess == "both":
-        from paper_2410_17446_gb300 import guess_train as GT
-        fam = "vector" if W.ncomp == 2 else "scalar"
-        net = GT.load(os.path.join(ROOT, "paper_2410_17446_gb300", "nets", f"guess_{fam}.npz"))
-        with torch.cuda.stream(stream):
-            prl = P.Propagator.from_table(grids, W.k0, W.n0, W.dz, tab, ncomp=W.ncomp, precision=P.PROP_FP32,
-                                          restart=W.restart, stream=stream, guess=P.PROP_GUESS_LEARNED)
-            prl.set_guess_net(net["channels"], net["weights"], net["biases"])
-            for i, b in enumerate(W.beams):
-                prl.set_field(i, np.ascontiguousarray(b.w0))
-        rl = timed(prl, clocks_on=False)
-        ml = max_over_ranks(rl["dev_ms"], ws, dev)
-        learned = {"value": whole_job_value(ws, W.points, args.steps, ml / 1e3), "ms_per_step": ml / args.steps,
-                   "arnoldi_steps_total": int(rl["st"].total_iters), "net": net["meta"],
-                   "guess_net_ms": round(rl["prof"]["guess_net"]["total_ms"], 3)}
-        prl.close()
-
-    ms = max_over_ranks(dev_ms, ws, dev)
-    pts = W.points
-    value = whole_job_value(ws, pts, args.steps, ms / 1e3)
+    legs = {}
+    main = None
+    for nm in names:
+        R = Runner(args, nm, P, torch, dev, stream, ws, local)
+        legs[nm] = {}
+        for gi, guess in enumerate(guesses):
+            d = R.leg(guess, clocks_on=(nm == args.workload and guess == "plain"))
+            if nm in cpu:
+                d["rel_l2_vs_oracle"] = R.sample_error(guess, os.path.join(tmpdir, nm + ".npz"))
+            if nm == args.workload and guess == "plain":
+                main = (R, d, R._last)
+            else:
+                R._last[0].close()
+            legs[nm][guess] = d
+        if nm != args.workload:
+            del R
+    R, d0, (pr, r0) = main
+    W = R.W
 
     # accuracy over the configuration's own run length, where a closed form exists
     acc = None
@@ -338,17 +475,18 @@ def ours(args) -> None:
             w = pr.get_field(0)[0]
         z = -(np.fft.fftfreq(b.grid.nx, b.grid.dx)[None, :] ** 2 + np.fft.fftfreq(b.grid.ny, b.grid.dy)[:, None] ** 2) \
             * (2 * math.pi) ** 2 / (W.k0 * W.n0) ** 2
-        poles = np.array([complex(*p) for p in tab["poles"]])
-        res = np.array([complex(*r) for r in tab["residues"]])
-        R = complex(*tab["r0"]) + sum(r / (z - p) for p, r in zip(poles, res))
-        ref = np.fft.ifft2(R ** total * np.fft.fft2(b.w0[0]))
+        poles = np.array([complex(*p) for p in R.tab["poles"]])
+        res = np.array([complex(*r) for r in R.tab["residues"]])
+        Rz = complex(*R.tab["r0"]) + sum(r / (z - p) for p, r in zip(poles, res))
+        ref = np.fft.ifft2(Rz ** total * np.fft.fft2(b.w0[0]))
         acc = float(np.linalg.norm(w - ref) / np.linalg.norm(ref))
 
-    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    # end to end through the public API with host buffers (pinned): each step's medium
+    # copied in and the field read back inside the timed region
     e2e = None
     if not args.no_e2e:
         host_out = [torch.empty(pr.shape(i), dtype=torch.complex128).pin_memory() for i in range(len(W.beams))]
-        host_media = {key: m.cpu().pin_memory() for key, m in media.items() if key[0] >= args.warmup}
+        host_media = {key: m.cpu().pin_memory() for key, m in R.media.items() if key[0] >= args.warmup}
         h2d = d2h = 0
         with torch.cuda.stream(stream):
             for i, b in enumerate(W.beams):
@@ -371,56 +509,32 @@ def ours(args) -> None:
             torch.cuda.synchronize(dev)
             e2e_s = time.perf_counter() - t0
         e2e_s = max_over_ranks(e2e_s, ws, dev)
-        e2e = {"value": whole_job_value(ws, pts, args.steps, e2e_s), "unit": UNIT,
+        e2e = {"value": whole_job_value(ws, W.points, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
 
-    # roofline of the dominant kernel (largest device time in the timed region)
-    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
-    achieved = dom[1]["alg_bytes"] / (dom[1]["total_ms"] / 1e3) / 1e9 if dom[1]["total_ms"] > 0 else 0.0
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        traffic = tj.get(dom[0])
-    roof = {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-            "alg_bytes_per_launch": dom[1]["alg_bytes"] / max(1, dom[1]["launches"]),
-            "launches": dom[1]["launches"], "share_of_step": dom[1]["total_ms"] / ms if ms else None}
-
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": args.workload, "points_per_step": pts, "beams": len(W.beams),
+        line = {"metric": METRIC, "value": d0["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": d0["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "points_per_step": W.points, "beams": len(W.beams),
                            "grid": f"{W.beams[0].grid.nx}x{W.beams[0].grid.ny}", "poles": W.npoles,
                            "ncomp": W.ncomp, "restart": W.restart, "tol": pr.opts.tol,
+                           "precond": "mean n^2" if pr.opts.precond == P.PROP_PRECOND_MEAN else "free space",
                            "l2": "flushed (256 MiB write) between timed steps",
                            "parallelism": f"replicas x{ws}"},
-                "roofline": roof, "gpu_launches": launches, "clocks": clk,
-                "wall_s": wall,
-                "gmres": {"iters_sum_last_step": int(iters.sum()), "iters_max_last_step": int(iters.max()),
-                          "total_iters": int(st.total_iters)},
-                "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
-                                "GBps": (v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9) if v["total_ms"] > 0 else None}
-                            for k, v in prof.items() if v["launches"]},
+                "roofline": d0["roofline"], "gpu_launches": d0["gpu_launches"], "clocks": r0["clk"],
+                "wall_s": r0["wall"],
+                "arnoldi_steps_total": d0["arnoldi_steps_total"],
+                "rel_l2_vs_oracle": d0.get("rel_l2_vs_oracle"),
                 "rel_err_vs_closed_form": acc,
-                "learned_guess": learned,
-                "plain_arnoldi_steps_total": int(st.total_iters),
-                "rel_err_steps": CONFIG_STEPS[args.workload] if acc is not None else None, "e2e": e2e}
-        if cpu is not None:
-            line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
-                                    "sample": cpu["sample"]}
+                "rel_err_steps": CONFIG_STEPS[args.workload] if acc is not None else None,
+                "legs": legs, "e2e": e2e}
+        if args.workload in cpu:
+            c = cpu[args.workload]
+            line["cpu_baseline"] = {"value": c["value"], "unit": UNIT, "cores": c["cores"], "kind": "oracle",
+                                    "sample": c["sample"]}
+            line["cpu_baseline_extra"] = {nm: {"value": c2["value"], "sample": c2["sample"]}
+                                          for nm, c2 in cpu.items() if nm != args.workload}
         print(json.dumps(line), flush=True)
     pr.close()
     if ws > 1:
@@ -431,19 +545,20 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: enough for a timed region of a few seconds)")
+                    help="timed steps (default: 20, enough for a timed region of a few seconds)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(TABLE_OF))
+    ap.add_argument("--extra", default=DEFAULT_EXTRA,
+                    help="comma-separated workloads measured beside the main one ('none' for none)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=0, help="shrink the grid (profiling runs only; not a bench line)")
-    ap.add_argument("--guess", default="plain", choices=["plain", "both"],
+    ap.add_argument("--guess", default="both", choices=["plain", "both"],
                     help="both: also time the learned initial guess (GMRES to the same tolerance)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"homogeneous_aperture_1024": 20000, "plain_scalar_64": 2000}.get(args.workload, 100)
+        args.steps = DEFAULT_STEPS.get(args.workload, 20)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

@@ -219,17 +219,20 @@ int prop_get_net_io(prop* h, int32_t beam, int32_t pole, void* d_in_bf16, float*
  * application owns every device allocation, or a program that must run inside
  * a fixed device-memory budget decided in advance.  They pass only the data;
  * the twiddle tables that prop_fft2 keeps in d_work live here in a file-scope
- * __device__ array of PROP_FFT2_NOALLOC_SCRATCH_BYTES (64 KiB), which every GPU
+ * __device__ array of PROP_FFT2_NOALLOC_SCRATCH_BYTES (32 KiB), which every GPU
  * that loads this library holds until the process exits.  A call needs
- * (nx + ny) complex twiddles of the chosen precision; requests that do not fit
- * return PROP_E_SCRATCH.  Nothing is allocated: no cudaMalloc, cudaFree or
- * allocating library routine is called.  The first call on each device looks
- * up the array's device address with that device current
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and each call rewrites the part it uses, so calls
- * that overlap on the GPU (different streams, or devices sharing nothing but
- * this process) race on the same memory: serialise them. */
-#define PROP_FFT2_NOALLOC_SCRATCH_BYTES 65536
+ * (nx + ny) complex twiddles of the chosen precision; every supported size fits
+ * (1024 + 1024 complex128 twiddles fill the array exactly), so PROP_E_SCRATCH
+ * only guards a build with larger sizes.  Nothing is allocated: no cudaMalloc,
+ * cudaFree or allocating library routine is called.  The first call on each
+ * device looks up the array's device address with that device current
+ * (cudaGetSymbolAddress, once per device even when host threads call at the
+ * same time); make that first call before any stream capture.  Each device has
+ * its own copy of the array; calls on one device share it, and each call
+ * rewrites the part it uses, so calls that overlap on the same device
+ * (different streams, or host threads without ordering) race on that memory:
+ * serialise them.  Calls on different devices do not interfere. */
+#define PROP_FFT2_NOALLOC_SCRATCH_BYTES 32768
 int prop_fft2_noalloc(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse,
                       void* d_data, void* stream);
 

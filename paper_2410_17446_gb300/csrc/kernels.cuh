@@ -372,6 +372,9 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   if (skip_homog && !g.nonhomog[u / g.P]) return;
+  // once any CTA's copy has failed the step is void: issue no further copies, so
+  // the CTAs still to come return at once instead of each waiting out its bound
+  if (*reinterpret_cast<volatile const int*>(g.err) != 0) return;
   const int x0 = blockIdx.x * NV;
   // self-check of the TMA alignment rules: 128-byte shared destinations, 64-byte
   // tensor maps, 16-byte x offsets; on a violation record it and do nothing

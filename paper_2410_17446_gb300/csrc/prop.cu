@@ -20,6 +20,7 @@
 #include <complex>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1416,18 +1417,25 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_fft2_noalloc_scratch[PROP_FFT2_NOALLOC_SCRATCH_BYTES];
 
+// Every supported request fits: the largest, 1024 + 1024 complex128 twiddles
+// with the second table 256-byte aligned, needs exactly the array's 32 KiB.
+static_assert(PROP_FFT2_NOALLOC_SCRATCH_BYTES >= 2 * 1024 * 16, "scratch must hold the largest twiddle tables");
+
 constexpr int NOALLOC_MAX_DEVICES = 64;
 void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up once per
+// device (std::call_once: host threads calling at the same time see one lookup).
 int noalloc_scratch(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PROP_E_CUDA;
-  if (!g_noalloc_ptr[dev]) {
+  std::call_once(g_noalloc_once[dev], [dev] {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_fft2_noalloc_scratch) != cudaSuccess || !p) return PROP_E_CUDA;
-    g_noalloc_ptr[dev] = p;
-  }
+    if (cudaGetSymbolAddress(&p, g_fft2_noalloc_scratch) == cudaSuccess && p) g_noalloc_ptr[dev] = p;
+    else cudaGetLastError();
+  });
+  if (!g_noalloc_ptr[dev]) return PROP_E_CUDA;
   *out = g_noalloc_ptr[dev];
   return PROP_OK;
 }

@@ -203,3 +203,54 @@ def test_hard_scattering_beam_fp32_six_steps(P):
     got = gpu_run(pr, W, 6)[0]
     ref = oracle_run(W, oracle_table("uneven_batch"), 6)
     assert rel_l2(got, ref) < FP32_TOL
+
+
+def test_uneven_384_and_768_beams_solutions(P):
+    """The radix-3 grids of the uneven batch (384 = 3 8 16, 768 = 3 16 16) in one
+    handle with a repeated 384 beam: after one FP32 step every beam's pole
+    solutions x_k = (Z_fs - p_k)^-1 w + e_k satisfy (Z - p_k) x_k = w under the
+    oracle's operator, and the GPU field is r0 w + sum r_k x_k (Eq. approx_prop)."""
+    from oracle import operators as ops
+    from paper_2410_17446_gb300 import workloads as wl
+    dz = 0.5
+    beams = []
+    for n, eps, period, waist in ((384, 0.05, 1.7, 4.0), (768, 0.08, 2.3, 6.0), (384, 0.03, 1.2, 3.0)):
+        g = wl.Grid(n, n, 0.25, 0.25)
+        width = max(8, n // 16)
+
+        def med(s, g=g, eps=eps, period=period, width=width):
+            return wl.sine_product_n2(g, eps, period, (s + 0.5) * dz, width, 0.2)
+
+        beams.append(wl.Beam(g, wl.gaussian_beam(g, waist)[None], med, lambda s: True, width, 0.2))
+    W = wl.Workload("uneven_384_768", wl.K0, 1.0, dz, 1, 12, 1, "fp32", 20, 1e-7, beams)
+    T = oracle_table("uneven_batch")
+    pr = gpu_propagator(W, "uneven_batch", P.PROP_FP32)
+    got = gpu_run(pr, W, 1)
+    for i, b in enumerate(W.beams):
+        med = ops.Medium(b.medium(0), b.grid.dx, b.grid.dy, W.k0, W.n0, 1)
+        out = T.r0 * b.w0
+        worst = 0.0
+        for k, (p, r) in enumerate(zip(T.poles, T.residues)):
+            x = med.freespace_solve(b.w0, p) + pr.get_correction(i, k)
+            worst = max(worst, np.linalg.norm(b.w0 - med.apply_shifted(x, p)) / np.linalg.norm(b.w0))
+            out = out + r * x
+        assert worst < 1e-4, (i, worst)
+        assert rel_l2(got[i], out) < 1e-6, i
+
+
+def test_mean_and_freespace_preconditioners_agree(P):
+    """The preconditioner changes only how GMRES gets there (Sec. 4.2): the
+    default constant-index preconditioner and the n = n0 free-space one give the
+    same FP64 field, and the oracle's, on the 64^2 workload with its border."""
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.plain_scalar_64(4)
+    fields, its = {}, {}
+    for pc in (P.PROP_PRECOND_MEAN, P.PROP_PRECOND_FREESPACE):
+        pr = gpu_propagator(W, "plain_scalar_64", P.PROP_FP64, tol=1e-12, precond=pc)
+        fields[pc] = gpu_run(pr, W, 4)[0]
+        its[pc] = int(pr.stats().total_iters)
+    ref = oracle_run(W, oracle_table("plain_scalar_64"), 4)
+    assert rel_l2(fields[P.PROP_PRECOND_MEAN], ref) < FP64_TOL
+    assert rel_l2(fields[P.PROP_PRECOND_FREESPACE], ref) < FP64_TOL
+    print("Arnoldi steps: mean", its[P.PROP_PRECOND_MEAN], "free space", its[P.PROP_PRECOND_FREESPACE])
+    assert its[P.PROP_PRECOND_MEAN] < its[P.PROP_PRECOND_FREESPACE]
