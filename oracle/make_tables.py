@@ -40,6 +40,44 @@ def table_for(workload, probe_steps=(0,)) -> al.PoleTable:
     return al.fit(workload.K, workload.npoles, lo, 2.0, im_shifts=shifts)
 
 
+def pf_max_err(T: al.PoleTable, lo: float, hi: float, shifts=()) -> float:
+    """Largest |r - g| of the partial-fraction form on a uniform sampling of the fit range."""
+    z = np.linspace(lo, hi, 4001).astype(np.complex128)
+    z = np.concatenate([z] + [z + 1j * s for s in shifts])
+    return float(np.max(np.abs(T(z) - al.target(z, T.K))))
+
+
+def pade_table(workload) -> dict:
+    """The shifted and rotated (10,10) Padé approximant (Sec. 3.1) for the workload's K."""
+    from . import pade
+    T = pade.rotated_pade_table(workload.K, 10)
+    d = T.to_json()
+    d["fit_max_err"] = pf_max_err(T, -1.0, 2.0)
+    d["kind"] = "pade_rotated"
+    d["alpha"] = float(np.pi / 8)
+    return d
+
+
+# The paper's lookup table for air (Sec. 3.1): one n0 = 1.00030, a set of k0 dz,
+# AAA-Lawson on its default range Re zeta in [-4, 2].
+LOOKUP_N0 = 1.0003
+LOOKUP_DZ = (0.25, 0.5, 1.0, 2.0, 5.0)
+LOOKUP_POLES = {5.0: 28}
+
+
+def lookup_table() -> dict:
+    entries = []
+    for dz in LOOKUP_DZ:
+        K = 2 * np.pi * LOOKUP_N0 * dz
+        T = al.fit(K, LOOKUP_POLES.get(dz, 25), -4.0, 2.0)
+        e = T.to_json()
+        e["k0dz"] = 2 * np.pi * dz
+        e["pf_max_err"] = pf_max_err(T, -4.0, 2.0)
+        entries.append(e)
+    return {"n0": LOOKUP_N0, "domain": [-4.0, 2.0], "entries": entries,
+            "source": "oracle.make_tables (AAA-Lawson oracle, uniform samples on [-4, 2])"}
+
+
 def main(argv=None) -> int:
     sys.path.insert(0, os.path.dirname(HERE))
     from paper_2410_17446_gb300 import workloads as wl
@@ -50,9 +88,19 @@ def main(argv=None) -> int:
         "batched_scalar_1024": lambda: wl.batched_scalar_1024(1, n=256),
         "vector_random_512": lambda: wl.vector_random_512(1, n=128),
         "uneven_batch": lambda: wl.uneven_batch(nbeams=48, nsteps=1, sizes=(128,)),
+        "multiwave_scalar_64": lambda: wl.multiwave_scalar_64(1),
     }
-    names = argv or list(makers)
+    extra = {"pade_scalar_64": lambda: pade_table(wl.plain_scalar_64(1)),
+             "lookup_n0_1.0003": lookup_table}
+    names = argv or (list(makers) + list(extra))
     for name in names:
+        if name in extra:
+            d = extra[name]()
+            d["workload"] = name
+            with open(os.path.join(TABLE_DIR, name + ".json"), "w") as f:
+                json.dump(d, f, indent=1)
+            print(f"{name}: written")
+            continue
         W = makers[name]()
         T = table_for(W)
         d = T.to_json()

@@ -231,6 +231,18 @@ def uneven_batch(nbeams: int = 48, nsteps: int = 64, seed: int = 11,
                     f"{nbeams} beams, sizes {sizes}, 12 poles")
 
 
+def multiwave_scalar_64(nsteps: int = 4) -> Workload:
+    """Multiple-wavelength steps (Sec. 3.1): dz = 5 lambda, 28 poles, on a 64^2
+    grid at dx = lambda/4 with an 8-cell border and a static sine product
+    (eps 0.05, period 2 lambda), Gaussian w = 2; FP64."""
+    g = Grid(64, 64, LAMBDA / 4, LAMBDA / 4)
+    n2 = sine_product_n2(g, 0.05, 2 * LAMBDA, None, 8, 0.2)
+    med, ch = _constant(n2)
+    beam = Beam(g, gaussian_beam(g, 2 * LAMBDA)[None], med, ch, 8, 0.2)
+    return Workload("multiwave_scalar_64", K0, 1.0, 5 * LAMBDA, nsteps, 28, 1, "fp64", 20, 1e-10,
+                    [beam], "64x64 scalar, dz = 5 lambda, 28 poles")
+
+
 def small_scalar(n: int = 16, dx: float = LAMBDA / 4, border: int = 3, eps: float = 0.1,
                  seed: int = 0, waist: float = 1.0) -> Workload:
     """Tiny random-medium scalar case (dense-LU sized) for unit tests."""
@@ -263,4 +275,5 @@ WORKLOADS = {
     "batched_scalar_1024": batched_scalar_1024,
     "vector_random_512": vector_random_512,
     "uneven_batch": uneven_batch,
+    "multiwave_scalar_64": multiwave_scalar_64,
 }

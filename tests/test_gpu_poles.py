@@ -1,0 +1,78 @@
+"""Alternative pole sets of Sec. 3.1 through the C ABI: each is only a
+different table given to prop_create, and the CUDA path must match the oracle
+run with the same table.
+
+* the shifted/rotated (10,10) Padé approximant, on the 64^2 workload (FP64);
+* the (28,28) AAA-Lawson table for multiple-wavelength steps, dz = 5 lambda,
+  on a 64^2 lambda/4 grid (FP64 and FP32);
+* an entry of the k0 dz lookup table for air (n0 = 1.00030) driving a
+  homogeneous n = n0 run, against the closed form IFFT[r(zeta_fs)^s FFT w]."""
+import math
+
+import numpy as np
+import pytest
+
+from util import gpu_propagator, gpu_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    from paper_2410_17446_gb300 import build, prop
+    build.build()
+    return prop
+
+
+def _oracle(W, table, steps):
+    from oracle import propagator as orp
+    b = W.beams[0]
+    return orp.run(b, W.k0, W.n0, table, W.ncomp, steps, tol=1e-12)
+
+
+def test_rotated_pade_table_fp64(P):
+    from oracle import aaa_lawson as al
+    from paper_2410_17446_gb300 import tables, workloads as wl
+    W = wl.plain_scalar_64(4)
+    d = tables.load("pade_scalar_64")
+    pr = gpu_propagator(W, "pade_scalar_64", P.PROP_FP64, tol=1e-12)
+    got = gpu_run(pr, W, 4)[0]
+    ref = _oracle(W, al.PoleTable.from_json(d), 4)
+    assert rel_l2(got, ref) < 1e-10
+    assert pr.iterations().shape[-1] == 10
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_multiwave_steps_28_poles(P, prec, bar):
+    from oracle import aaa_lawson as al
+    from paper_2410_17446_gb300 import tables, workloads as wl
+    W = wl.multiwave_scalar_64(2)
+    pr = gpu_propagator(W, "multiwave_scalar_64", P.PROP_FP64 if prec == "fp64" else P.PROP_FP32,
+                        **({"tol": 1e-12} if prec == "fp64" else {}))
+    got = gpu_run(pr, W, 2)[0]
+    ref = _oracle(W, al.PoleTable.from_json(tables.load("multiwave_scalar_64")), 2)
+    assert rel_l2(got, ref) < bar
+    assert pr.iterations().shape[-1] == 28
+
+
+def test_lookup_entry_drives_a_homogeneous_run(P):
+    """n0 = 1.00030 and n^2 = n0^2 everywhere: delta = 0, so each step is the
+    free-space rational step of Eq. approx_fs_prop with the looked-up table."""
+    from oracle import aaa_lawson as al
+    from oracle import propagator as orp
+    from paper_2410_17446_gb300 import prop as Pm, tables, workloads as wl
+    n0, dz = 1.0003, 0.5
+    e = tables.lookup(n0, 2 * math.pi * dz)
+    g = wl.Grid(256, 256, 0.25, 0.25)
+    w0 = wl.gaussian_beam(g, 3.0)[None]
+    pr = Pm.Propagator.from_table([(g.nx, g.ny, g.dx, g.dy)], 2 * math.pi, n0, dz, e, precision=P.PROP_FP32)
+    pr.set_field(0, w0)
+    pr.set_medium(0, np.full((g.ny, g.nx), n0 * n0, np.complex128))
+    for _ in range(10):
+        pr.step()
+    got = pr.get_field(0)
+    ref = orp.homogeneous_rational_step(w0, g.dx, g.dy, 2 * math.pi * n0, al.PoleTable.from_json(e), 10)
+    assert rel_l2(got, ref) < 1e-5
+    assert pr.iterations().max() == 0
