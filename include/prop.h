@@ -149,7 +149,19 @@ int prop_set_medium(prop* h, int32_t beam, const void* n2);
 int prop_set_field(prop* h, int32_t beam, const void* w);
 int prop_get_field(prop* h, int32_t beam, void* w);
 
-/* Advance every beam by dz (one z-step, Eq. approx_prop). */
+/* The longitudinal component E3 of one beam's current field (envelope, same
+ * exp(i k0 n0 z) factor as w), recovered from Gauss's law div(n^2 E) = 0 (Sec. 2:
+ * within a step n^2 = n^2(x, y), so E3 follows from (w1, w2) and the current
+ * medium).  The z-derivative of each plane-wave component of D = n^2 E is taken
+ * in the reference medium, i kz D3^ = -i (kx D1^ + ky D2^) with
+ * kz = sqrt((k0 n0)^2 - kx^2 - ky^2), Im kz >= 0 (Eq. exp_prop_planewave), and
+ * E3 = D3 / n^2; exact for a homogeneous medium.  kx, ky are first-derivative
+ * symbols (Nyquist entry 0); a mode with kz = 0 exactly gets 0.  Vector handles
+ * only (PROP_E_UNSUPPORTED otherwise).  out: complex128 [ny][nx], host or device
+ * (synchronises for host memory).  Uses the beam's FFT scratch between steps. */
+int prop_get_e3(prop* h, int32_t beam, void* out);
+
+/* Advance every beam by dz (one z-step, Eq. approx_prop). *//* Advance every beam by dz (one z-step, Eq. approx_prop). */
 int prop_step(prop* h);
 
 /* Callback run before step s (0-based within this call); it may call

@@ -76,6 +76,7 @@ template <typename T> struct GV {
                  //                X = psit_xy, px = psit_x, py = psit_y (psit = psi/(k0 n0)^2, psi = Log n^2)
   C* Tmp2;       // [nsys][ncomp][npts] second column-pass output (the d/dy branch)
   T kx0, ky0;    // 2 pi/(nx dx), 2 pi/(ny dy): wavenumber of FFT index 1
+  double kx0d, ky0d;   // the same in FP64
   int* err;      // error word: 1 = a bounded wait for an asynchronous copy gave up, 2 = TMA alignment check failed
   const int* ulist;   // optional: grid row y works on unit ulist[y] (the compacted iterating systems)
 };
@@ -1040,6 +1041,70 @@ __global__ void __launch_bounds__(NT) k_field_io(GV<T> g, int slot, double2* sta
       if (to_field) g.W64[i] = stage[p];
       else stage[p] = g.W64[i];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// E3 from Gauss's law (Sec. 2): div(n^2 E) = 0 with n^2 = n^2(x, y) in a step and
+// the z-derivative of each plane wave of D taken in the reference medium,
+// i kz D3^ = -i (kx D1^ + ky D2^), kz = sqrt((k0 n0)^2 - kx^2 - ky^2), Im kz >= 0.
+// Working planes hold D' = (n^2/n0^2) w = (1 + delta) w.
+// ---------------------------------------------------------------------------
+// D'_c = (1 + delta) w_c for both components of beam `slot` into work[2][npts].
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_e3_pre(GV<T> g, int slot, typename Cx<T>::t* work) {
+  using C = typename Cx<T>::t;
+  const C* d = g.delta + (long)slot * g.npts;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < g.npts; p += (long)gridDim.x * NT) {
+    C r = d[p];
+    r.x += (T)1;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const long i = ((long)slot * 2 + c) * g.npts + p;
+      C w;
+      if constexpr (sizeof(T) == 4) {   // double-float field: the hi plane is the FP32 value
+        w = reinterpret_cast<const float2*>(g.W64)[i];
+      } else {
+        w = g.W64[i];
+      }
+      work[(long)c * g.npts + p] = cmul(r, w);
+    }
+  }
+}
+
+// In Fourier space: work[0] = -(kx D1^ + ky D2^)/kz / (nx ny) (the inverse
+// transform's scale folded in); kx, ky as first derivatives (Nyquist entry 0),
+// kz from the full wavenumbers; a mode with kz = 0 gets 0.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_e3_spectral(GV<T> g, typename Cx<T>::t* work, double k0n0) {
+  using C = typename Cx<T>::t;
+  const double sc = 1.0 / (double)g.npts;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < g.npts; p += (long)gridDim.x * NT) {
+    const int i = (int)(p % g.nx), n = (int)(p / g.nx);
+    const double kxf = (double)ffreq(i, g.nx) * (double)g.kx0d, kyf = (double)ffreq(n, g.ny) * (double)g.ky0d;
+    const double kx = ((g.nx % 2) == 0 && i == g.nx / 2) ? 0.0 : kxf;
+    const double ky = ((g.ny % 2) == 0 && n == g.ny / 2) ? 0.0 : kyf;
+    const double a = k0n0 * k0n0 - kxf * kxf - kyf * kyf;
+    // 1/kz: kz = sqrt(a) (propagating) or i sqrt(-a) (evanescent, Im kz > 0)
+    double2 ikz = make_double2(0.0, 0.0);
+    if (a > 0.0) ikz.x = 1.0 / sqrt(a);
+    else if (a < 0.0) ikz.y = -1.0 / sqrt(-a);
+    const double2 d1 = to_d(work[p]), d2 = to_d(work[g.npts + p]);
+    const double2 num = make_double2(-(kx * d1.x + ky * d2.x) * sc, -(kx * d1.y + ky * d2.y) * sc);
+    work[p] = to_c(make_double2(num.x * ikz.x - num.y * ikz.y, num.x * ikz.y + num.y * ikz.x), T());
+  }
+}
+
+// E3 = D3 / (1 + delta) into the complex128 stage.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_e3_post(GV<T> g, int slot, const typename Cx<T>::t* work, double2* stage) {
+  using C = typename Cx<T>::t;
+  const C* d = g.delta + (long)slot * g.npts;
+  for (long p = (long)blockIdx.x * NT + threadIdx.x; p < g.npts; p += (long)gridDim.x * NT) {
+    const double2 r = to_d(d[p]);
+    const double2 v = to_d(work[p]);
+    const double rx = 1.0 + r.x, ry = r.y, den = rx * rx + ry * ry;
+    stage[p] = make_double2((v.x * rx + v.y * ry) / den, (v.y * rx - v.x * ry) / den);
   }
 }
 

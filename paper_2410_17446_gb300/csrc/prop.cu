@@ -190,8 +190,10 @@ template <typename T> GV<T> view(const prop* h, const Group& G) {
   g.Tmp2 = (C*)(b + L.Tmp2);
   g.err = (int*)(b + h->counts_off) + ERR_SLOT;
   g.ulist = nullptr;
-  g.kx0 = (T)(2.0 * M_PI / ((double)G.nx * G.dx));
-  g.ky0 = (T)(2.0 * M_PI / ((double)G.ny * G.dy));
+  g.kx0d = 2.0 * M_PI / ((double)G.nx * G.dx);
+  g.ky0d = 2.0 * M_PI / ((double)G.ny * G.dy);
+  g.kx0 = (T)g.kx0d;
+  g.ky0 = (T)g.ky0d;
   return g;
 }
 
@@ -891,6 +893,40 @@ template <typename T> int psi_derivatives(prop* h, Group& G, int slot) {
   return PROP_OK;
 }
 
+// E3 of one beam from Gauss's law (prop_get_e3): D' = (1 + delta) w into the
+// beam's two Btmp planes, 2-D DFT of both, the spectral combination, inverse
+// DFT, division by 1 + delta into the complex128 stage.
+template <typename T> int e3_impl(prop* h, Group& G, int slot) {
+  using C = typename Cx<T>::t;
+  GV<T> g = view<T>(h, G);
+  cudaStream_t st = h->stream;
+  const long npts = g.npts;
+  C* work = g.Btmp + (long)slot * 2 * npts;
+  double2* stage = (double2*)(h->ws + G.off.stage);
+  const int blocks = (int)std::min<long>(1024, (npts + 255) / 256);
+  { Prof p_(h, K_FIELD_IO, (16.0 + 3 * sizeof(C)) * npts);
+    k_e3_pre<T, 256><<<blocks, 256, 0, st>>>(g, slot, work); }
+  CK(cudaGetLastError());
+  GV<T> g1 = g;
+  g1.ncomp = 1;   // two single planes
+  { Prof p_(h, K_ROWS_FWD, 4.0 * sizeof(C) * npts);
+    CK(rows_fwd<T, C>(g1, buf(work, npts), buf(work, npts), -1, nullptr, 2, st)); }
+  { Prof p_(h, K_COLS, 4.0 * sizeof(C) * npts);
+    CK(cols<T>(g1, buf(work, npts), buf(work, npts), -1, 1, MUL_NONE, 0, 0, -1, (T)1, 2, st)); }
+  { Prof p_(h, K_FIELD_IO, 3.0 * sizeof(C) * npts);
+    k_e3_spectral<T, 256><<<blocks, 256, 0, st>>>(g, work, h->k0 * h->n0); }
+  CK(cudaGetLastError());
+  { Prof p_(h, K_COLS, 2.0 * sizeof(C) * npts);
+    CK(cols<T>(g1, buf(work, npts), buf(work, npts), -1, 0, MUL_NONE, 1, 0, -1, (T)1, 1, st)); }
+  { Prof p_(h, K_ROWS_INV, 2.0 * sizeof(C) * npts);
+    CK(rows_inv<T>(g1, buf(work, npts), buf(work, npts), -1, 0, epi(EPI_STORE), 1, st)); }
+  { Prof p_(h, K_FIELD_IO, (16.0 + 2 * sizeof(C)) * npts);
+    k_e3_post<T, 256><<<blocks, 256, 0, st>>>(g, slot, work, stage); }
+  CK(cudaGetLastError());
+  G.carry = false;   // the beam's Btmp planes were used as scratch
+  return PROP_OK;
+}
+
 int validate_opts(const prop_opts* o) {
   if (!o) return PROP_E_ARG;
   if (o->ncomp != 1 && o->ncomp != 2) return PROP_E_UNSUPPORTED;
@@ -1091,6 +1127,22 @@ int prop_get_field(prop* h, int32_t beam, void* w) {
   CK(cudaMemcpyAsync(w, h->ws + G.off.stage, F * 16, cudaMemcpyDefault, h->stream));
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, w) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return PROP_OK;
+}
+
+int prop_get_e3(prop* h, int32_t beam, void* out) {
+  if (!h || !out || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
+  if (h->C != 2) return PROP_E_UNSUPPORTED;
+  Group& G = h->groups[h->beam_group[beam]];
+  const int slot = h->beam_slot[beam];
+  const int rc = h->prec == PROP_FP64 ? e3_impl<double>(h, G, slot) : e3_impl<float>(h, G, slot);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(out, h->ws + G.off.stage, G.npts * 16, cudaMemcpyDefault, h->stream));
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, out) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
     cudaGetLastError();
     CK(cudaStreamSynchronize(h->stream));
   }

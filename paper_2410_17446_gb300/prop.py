@@ -70,6 +70,7 @@ _SIGS = {
     "prop_set_field": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "prop_get_field": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "prop_step": (ct.c_int, [ct.c_void_p]),
+    "prop_get_e3": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "prop_run": (ct.c_int, [ct.c_void_p, ct.c_int32, MEDIUM_FN, ct.c_void_p]),
     "prop_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(prop_stats)]),
     "prop_get_iterations": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
@@ -233,6 +234,14 @@ class Propagator:
         if out is None:
             out = np.empty(self.shape(beam), np.complex128)
         check(lib().prop_get_field(self.h, beam, _dptr(out)), "prop_get_field")
+        return out
+
+    def get_e3(self, beam: int, out=None):
+        """E3 recovered from Gauss's law for the beam's current field (vector handles)."""
+        if out is None:
+            g = self.grids[beam]
+            out = np.empty((g.ny, g.nx), np.complex128)
+        check(lib().prop_get_e3(self.h, beam, _dptr(out)), "prop_get_e3")
         return out
 
     def step(self) -> None:
