@@ -309,7 +309,7 @@ class Runner:
         grids = [(b.grid.nx, b.grid.ny, b.grid.dx, b.grid.dy) for b in W.beams]
         with self.torch.cuda.stream(self.stream):
             pr = P.Propagator.from_table(grids, W.k0, W.n0, W.dz, self.tab, ncomp=W.ncomp, precision=P.PROP_FP32,
-                                         restart=W.restart, stream=self.stream,
+                                         restart=self.args.restart or W.restart, stream=self.stream,
                                          guess=P.PROP_GUESS_LEARNED if guess == "learned" else P.PROP_GUESS_ZERO)
             if guess == "learned":
                 net = self.load_net()
@@ -443,6 +443,15 @@ def ours(args) -> None:
         for nm in names:
             cpu[nm] = run_oracle_sample(nm, 1, os.path.join(tmpdir, nm + ".npz"))
 
+    # FFT pass variants for the grid sizes in use: the committed plans measured on this
+    # GPU model, else tuned here (prop_fft_autotune) before anything is timed
+    from paper_2410_17446_gb300 import autotune as AT
+    sizes = set()
+    for nm in names:
+        for b in make_workload(nm, 1, args.n).beams:
+            sizes |= {b.grid.nx, b.grid.ny}
+    plans = AT.load_or_tune(sizes, P.PROP_FP32, write=False, retune=args.retune)
+
     stream = torch.cuda.Stream(device=dev)
     legs = {}
     main = None
@@ -518,7 +527,7 @@ def ours(args) -> None:
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "points_per_step": W.points, "beams": len(W.beams),
                            "grid": f"{W.beams[0].grid.nx}x{W.beams[0].grid.ny}", "poles": W.npoles,
-                           "ncomp": W.ncomp, "restart": W.restart, "tol": pr.opts.tol,
+                           "ncomp": W.ncomp, "restart": pr.opts.restart, "tol": pr.opts.tol,
                            "precond": "mean n^2" if pr.opts.precond == P.PROP_PRECOND_MEAN else "free space",
                            "l2": "flushed (256 MiB write) between timed steps",
                            "parallelism": f"replicas x{ws}"},
@@ -528,7 +537,9 @@ def ours(args) -> None:
                 "rel_l2_vs_oracle": d0.get("rel_l2_vs_oracle"),
                 "rel_err_vs_closed_form": acc,
                 "rel_err_steps": CONFIG_STEPS[args.workload] if acc is not None else None,
-                "legs": legs, "e2e": e2e}
+                "legs": legs, "e2e": e2e,
+                "fft_plans": {str(n): {k: r[k] for k in ("rows", "cols", "rows_ms", "cols_ms", "source")}
+                              for n, r in plans.items()}}
         if args.workload in cpu:
             c = cpu[args.workload]
             line["cpu_baseline"] = {"value": c["value"], "unit": UNIT, "cores": c["cores"], "kind": "oracle",
@@ -554,6 +565,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="shrink the grid (profiling runs only; not a bench line)")
+    ap.add_argument("--restart", type=int, default=0, help="GMRES restart length (default: the workload's)")
+    ap.add_argument("--retune", action="store_true", help="time the FFT variants here even if plans are cached")
     ap.add_argument("--guess", default="both", choices=["plain", "both"],
                     help="both: also time the learned initial guess (GMRES to the same tolerance)")
     args = ap.parse_args()

@@ -86,9 +86,23 @@ typedef struct prop_opts {
                               (dbar = mean delta), which carries the absorbing border's mean loss,
                               as the paper's preconditioner carries its PML.  Both are diagonal in
                               Fourier space. */
+  int32_t form;            /* PROP_FORM_EXPONENTIAL: prop_step applies r(Z) (Eq. approx_prop).
+                              PROP_FORM_PSEUDODIFF: the table is the partial-fraction form of a
+                              square root S(zeta) ~ sqrt(1 + zeta) (Sec. 3.2, Eq. pf_sqrt_exp: s0 =
+                              c_alpha + sum wt_j, poles -(1 + i alpha sigma_j), residues
+                              -i alpha wt_j (1 + sigma_j)) and prop_step advances dw/dz =
+                              i k0 n0 (S(Z) - I) w (Eqs. eq_barZfactor2, eq:ApproxPropagator_W) by dz
+                              with `substeps` classical Runge-Kutta steps; each stage applies S(Z)
+                              by the same shifted solves (Eq. eq:Auxiliary_W).  The paper names no
+                              z-integrator; RK4 is this library's choice. */
+  int32_t substeps;        /* RK4 steps per dz for PROP_FORM_PSEUDODIFF; 0 = the fewest with
+                              h k0 n0 (1 + sqrt(1.5 + |zeta_min|)) <= 2.5 on every grid, zeta_min =
+                              -((pi/dx)^2 + (pi/dy)^2)/(k0 n0)^2 (inside RK4's stability region on
+                              the operator's spectrum) */
 } prop_opts;
 
 enum prop_precond { PROP_PRECOND_FREESPACE = 0, PROP_PRECOND_MEAN = 1 };
+enum prop_form { PROP_FORM_EXPONENTIAL = 0, PROP_FORM_PSEUDODIFF = 1 };
 
 enum prop_guess { PROP_GUESS_ZERO = 0, PROP_GUESS_LEARNED = 1 };
 #define PROP_GUESS_CHANNELS 16   /* padded input / output width of the guess network */
@@ -119,7 +133,7 @@ typedef struct prop_kernel_profile {
 typedef struct prop prop; /* opaque handle */
 
 /* Fill *o with the defaults for `precision` (tol 1e-12 FP64, 1e-7 FP32; restart 20;
- * PROP_GUESS_ZERO; PROP_PRECOND_MEAN). */
+ * PROP_GUESS_ZERO; PROP_PRECOND_MEAN; PROP_FORM_EXPONENTIAL, substeps 0). */
 int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision);
 
 /* Bytes of device workspace prop_create needs for these beams and options.
@@ -161,7 +175,11 @@ int prop_get_field(prop* h, int32_t beam, void* w);
  * (synchronises for host memory).  Uses the beam's FFT scratch between steps. */
 int prop_get_e3(prop* h, int32_t beam, void* out);
 
-/* Advance every beam by dz (one z-step, Eq. approx_prop). *//* Advance every beam by dz (one z-step, Eq. approx_prop). */
+/* Runge-Kutta steps per dz of a PROP_FORM_PSEUDODIFF handle (the automatic
+ * choice when opts.substeps was 0); 0 for the exponential form. */
+int prop_get_substeps(prop* h, int32_t* substeps);
+
+/* Advance every beam by dz (one z-step, Eq. approx_prop). */
 int prop_step(prop* h);
 
 /* Callback run before step s (0-based within this call); it may call
@@ -207,6 +225,36 @@ void prop_destroy(prop* h);
 int prop_fft2_workspace_size(int32_t nx, int32_t ny, int32_t precision, size_t* bytes);
 int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t inverse,
               void* d_data, void* d_work, size_t work_bytes, void* stream);
+
+/* ---- FFT plans and their autotuner (the paper has no counterpart) ------ *
+ * Each FFT pass has variants with the same arithmetic: the row pass by a
+ * block-wide shared-memory Stockham transform or by warps (one row per warp,
+ * N = 512 and 1024 only); the column pass by TMA tiles of 32-byte rows, by
+ * plain loads, or by warps (one column per warp in registers, N = 512 and 1024
+ * only).  The choice is process-wide per (size, precision) and read at every
+ * launch, so it applies to every handle; set it between steps, not while work
+ * of another thread is being enqueued.  Defaults: PROP_ROWS_BLOCK,
+ * PROP_COLS_TMA. */
+enum prop_fft_rows { PROP_ROWS_BLOCK = 0, PROP_ROWS_WARP = 1 };
+enum prop_fft_cols { PROP_COLS_TMA = 0, PROP_COLS_PLAIN = 1, PROP_COLS_WARP = 2 };
+typedef struct prop_fft_plan { int32_t rows, cols; } prop_fft_plan;
+
+/* Current plan for size n (a supported size) and precision. */
+int prop_get_fft_plan(int32_t n, int32_t precision, prop_fft_plan* out);
+/* Install a plan; PROP_E_UNSUPPORTED if a variant does not exist for n. */
+int prop_set_fft_plan(int32_t n, int32_t precision, const prop_fft_plan* plan);
+/* Device bytes prop_fft_autotune needs for `batch` n x n arrays. */
+int prop_fft_autotune_workspace_size(int32_t n, int32_t precision, int32_t batch, size_t* bytes);
+/* Time every variant on `batch` n x n arrays in d_work (256-byte aligned,
+ * contents overwritten): a row round trip (forward then inverse rows) per row
+ * variant and a column pass (forward, scale, inverse) per column variant, best
+ * of `reps` runs after one warm-up, CUDA events on `stream`.  ms[5] receives the
+ * times in ms (rows block, rows warp, cols TMA, cols plain, cols warp; -1 for a
+ * variant that does not exist) and *best the fastest of each pass.  Installs
+ * nothing (call prop_set_fft_plan) and leaves the current plan unchanged.
+ * Synchronises the stream. */
+int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps, void* d_work, size_t work_bytes,
+                      void* stream, prop_fft_plan* best, float* ms);
 
 /* Install the initial-guess network (include/prop_cnn.h) for PROP_GUESS_LEARNED.
  * The paper has no learned part: GMRES still runs to the same tolerance, the

@@ -78,6 +78,20 @@ def lookup_table() -> dict:
             "source": "oracle.make_tables (AAA-Lawson oracle, uniform samples on [-4, 2])"}
 
 
+def cauchy_table() -> dict:
+    """The Cauchy-integral square root of Sec. 3.2 (N = 25, alpha = 1), the table
+    of the pseudo-differential form (S(zeta) ~ sqrt(1 + zeta); K is not used)."""
+    from . import cauchy
+    T = cauchy.cauchy_sqrt_table(25, 1.0)
+    d = T.to_json()
+    z = np.linspace(-4, 2, 6001)
+    far = np.abs(z + 1) > 0.2
+    d["fit_max_err"] = float(np.max(np.abs(T(z[far]) - np.sqrt(1 + z[far] + 0j))))
+    d["kind"] = "cauchy_sqrt"
+    d["alpha"] = 1.0
+    return d
+
+
 def main(argv=None) -> int:
     sys.path.insert(0, os.path.dirname(HERE))
     from paper_2410_17446_gb300 import workloads as wl
@@ -89,9 +103,13 @@ def main(argv=None) -> int:
         "vector_random_512": lambda: wl.vector_random_512(1, n=128),
         "uneven_batch": lambda: wl.uneven_batch(nbeams=48, nsteps=1, sizes=(128,)),
         "multiwave_scalar_64": lambda: wl.multiwave_scalar_64(1),
+        "sineprod_q2": lambda: wl.sineprod_helmholtz(2.0, 1, 64),
+        "sineprod_q1": lambda: wl.sineprod_helmholtz(1.0, 1, 64),
+        "sineprod_q05": lambda: wl.sineprod_helmholtz(0.5, 1, 64),
     }
     extra = {"pade_scalar_64": lambda: pade_table(wl.plain_scalar_64(1)),
-             "lookup_n0_1.0003": lookup_table}
+             "lookup_n0_1.0003": lookup_table,
+             "cauchy_sqrt_25": cauchy_table}
     names = argv or (list(makers) + list(extra))
     for name in names:
         if name in extra:

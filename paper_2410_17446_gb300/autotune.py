@@ -1,0 +1,103 @@
+"""FFT plan autotuner: times the variants of the row and column passes on this
+GPU (prop_fft_autotune) and installs the fastest (prop_set_fft_plan).
+
+Results are cached as JSON keyed by the GPU's name: ``load_or_tune`` installs a
+cached plan when one exists for this GPU and size, and otherwise tunes, installs
+and records it.  The package ships the plans measured on GB300 in
+``tune/fft_plans.json``.  The tuning data are ``batch`` n x n complex arrays of
+at least 256 MiB in all, more than the L2 cache, so that each timing reads HBM.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Iterable, Optional
+
+from . import prop as P
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "tune", "fft_plans.json")
+ROWS = {P.PROP_ROWS_BLOCK: "block", P.PROP_ROWS_WARP: "warp"}
+COLS = {P.PROP_COLS_TMA: "tma", P.PROP_COLS_PLAIN: "plain", P.PROP_COLS_WARP: "warp"}
+PREC = {P.PROP_FP32: "fp32", P.PROP_FP64: "fp64"}
+
+
+def gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def tune(n: int, precision: int, reps: int = 5, min_bytes: int = 256 << 20) -> dict:
+    """Time every variant for size n; returns the record (times and the best plan)."""
+    import torch
+    cs = 8 if precision == P.PROP_FP32 else 16
+    batch = max(1, -(-min_bytes // (n * n * cs)))
+    nb = P.prop_fft_autotune_workspace_size(n, precision, batch)
+    work = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    best, ms = P.prop_fft_autotune(n, precision, batch, reps, work, nb, stream)
+    del work
+    return {"n": n, "precision": PREC[precision], "batch": batch, "reps": reps,
+            "rows_ms": {"block": ms[0], "warp": ms[1] if ms[1] >= 0 else None},
+            "cols_ms": {"tma": ms[2] if ms[2] >= 0 else None, "plain": ms[3], "warp": ms[4] if ms[4] >= 0 else None},
+            "rows": ROWS[best.rows], "cols": COLS[best.cols]}
+
+
+def install(rec: dict) -> None:
+    prec = {v: k for k, v in PREC.items()}[rec["precision"]]
+    rows = {v: k for k, v in ROWS.items()}[rec["rows"]]
+    cols = {v: k for k, v in COLS.items()}[rec["cols"]]
+    P.prop_set_fft_plan(rec["n"], prec, rows, cols)
+
+
+def _read(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def load_or_tune(sizes: Iterable[int], precision: int = P.PROP_FP32, path: Optional[str] = None,
+                 write: bool = True, retune: bool = False) -> Dict[int, dict]:
+    """Install a plan for each size: from the cache for this GPU, else by tuning
+    (then recorded in the cache when `write`).  Returns the records used."""
+    path = path or CACHE
+    data = _read(path)
+    name = gpu_name()
+    entry = data.setdefault(name, {})
+    used, changed = {}, False
+    for n in sorted(set(int(x) for x in sizes)):
+        key = f"{PREC[precision]}:{n}"
+        rec = None if retune else entry.get(key)
+        source = "cache"
+        if rec is None:
+            rec = tune(n, precision)
+            entry[key] = rec
+            changed, source = True, "tuned now"
+        install(rec)
+        used[n] = dict(rec, source=source, gpu=name)
+    if changed and write:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+    return used
+
+
+def main(argv=None) -> int:
+    """python -m paper_2410_17446_gb300.autotune [--out PATH] [--fp64] N [N ...]: tune and record."""
+    import argparse
+    from . import build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("sizes", type=int, nargs="+")
+    ap.add_argument("--out", default=CACHE)
+    ap.add_argument("--fp64", action="store_true")
+    a = ap.parse_args(argv)
+    build.build()
+    used = load_or_tune(a.sizes, P.PROP_FP64 if a.fp64 else P.PROP_FP32, a.out, retune=True)
+    print(json.dumps(used, indent=1))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -87,6 +87,40 @@ template <int M, bool INV, typename C> __device__ __forceinline__ C tw16(C a) {
   }
 }
 
+// cos(2 pi m / 32) for integer m, from the exact values of the 32nd roots of unity
+// (odd m; even m reduce to cos16).
+__host__ __device__ constexpr double cos32(int m) {
+  return ((m % 32 + 32) % 32) % 2 == 0 ? cos16(((m % 32 + 32) % 32) / 2) :
+         ((m % 32 + 32) % 32) == 1 ? 0.98078528040323044913 :
+         ((m % 32 + 32) % 32) == 3 ? 0.83146961230254523708 :
+         ((m % 32 + 32) % 32) == 5 ? 0.55557023301960222474 :
+         ((m % 32 + 32) % 32) == 7 ? 0.19509032201612826785 :
+         ((m % 32 + 32) % 32) == 9 ? -0.19509032201612826785 :
+         ((m % 32 + 32) % 32) == 11 ? -0.55557023301960222474 :
+         ((m % 32 + 32) % 32) == 13 ? -0.83146961230254523708 :
+         ((m % 32 + 32) % 32) == 15 ? -0.98078528040323044913 :
+         ((m % 32 + 32) % 32) == 17 ? -0.98078528040323044913 :
+         ((m % 32 + 32) % 32) == 19 ? -0.83146961230254523708 :
+         ((m % 32 + 32) % 32) == 21 ? -0.55557023301960222474 :
+         ((m % 32 + 32) % 32) == 23 ? -0.19509032201612826785 :
+         ((m % 32 + 32) % 32) == 25 ? 0.19509032201612826785 :
+         ((m % 32 + 32) % 32) == 27 ? 0.55557023301960222474 :
+         ((m % 32 + 32) % 32) == 29 ? 0.83146961230254523708 : 0.98078528040323044913;
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+// a * exp(-+ 2 pi i m / 32), sign by direction
+template <int M, bool INV, typename C> __device__ __forceinline__ C tw32(C a) {
+  if constexpr ((M % 2) == 0) return tw16<M / 2, INV>(a);
+  else {
+    using R = decltype(a.x);
+    constexpr double cr = cos32(M);
+    constexpr double ci = INV ? sin32(M) : -sin32(M);
+    C w; w.x = (R)cr; w.y = (R)ci;
+    return cmul(a, w);
+  }
+}
+
 template <bool INV, typename C> __device__ __forceinline__ void dft2(C* x) {
   C a = x[0], b = x[1];
   x[0] = a + b; x[1] = a - b;
@@ -144,12 +178,32 @@ template <bool INV, typename C> __device__ __forceinline__ void dft16(C* x) {
   }
 }
 
+// 32-point DFT (natural order in and out): two 16-point DFTs of the even and odd
+// points, then X[k] = E[k] + w32^k O[k], X[k+16] = E[k] - w32^k O[k].
+template <int K, bool INV, typename C> __device__ __forceinline__ void dft32_join(C* x, const C* e, const C* o) {
+  if constexpr (K < 16) {
+    const C t = tw32<K, INV>(o[K]);
+    x[K] = e[K] + t;
+    x[K + 16] = e[K] - t;
+    dft32_join<K + 1, INV>(x, e, o);
+  }
+}
+template <bool INV, typename C> __device__ __forceinline__ void dft32(C* x) {
+  C e[16], o[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) { e[k] = x[2 * k]; o[k] = x[2 * k + 1]; }
+  dft16<INV>(e);
+  dft16<INV>(o);
+  dft32_join<0, INV>(x, e, o);
+}
+
 template <int R, bool INV, typename C> __device__ __forceinline__ void dftR(C* x) {
   if constexpr (R == 2) dft2<INV>(x);
   else if constexpr (R == 3) dft3<INV>(x);
   else if constexpr (R == 4) dft4<INV>(x);
   else if constexpr (R == 8) dft8<INV>(x);
   else if constexpr (R == 16) dft16<INV>(x);
+  else if constexpr (R == 32) dft32<INV>(x);
 }
 
 // Radix plans: product equals N, at most three stages.
@@ -224,6 +278,123 @@ __device__ __forceinline__ void fft_smem(C* s, const C* __restrict__ tw, int tid
   fft_stage<C, N, P::R0, 1, INV, NV, NT, COL, TWS>(s, tw, tid);
   if constexpr (P::S >= 2) fft_stage<C, N, P::R1, P::R0, INV, NV, NT, COL, TWS>(s, tw, tid);
   if constexpr (P::S >= 3) fft_stage<C, N, P::R2, P::R0 * P::R1, INV, NV, NT, COL, TWS>(s, tw, tid);
+}
+
+// ---------------------------------------------------------------------------
+// Row transforms by warps: one warp transforms one N-point row (N = 32 L,
+// L = 32 or 16) held in shared memory in the padded row layout, with no block
+// barrier.  With n = n1 + 32 n2 and k = k2 + L k1:
+//   step 1 (lane n1):  Y[n1][k2] = sum_{n2<L} x[n1 + 32 n2] w_L^{n2 k2}, times w_N^{n1 k2}
+//   transpose through the row's own slots (Y[n1][k2] to slot 32 k2 + n1)
+//   step 2:            X[k2 + L k1] = sum_{n1<32} Y[n1][k2] w_32^{n1 k1}
+// For L = 32 lane k2 does one 32-point DFT.  For L = 16 two lanes share k2:
+// lane (k2, h) takes the odd/even half k1 = h + 2 k1' by one radix-2 step,
+// (Y[n] + (-1)^h Y[n + 16]) w_32^{h n}, then a 16-point DFT.
+// ---------------------------------------------------------------------------
+template <int N> __device__ __forceinline__ int rpad(int n) { return n + (n >> 4); }
+
+template <int K, bool INV, typename C> __device__ __forceinline__ void half_twiddle(C* y, int h) {
+  if constexpr (K < 16) {
+    const C t = tw32<K, INV>(y[K]);
+    y[K] = h ? t : y[K];
+    half_twiddle<K + 1, INV>(y, h);
+  }
+}
+
+template <typename C, int N, bool INV, bool TWS>
+__device__ __forceinline__ void warp_fft_row(C* row, const C* __restrict__ tw, int lane) {
+  constexpr int L = N / 32;
+  static_assert(L == 32 || L == 16, "warp row transform covers N = 1024 and N = 512");
+  C x[L];
+#pragma unroll
+  for (int n2 = 0; n2 < L; ++n2) x[n2] = row[rpad<N>(lane + 32 * n2)];
+  dftR<L, INV>(x);
+#pragma unroll
+  for (int k2 = 1; k2 < L; ++k2) {
+    C w = TWS ? tw[(lane * k2) % N] : __ldg(&tw[(lane * k2) % N]);
+    if (INV) w.y = -w.y;
+    x[k2] = cmul(x[k2], w);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k2 = 0; k2 < L; ++k2) row[rpad<N>(32 * k2 + lane)] = x[k2];
+  __syncwarp();
+  if constexpr (L == 32) {
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) x[n1] = row[rpad<N>(32 * lane + n1)];
+    dft32<INV>(x);
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) row[rpad<N>(lane + 32 * k1)] = x[k1];
+  } else {
+    const int k2 = lane & 15, h = lane >> 4;
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      const C a = row[rpad<N>(32 * k2 + n)], b = row[rpad<N>(32 * k2 + n + 16)];
+      x[n] = h ? a - b : a + b;
+    }
+    half_twiddle<0, INV>(x, h);
+    dft16<INV>(x);
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) row[rpad<N>(k2 + 16 * (h + 2 * k1))] = x[k1];
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// The same two-step transform for data already in registers: lane l holds the
+// points l + 32 m (m < L) of one length-N vector (N = 32 L, L = 32 or 16) and
+// gets back the transform at the same positions (k = l + 32 m), so a forward
+// transform, a pointwise multiply and an inverse transform chain in registers.
+// `slot(s)` maps a scratch slot s < N to this warp's shared memory; the
+// transpose writes slot 32 k2 + n1 and reads it back by k2.
+// ---------------------------------------------------------------------------
+template <typename C, int N, bool INV, typename SLOT>
+__device__ __forceinline__ void warp_fft_regs(C (&x)[N / 32], const C* __restrict__ tw, int lane, SLOT slot) {
+  constexpr int L = N / 32;
+  static_assert(L == 32 || L == 16, "register transform covers N = 1024 and N = 512");
+  dftR<L, INV>(x);
+#pragma unroll
+  for (int k2 = 1; k2 < L; ++k2) {
+    C w = __ldg(&tw[(lane * k2) % N]);
+    if (INV) w.y = -w.y;
+    x[k2] = cmul(x[k2], w);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k2 = 0; k2 < L; ++k2) *slot(32 * k2 + lane) = x[k2];
+  __syncwarp();
+  if constexpr (L == 32) {
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) x[n1] = *slot(32 * lane + n1);
+    dft32<INV>(x);      // lane k2 holds X[k2 + 32 k1] = position lane + 32 k1
+  } else {
+    const int k2 = lane & 15, h = lane >> 4;
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      const C a = *slot(32 * k2 + n), b = *slot(32 * k2 + n + 16);
+      x[n] = h ? a - b : a + b;
+    }
+    half_twiddle<0, INV>(x, h);
+    dft16<INV>(x);      // lane (k2, h) holds X[k2 + 16 (h + 2 k1')] = position lane + 32 k1'
+  }
+  __syncwarp();
+}
+
+// Row transform of the NV rows held in s (padded row layout; caller synchronises
+// before the call): by warps for N = 512 and 1024 when WF, else the block-wide
+// Stockham.
+template <typename C, int N, bool INV, int NV, int NT, bool WF = true, bool TWS = false>
+__device__ __forceinline__ void fft_rows(C* s, const C* __restrict__ tw, int tid) {
+  if constexpr (WF && (N == 1024 || N == 512) && NT >= 32) {
+    constexpr int NW = NT / 32;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int r = warp; r < NV; r += NW) warp_fft_row<C, N, INV, TWS>(s + r * (N + N / 16), tw, lane);
+    __syncthreads();
+  } else {
+    fft_smem<C, N, INV, NV, NT, false, TWS>(s, tw, tid);
+  }
 }
 
 }  // namespace prop_dev

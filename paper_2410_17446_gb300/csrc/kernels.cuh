@@ -198,7 +198,7 @@ template <typename T> __device__ __forceinline__ typename Cx<T>::t dbar_of(const
 // ---------------------------------------------------------------------------
 // Pass 1: forward row DFTs.  grid = (ny/NR, units*ncomp).
 // ---------------------------------------------------------------------------
-template <typename T, int N, int NR, int NT, typename SRC>
+template <typename T, int N, int NR, int NT, typename SRC, bool WF>
 __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, double* norm_acc) {
   using C = typename Cx<T>::t;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
     }
   }
   __syncthreads();
-  fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
+  fft_rows<C, N, false, NR, NT, WF>(s, g.twx, threadIdx.x);
   if (vec) {
 #pragma unroll
     for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   // once any CTA's copy has failed the step is void: issue no further copies, so
   // the CTAs still to come return at once instead of each waiting out its bound
-  if (*reinterpret_cast<volatile const int*>(g.err) != 0) return;
+  if (g.err == nullptr || *reinterpret_cast<volatile const int*>(g.err) != 0) return;
   const int x0 = blockIdx.x * NV;
   // self-check of the TMA alignment rules: 128-byte shared destinations, 64-byte
   // tensor maps, 16-byte x offsets; on a violation record it and do nothing
@@ -458,6 +458,106 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   }
 }
 
+// The column pass by warps (NY = 512 or 1024): a CTA of 8 warps takes 8 adjacent
+// columns (64-byte row segments, moved with 8-byte cp.async), one column per
+// warp.  A warp loads its column into registers (lane l: rows l + 32 m), and the
+// forward column DFT, the Fourier-diagonal multiply and the inverse column DFT
+// all run in registers (warp_fft_regs), with the column's own shared memory as
+// the transpose scratch.  Element (row n, column v) sits at 9 n + n/32 + v: the
+// odd row stride and the skew every 32 rows keep the column reads, the
+// transpose writes and the transpose reads free of bank conflicts.  Same
+// arithmetic as k_cols for the modes it serves (no spectrum output, no
+// multiplier table, no d/dy branch).
+constexpr int CW_NV = 8;
+template <int NY> __host__ __device__ constexpr int cw_elems() { return 9 * NY + NY / 32 + CW_NV; }
+__device__ __forceinline__ int cw_at(int n, int v) { return 9 * n + (n >> 5) + v; }
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T, int NY>
+__global__ void __launch_bounds__(32 * CW_NV) k_cols_warp(GV<T> g, Buf<typename Cx<T>::t> src,
+                                                        Buf<typename Cx<T>::t> dst, int mask, int fwd, int mul,
+                                                        int inv, int skip_homog, int pole, T scale) {
+  using C = typename Cx<T>::t;
+  constexpr int NT = 32 * CW_NV, L = NY / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
+  if (!unit_active(g.st, mask, u)) return;
+  if (skip_homog && !g.nonhomog[u / g.P]) return;
+  const int x0 = blockIdx.x * CW_NV;
+  const C* in = src.at(u, c, g.npts) + x0;
+#pragma unroll 8
+  for (int e = threadIdx.x; e < NY * CW_NV; e += NT) {
+    const int n = e / CW_NV, v = e % CW_NV;
+    if constexpr (sizeof(C) == 8) cp_async8(s + cw_at(n, v), in + (long)n * g.nx + v);
+    else cp_async16(s + cw_at(n, v), in + (long)n * g.nx + v);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int v = threadIdx.x >> 5, lane = threadIdx.x & 31, i = x0 + v;
+  auto slot = [&](int q) { return s + cw_at(q, v); };
+  C x[L];
+#pragma unroll
+  for (int m = 0; m < L; ++m) x[m] = *slot(lane + 32 * m);
+  if (fwd) warp_fft_regs<C, NY, false>(x, g.twy, lane, slot);
+  if (mul != MUL_NONE) {
+    const bool pm = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD || mul == MUL_PREC_INV);
+    const int k = pm ? (pole >= 0 ? pole : u % g.P) : 0;
+    C sh; sh.x = 0; sh.y = 0;
+    if (mul == MUL_PREC_INV) sh = dbar_of(g, u / g.P);
+    T axh = 0, axl = 0, pim = 0;
+    const T* ay = nullptr;
+    if (pm) {
+      axh = g.ax[((long)k * g.nx + i) * 2];
+      axl = g.ax[((long)k * g.nx + i) * 2 + 1];
+      ay = g.ay + (long)k * g.ny * 2;
+      pim = g.pim[k] + sh.y;
+    }
+#pragma unroll
+    for (int m = 0; m < L; ++m) {
+      const int n = lane + 32 * m;
+      C a = x[m];
+      if (mul == MUL_SCALE) {
+        a.x *= scale; a.y *= scale;
+      } else if (mul == MUL_DY) {
+        a = cmul(a, ik_factor<C>(n, g.ny, g.ky0));
+        a.x *= scale; a.y *= scale;
+      } else if (mul == MUL_DYY) {
+        const T kk = (T)ffreq(n, g.ny) * g.ky0;
+        a.x *= -kk * kk * scale; a.y *= -kk * kk * scale;
+      } else {   // Re(zeta_fs - p) from (hi, lo) pairs, as in k_cols
+        const T re = ((axh + __ldg(&ay[2 * n])) + (axl + __ldg(&ay[2 * n + 1]))) + sh.x;
+        C f;
+        if (mul != MUL_POLE_FWD) {
+          const T d = scale / (re * re + pim * pim);
+          f.x = re * d; f.y = -pim * d;
+        } else {
+          f.x = re * scale; f.y = pim * scale;
+        }
+        a = cmul(a, f);
+      }
+      x[m] = a;
+    }
+  }
+  if (inv) warp_fft_regs<C, NY, true>(x, g.twy, lane, slot);
+#pragma unroll
+  for (int m = 0; m < L; ++m) *slot(lane + 32 * m) = x[m];
+  __syncthreads();
+  C* out = dst.at(u, c, g.npts) + x0;
+#pragma unroll 8
+  for (int e = threadIdx.x; e < NY * CW_NV; e += NT) {
+    const int n = e / CW_NV, vv = e % CW_NV;
+    out[(long)n * g.nx + vv] = s[cw_at(n, vv)];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pass 3: inverse row DFTs and the pointwise epilogue.  grid = (ny/NR, units*ncomp).
 // ---------------------------------------------------------------------------
@@ -473,7 +573,7 @@ struct EpiArgs {
 
 // ARN: the instantiation for the EPI_ARNOLDI epilogue (kept apart so that the
 // other epilogues do not carry its register footprint).
-template <typename T, int N, int NR, int NT, bool ARN>
+template <typename T, int N, int NR, int NT, bool ARN, bool WF>
 __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, int skip_homog, EpiArgs ep) {
   using C = typename Cx<T>::t;
@@ -527,7 +627,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     }
   }
   __syncthreads();
-  fft_smem<C, N, true, NR, NT, false>(s, g.twx, threadIdx.x);
+  fft_rows<C, N, true, NR, NT, WF>(s, g.twx, threadIdx.x);
   const C* dl = g.delta + (long)beam * g.npts + off;
   const long unit_off = ((long)u * g.ncomp + c) * g.npts + off;   // [unit][c][pt] arrays
   if constexpr (ARN) {
@@ -651,7 +751,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   }
   if (ep.mode == EPI_ACCUM64 && ep.fwd_out) {   // forward row DFT of the new field for the next step
     __syncthreads();
-    fft_smem<C, N, false, NR, NT, false>(s, g.twx, threadIdx.x);
+    fft_rows<C, N, false, NR, NT, WF>(s, g.twx, threadIdx.x);
     C* o = reinterpret_cast<C*>(ep.fwd_out) + unit_off;
     if (sizeof(T) == 4 && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
       for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {
@@ -730,7 +830,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
     }
   }
   __syncthreads();
-  fft_smem<C, N, true, NVV, NT, false>(s, g.twx, threadIdx.x);
+  fft_rows<C, N, true, NVV, NT>(s, g.twx, threadIdx.x);
   const C* cf = g.psi + (long)beam * 5 * g.npts + off;    // D1, D2, X, px, py planes
   const long F = 2 * g.npts;
   double acc = 0.0, acc2 = 0.0;
@@ -1105,6 +1205,63 @@ __global__ void __launch_bounds__(NT) k_e3_post(GV<T> g, int slot, const typenam
     const double2 v = to_d(work[p]);
     const double rx = 1.0 + r.x, ry = r.y, den = rx * rx + ry * ry;
     stage[p] = make_double2((v.x * rx + v.y * ry) / den, (v.y * rx - v.x * ry) / den);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Classical Runge-Kutta for the pseudo-differential form dw/dz = i k0 n0 (S(Z) - I) w
+// (Sec. 3.2).  The field arrays hold L = nb ncomp npts points: complex128 for FP64,
+// double-float planes (hi, then lo) for FP32; the stage data are complex128.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ double2 field_get(const double2* W, long i, long L) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 h = reinterpret_cast<const float2*>(W)[i], l = reinterpret_cast<const float2*>(W)[L + i];
+    return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+  } else {
+    return W[i];
+  }
+}
+template <typename T> __device__ __forceinline__ void field_put(double2* W, long i, long L, double2 v) {
+  if constexpr (sizeof(T) == 4) {
+    float2 h, l;
+    h.x = (float)v.x; h.y = (float)v.y;
+    l.x = (float)(v.x - (double)h.x); l.y = (float)(v.y - (double)h.y);
+    reinterpret_cast<float2*>(W)[i] = h;
+    reinterpret_cast<float2*>(W)[L + i] = l;
+  } else {
+    W[i] = v;
+  }
+}
+
+// dst = field (copies of the field at the start of a step or substep)
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_rk_copy(const double2* W, double2* d0, double2* d1, long L) {
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < L; i += (long)gridDim.x * NT) {
+    const double2 v = field_get<T>(W, i, L);
+    d0[i] = v;
+    if (d1) d1[i] = v;
+  }
+}
+// field = src
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_rk_restore(double2* W, const double2* src, long L) {
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < L; i += (long)gridDim.x * NT) field_put<T>(W, i, L, src[i]);
+}
+// After a stage: Wcur holds S(Z) y, Wprev holds y.  k = i k0n0 (S y - y),
+// ACC += hb k; the field becomes the next stage's input W0 + hc k, or ACC after
+// the last stage.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_rk_stage(double2* Wcur, const double2* Wprev, const double2* W0, double2* ACC,
+                                                 long L, double hb, double hc, double k0n0, int last) {
+  for (long i = (long)blockIdx.x * NT + threadIdx.x; i < L; i += (long)gridDim.x * NT) {
+    const double2 sy = field_get<T>(Wcur, i, L), y = field_get<T>(Wprev, i, L);
+    const double2 kk = make_double2(-k0n0 * (sy.y - y.y), k0n0 * (sy.x - y.x));
+    double2 a = ACC[i];
+    a.x += hb * kk.x; a.y += hb * kk.y;
+    ACC[i] = a;
+    double2 nxt = a;
+    if (!last) { const double2 w0 = W0[i]; nxt = make_double2(w0.x + hc * kk.x, w0.y + hc * kk.y); }
+    field_put<T>(Wcur, i, L, nxt);
   }
 }
 

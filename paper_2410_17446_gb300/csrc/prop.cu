@@ -19,6 +19,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdlib>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -59,6 +60,29 @@ template <typename T> constexpr int cols_per_cta() { return sizeof(T) == 4 ? 4 :
 template <int N> constexpr int rows_nr() { return N <= 128 ? 16 : (N == 256 ? 8 : (N <= 512 ? 4 : 2)); }
 constexpr int clamp_nt(int t) { return t < 64 ? 64 : (t > 256 ? 256 : t); }
 template <int N> constexpr int rows_nt() { return clamp_nt(rows_nr<N>() * N / 16); }
+// the warp row transform (N = 512, 1024): four rows a CTA, one warp per row
+constexpr int WROWS = 4;
+constexpr bool warp_n_c(int n) { return n == 512 || n == 1024; }
+
+// ---------------------------------------------------------------------------
+// FFT pass variants per (size, precision), process-wide: the row pass by the
+// block-wide Stockham or by warps, the column pass by TMA tiles, plain loads or
+// warps.  prop_set_fft_plan installs a choice (the autotuner's); every launch
+// reads it.
+// ---------------------------------------------------------------------------
+constexpr int NSIZES = 9;
+int size_index(int n) {
+  switch (n) {
+    case 16: return 0; case 32: return 1; case 64: return 2; case 128: return 3; case 256: return 4;
+    case 384: return 5; case 512: return 6; case 768: return 7; case 1024: return 8; default: return -1;
+  }
+}
+std::atomic<int> g_plan_rows[2][NSIZES];
+std::atomic<int> g_plan_cols[2][NSIZES];
+bool warp_n(int n) { return n == 512 || n == 1024; }
+int plan_rows(int prec, int n) { const int i = size_index(n); return i < 0 ? PROP_ROWS_BLOCK : g_plan_rows[prec][i].load(std::memory_order_relaxed); }
+int plan_cols(int prec, int n) { const int i = size_index(n); return i < 0 ? PROP_COLS_TMA : g_plan_cols[prec][i].load(std::memory_order_relaxed); }
+template <typename T> constexpr int prec_of() { return sizeof(T) == 4 ? PROP_FP32 : PROP_FP64; }
 template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * cols_per_cta<T>() / 16); }
 constexpr int NT_VEC = 256;
 constexpr int EPT_GS = 4;     // points per thread of the update sweep
@@ -70,7 +94,8 @@ constexpr int ERR_SLOT = 3 * (MMAX + 2) - 1;   // int in the counts area: the as
 
 struct Layout {
   size_t V, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog, dsum,
-      rk, anorm, part, psi, Tmp2, poles, act0, act1, netout, stage, iters, cycles, resid, flags, ulist, end;
+      rk, anorm, part, psi, Tmp2, poles, act0, act1, netout, stage, iters, cycles, resid, flags, ulist, rkw0, rkacc,
+      rkstart, end;
 };
 
 struct Group {
@@ -92,7 +117,7 @@ struct Group {
 }  // namespace
 
 struct prop {
-  int nbeams, P, C, prec, m, max_restarts, precond;
+  int nbeams, P, C, prec, m, max_restarts, precond, form, substeps;
   double tol, k0, n0, dz;
   std::vector<cplx> poles, res;
   cplx r0;
@@ -123,7 +148,7 @@ namespace {
 size_t elem_size(int prec) { return prec == PROP_FP64 ? sizeof(double) : sizeof(float); }
 
 // Carve one group's buffers starting at `base`; returns the end offset.
-size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
+size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess, int form) {
   const size_t es = elem_size(prec), cs = 2 * es;
   const size_t nb = G.beams.size(), nsys = nb * P, npts = G.npts;
   Layout& L = G.off;
@@ -163,6 +188,10 @@ size_t carve(Group& G, size_t base, int P, int C, int m, int prec, int guess) {
   L.resid = take(nsys * sizeof(double));
   L.flags = take(nsys * sizeof(int));
   L.ulist = take(nsys * sizeof(int));
+  // pseudo-differential form: the Runge-Kutta substep start, accumulator and step start
+  L.rkw0 = take(form ? nb * C * npts * 16 : 0);
+  L.rkacc = take(form ? nb * C * npts * 16 : 0);
+  L.rkstart = take(form ? nb * C * npts * 16 : 0);
   L.end = o;
   return o;
 }
@@ -251,9 +280,21 @@ template <typename T, int N, typename SRC>
 cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst, int mask, double* nacc,
                        int units, cudaStream_t st) {
   using C = typename Cx<T>::t;
+  if constexpr (warp_n_c(N)) {
+    if (plan_rows(prec_of<T>(), N) == PROP_ROWS_WARP) {
+      const size_t sm = smem_elems<N, WROWS, false>() * sizeof(C);
+      auto k = k_rows_fwd<T, N, WROWS, 32 * WROWS, SRC, true>;
+      static bool attr = false;
+      cudaError_t e = set_smem_once(k, sm, attr);
+      if (e != cudaSuccess) return e;
+      dim3 grid(g.ny / WROWS, units * g.ncomp);
+      k<<<grid, 32 * WROWS, sm, st>>>(g, src, dst, mask, nacc);
+      return cudaGetLastError();
+    }
+  }
   constexpr int NR = rows_nr<N>(), NT = rows_nt<N>();
   const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
-  auto k = k_rows_fwd<T, N, NR, NT, SRC>;
+  auto k = k_rows_fwd<T, N, NR, NT, SRC, false>;
   static bool attr = false;
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
@@ -266,10 +307,22 @@ template <typename T, int N>
 cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask,
                        int skip, EpiArgs ep, int units, cudaStream_t st) {
   using C = typename Cx<T>::t;
+  const bool arn = ep.mode == EPI_ARNOLDI;
+  if constexpr (warp_n_c(N)) {
+    if (plan_rows(prec_of<T>(), N) == PROP_ROWS_WARP) {
+      const size_t sm = smem_elems<N, WROWS, false>() * sizeof(C);
+      auto k = arn ? k_rows_inv<T, N, WROWS, 32 * WROWS, true, true> : k_rows_inv<T, N, WROWS, 32 * WROWS, false, true>;
+      static bool attr[2] = {false, false};
+      cudaError_t e = set_smem_once(k, sm, attr[arn ? 1 : 0]);
+      if (e != cudaSuccess) return e;
+      dim3 grid(g.ny / WROWS, units * g.ncomp);
+      k<<<grid, 32 * WROWS, sm, st>>>(g, src, dst, mask, skip, ep);
+      return cudaGetLastError();
+    }
+  }
   constexpr int NR = rows_nr<N>(), NT = rows_nt<N>();
   const size_t sm = smem_elems<N, NR, false>() * sizeof(C);
-  const bool arn = ep.mode == EPI_ARNOLDI;
-  auto k = arn ? k_rows_inv<T, N, NR, NT, true> : k_rows_inv<T, N, NR, NT, false>;
+  auto k = arn ? k_rows_inv<T, N, NR, NT, true, false> : k_rows_inv<T, N, NR, NT, false, false>;
   static bool attr[2] = {false, false};
   cudaError_t e = set_smem_once(k, sm, attr[arn ? 1 : 0]);
   if (e != cudaSuccess) return e;
@@ -286,7 +339,23 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
                     int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
                     Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy, ColMaps cm) {
   using C = typename Cx<T>::t;
-  if (cm.src && cm.dst && (mul != MUL_TABLE || cm.tab) && (!DY || (cm.dy && mul != MUL_TABLE))) {
+  const int cplan = plan_cols(prec_of<T>(), NY);
+  if constexpr (warp_n_c(NY) && !DY) {
+    // column pass by warps: every mode but the multiplier table and the spectrum output
+    if (cplan == PROP_COLS_WARP && mul != MUL_TABLE && !spec.base && g.nx % CW_NV == 0) {
+      const size_t sm = (size_t)cw_elems<NY>() * sizeof(C);
+      auto k = k_cols_warp<T, NY>;
+      static bool attr = false;
+      cudaError_t e = set_smem_once(k, sm, attr);
+      if (e != cudaSuccess) return e;
+      dim3 grid(g.nx / CW_NV, units * g.ncomp);
+      k<<<grid, 32 * CW_NV, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale);
+      return cudaGetLastError();
+    }
+  }
+  // the TMA pass reports failed copies through g.err: it runs only with an error word
+  if (cplan != PROP_COLS_PLAIN && g.err && cm.src && cm.dst && (mul != MUL_TABLE || cm.tab) &&
+      (!DY || (cm.dy && mul != MUL_TABLE))) {
     constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
     const size_t sm = ((size_t)NY * NV * (mul == MUL_TABLE || DY ? 2 : 1) + NY) * sizeof(C) + 128;   // + twiddles, slack
     auto k = k_cols_tma<T, NY, NV, NT, DY>;
@@ -936,6 +1005,8 @@ int validate_opts(const prop_opts* o) {
   if (!(o->tol > 0.0)) return PROP_E_ARG;
   if (o->guess != PROP_GUESS_ZERO && o->guess != PROP_GUESS_LEARNED) return PROP_E_ARG;
   if (o->precond != PROP_PRECOND_FREESPACE && o->precond != PROP_PRECOND_MEAN) return PROP_E_ARG;
+  if (o->form != PROP_FORM_EXPONENTIAL && o->form != PROP_FORM_PSEUDODIFF) return PROP_E_ARG;
+  if (o->substeps < 0 || o->substeps > 100000) return PROP_E_ARG;
   return PROP_OK;
 }
 
@@ -967,10 +1038,10 @@ int build_groups(int nbeams, const prop_grid* grids, std::vector<Group>& groups,
   return PROP_OK;
 }
 
-size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, int guess, size_t* counts_off,
-                    size_t* net_off) {
+size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, int guess, int form,
+                    size_t* counts_off, size_t* net_off) {
   size_t o = 0;
-  for (Group& G : groups) o = carve(G, o, P, C, m, prec, guess);
+  for (Group& G : groups) o = carve(G, o, P, C, m, prec, guess, form);
   *net_off = align_up(o);
   *counts_off = align_up(*net_off + NET_W_BYTES + NET_B_BYTES);
   return *counts_off + align_up(3 * (MMAX + 2) * sizeof(int));
@@ -995,6 +1066,8 @@ int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision) {
   o->tol = precision == PROP_FP64 ? 1e-12 : 1e-7;
   o->guess = PROP_GUESS_ZERO;
   o->precond = PROP_PRECOND_MEAN;
+  o->form = PROP_FORM_EXPONENTIAL;
+  o->substeps = 0;
   return PROP_OK;
 }
 
@@ -1007,7 +1080,8 @@ int prop_workspace_size(int32_t nbeams, const prop_grid* grids, int32_t npoles, 
   rc = build_groups(nbeams, grids, groups, bg, bs);
   if (rc) return rc;
   size_t co, no;
-  *bytes = total_layout(groups, npoles, opts->ncomp, opts->restart, opts->precision, opts->guess, &co, &no);
+  *bytes = total_layout(groups, npoles, opts->ncomp, opts->restart, opts->precision, opts->guess, opts->form, &co,
+                        &no);
   return PROP_OK;
 }
 
@@ -1024,7 +1098,8 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   prop* h = new (std::nothrow) prop();
   if (!h) return PROP_E_ARG;
   h->nbeams = nbeams; h->P = npoles; h->C = opts->ncomp; h->prec = opts->precision; h->m = opts->restart;
-  h->max_restarts = opts->max_restarts; h->tol = opts->tol; h->precond = opts->precond; h->k0 = k0; h->n0 = n0; h->dz = dz;
+  h->max_restarts = opts->max_restarts; h->tol = opts->tol; h->precond = opts->precond;
+  h->form = opts->form; h->substeps = opts->substeps; h->k0 = k0; h->n0 = n0; h->dz = dz;
   h->poles.resize(npoles); h->res.resize(npoles);
   for (int k = 0; k < npoles; ++k) {
     h->poles[k] = cplx(poles[2 * k], poles[2 * k + 1]);
@@ -1036,7 +1111,19 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   if (rc) { delete h; return rc; }
   h->guess = opts->guess;
   h->net_layers = 0;
-  const size_t need = total_layout(h->groups, h->P, h->C, h->m, h->prec, h->guess, &h->counts_off, &h->net_off);
+  if (h->form == PROP_FORM_PSEUDODIFF && h->substeps == 0) {
+    // the fewest RK4 steps with h |lambda| <= 2.5, |lambda| <= k0 n0 (1 + sqrt(1.5 + |zeta_min|))
+    // for lambda = i k0 n0 (S(zeta) - 1) over the grids' spectra (medium terms within 0.5)
+    double lam = 0.0;
+    for (int b = 0; b < nbeams; ++b) {
+      const double kx = M_PI / grids[b].dx, ky = M_PI / grids[b].dy, k0n0 = k0 * n0;
+      const double zmin = (kx * kx + ky * ky) / (k0n0 * k0n0);
+      lam = std::max(lam, k0n0 * (1.0 + std::sqrt(1.5 + zmin)));
+    }
+    h->substeps = std::max(1, (int)std::ceil(dz * lam / 2.5));
+  }
+  const size_t need = total_layout(h->groups, h->P, h->C, h->m, h->prec, h->guess, h->form, &h->counts_off,
+                                   &h->net_off);
   if (ws_bytes < need) { delete h; return PROP_E_WORKSPACE; }
   h->ws = (char*)d_workspace; h->ws_bytes = ws_bytes;
   h->stream = (cudaStream_t)stream;
@@ -1133,6 +1220,48 @@ int prop_get_field(prop* h, int32_t beam, void* w) {
   return PROP_OK;
 }
 
+}  // extern "C"
+
+// The pseudo-differential form (Sec. 3.2): `substeps` classical Runge-Kutta steps
+// of dw/dz = i k0 n0 (S(Z) - I) w per dz.  Each stage is one step_group with the
+// square root's table (field := S(Z) y, the other field buffer keeps y),
+// followed by k_rk_stage.  On an error the field returns to the step's start.
+template <typename T> static int rk4_group(prop* h, Group& G) {
+  const long L = (long)G.beams.size() * h->C * G.npts;
+  double2* W0 = (double2*)(h->ws + G.off.rkw0);
+  double2* ACC = (double2*)(h->ws + G.off.rkacc);
+  double2* START = (double2*)(h->ws + G.off.rkstart);
+  const int blocks = (int)std::min<long>(2048, (L + 255) / 256);
+  const double hs = h->dz / (double)h->substeps, k0n0 = h->k0 * h->n0;
+  const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, c[4] = {0.0, 0.5, 0.5, 1.0};
+  auto cur = [&]() { return (double2*)(h->ws + (G.cur == 0 ? G.off.W64a : G.off.W64b)); };
+  auto prev = [&]() { return (double2*)(h->ws + (G.cur == 0 ? G.off.W64b : G.off.W64a)); };
+  { Prof p_(h, K_FIELD_IO, 48.0 * L);
+    k_rk_copy<T, 256><<<blocks, 256, 0, h->stream>>>(cur(), START, nullptr, L); }
+  CK(cudaGetLastError());
+  for (int sub = 0; sub < h->substeps; ++sub) {
+    { Prof p_(h, K_FIELD_IO, 48.0 * L);
+      k_rk_copy<T, 256><<<blocks, 256, 0, h->stream>>>(cur(), W0, ACC, L); }
+    CK(cudaGetLastError());
+    for (int s = 0; s < 4; ++s) {
+      const int rc = step_group<T>(h, G);
+      if (rc) {
+        k_rk_restore<T, 256><<<blocks, 256, 0, h->stream>>>(cur(), START, L);
+        G.carry = false;
+        return rc;
+      }
+      { Prof p_(h, K_FIELD_IO, 96.0 * L);
+        k_rk_stage<T, 256><<<blocks, 256, 0, h->stream>>>(cur(), prev(), W0, ACC, L, hs * b[s],
+                                                          s < 3 ? hs * c[s + 1] : 0.0, k0n0, s == 3 ? 1 : 0); }
+      CK(cudaGetLastError());
+      G.carry = false;   // the field was rewritten after the row DFT the step kept
+    }
+  }
+  return PROP_OK;
+}
+
+extern "C" {
+
 int prop_get_e3(prop* h, int32_t beam, void* out) {
   if (!h || !out || beam < 0 || beam >= h->nbeams) return PROP_E_ARG;
   if (h->C != 2) return PROP_E_UNSUPPORTED;
@@ -1149,10 +1278,18 @@ int prop_get_e3(prop* h, int32_t beam, void* out) {
   return PROP_OK;
 }
 
+int prop_get_substeps(prop* h, int32_t* substeps) {
+  if (!h || !substeps) return PROP_E_ARG;
+  *substeps = h->form == PROP_FORM_PSEUDODIFF ? h->substeps : 0;
+  return PROP_OK;
+}
+
 int prop_step(prop* h) {
   if (!h) return PROP_E_ARG;
   for (Group& G : h->groups) {
-    const int rc = h->prec == PROP_FP64 ? step_group<double>(h, G) : step_group<float>(h, G);
+    int rc;
+    if (h->form == PROP_FORM_PSEUDODIFF) rc = h->prec == PROP_FP64 ? rk4_group<double>(h, G) : rk4_group<float>(h, G);
+    else rc = h->prec == PROP_FP64 ? step_group<double>(h, G) : step_group<float>(h, G);
     if (rc) { h->last_status = rc; return rc; }
   }
   h->steps += 1;
@@ -1344,6 +1481,134 @@ int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t 
   if (precision == PROP_FP64) return fft2_impl<double>(nx, ny, batch, inverse, d_data, d_work, (cudaStream_t)stream);
   if (precision == PROP_FP32) return fft2_impl<float>(nx, ny, batch, inverse, d_data, d_work, (cudaStream_t)stream);
   return PROP_E_ARG;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// FFT plan selection (prop_get/set_fft_plan, prop_fft_autotune)
+// ---------------------------------------------------------------------------
+static bool plan_valid(int n, int prec, const prop_fft_plan& p) {
+  if (p.rows != PROP_ROWS_BLOCK && p.rows != PROP_ROWS_WARP) return false;
+  if (p.cols != PROP_COLS_TMA && p.cols != PROP_COLS_PLAIN && p.cols != PROP_COLS_WARP) return false;
+  if (!warp_n(n) && (p.rows == PROP_ROWS_WARP || p.cols == PROP_COLS_WARP)) return false;
+  return prec == PROP_FP32 || prec == PROP_FP64;
+}
+
+// Times (CUDA events, best of reps) of one row round trip (forward rows, inverse
+// rows) and of one column pass (forward, scale, inverse) per variant, on `batch`
+// n x n arrays in the work buffer.
+template <typename T>
+static int autotune_impl(int n, int batch, int reps, char* work, cudaStream_t st, float* ms) {
+  using C = typename Cx<T>::t;
+  const size_t data_b = align_up((size_t)batch * n * n * sizeof(C));
+  std::vector<T> tw;
+  twiddles<T>(n, tw);
+  C* d = (C*)work;
+  int* err = (int*)(work + data_b + align_up((size_t)n * sizeof(C)));   // the TMA pass's error word
+  CK(cudaMemsetAsync(d, 0, (size_t)batch * n * n * sizeof(C), st));
+  CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  CK(cudaMemcpyAsync(work + data_b, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  GV<T> g;
+  std::memset(&g, 0, sizeof(g));
+  g.nx = n; g.ny = n; g.ncomp = 1; g.P = 1; g.m = 1; g.nb = batch; g.nsys = batch; g.npts = (long)n * n;
+  g.twx = (const C*)(work + data_b); g.twy = g.twx;
+  g.err = err;
+  const long F = g.npts;
+  const T scale = (T)(1.0 / (double)F);
+  CUtensorMap tm;
+  const bool tma = make_col_map(&tm, d, n, n, batch, (int)sizeof(C), cols_per_cta<T>());
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return PROP_E_CUDA;
+  const int prec = prec_of<T>(), si = size_index(n);
+  const int rows_saved = g_plan_rows[prec][si].load(), cols_saved = g_plan_cols[prec][si].load();
+  int rc = PROP_OK;
+  auto time_it = [&](auto&& launch) -> float {
+    float best = -1.f;
+    for (int r = 0; r < reps + 1 && rc == PROP_OK; ++r) {   // the first run warms up
+      if (cudaEventRecord(a, st) != cudaSuccess) { rc = PROP_E_CUDA; break; }
+      if (launch() != cudaSuccess) { rc = PROP_E_CUDA; break; }
+      if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) { rc = PROP_E_CUDA; break; }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, a, b);
+      if (r > 0 && (best < 0.f || t < best)) best = t;
+    }
+    return best;
+  };
+  for (int v = 0; v < 5; ++v) ms[v] = -1.f;
+  for (int rv = 0; rv < 2 && rc == PROP_OK; ++rv) {
+    if (rv == PROP_ROWS_WARP && !warp_n(n)) continue;
+    g_plan_rows[prec][si].store(rv);
+    ms[rv] = time_it([&]() {
+      cudaError_t e = rows_fwd<T, C>(g, buf(d, F), buf(d, F), -1, nullptr, batch, st);
+      return e != cudaSuccess ? e : rows_inv<T>(g, buf(d, F), buf(d, F), -1, 0, epi(EPI_STORE), batch, st);
+    });
+  }
+  for (int cv = 0; cv < 3 && rc == PROP_OK; ++cv) {
+    if (cv == PROP_COLS_WARP && !warp_n(n)) continue;
+    if (cv == PROP_COLS_TMA && !tma) continue;
+    g_plan_cols[prec][si].store(cv);
+    const ColMaps cm = cv == PROP_COLS_TMA ? ColMaps{&tm, &tm, nullptr, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
+    ms[2 + cv] = time_it([&]() {
+      return cols<T>(g, buf(d, F), buf(d, F), -1, 1, MUL_SCALE, 1, 0, -1, scale, batch, st,
+                     Buf<C>{nullptr, 0, 1}, Buf<C>{nullptr, 0, 1}, cm);
+    });
+  }
+  g_plan_rows[prec][si].store(rows_saved);
+  g_plan_cols[prec][si].store(cols_saved);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc == PROP_OK) {
+    int e = 0;
+    if (cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PROP_E_CUDA;
+    rc = async_status(e);
+  }
+  return rc;
+}
+
+extern "C" {
+
+int prop_get_fft_plan(int32_t n, int32_t precision, prop_fft_plan* out) {
+  if (!out || (precision != PROP_FP32 && precision != PROP_FP64)) return PROP_E_ARG;
+  if (size_index(n) < 0) return PROP_E_UNSUPPORTED;
+  out->rows = plan_rows(precision, n);
+  out->cols = plan_cols(precision, n);
+  return PROP_OK;
+}
+
+int prop_set_fft_plan(int32_t n, int32_t precision, const prop_fft_plan* plan) {
+  if (!plan) return PROP_E_ARG;
+  if (size_index(n) < 0) return PROP_E_UNSUPPORTED;
+  if (!plan_valid(n, precision, *plan)) return PROP_E_UNSUPPORTED;
+  g_plan_rows[precision][size_index(n)].store(plan->rows);
+  g_plan_cols[precision][size_index(n)].store(plan->cols);
+  return PROP_OK;
+}
+
+int prop_fft_autotune_workspace_size(int32_t n, int32_t precision, int32_t batch, size_t* bytes) {
+  if (!bytes || batch < 1 || (precision != PROP_FP32 && precision != PROP_FP64)) return PROP_E_ARG;
+  if (size_index(n) < 0) return PROP_E_UNSUPPORTED;
+  const size_t cs = 2 * elem_size(precision);
+  *bytes = align_up((size_t)batch * n * n * cs) + align_up((size_t)n * cs) + align_up(sizeof(int));
+  return PROP_OK;
+}
+
+int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps, void* d_work, size_t work_bytes,
+                      void* stream, prop_fft_plan* best, float* ms) {
+  size_t need;
+  int rc = prop_fft_autotune_workspace_size(n, precision, batch, &need);
+  if (rc) return rc;
+  if (!d_work || !best || !ms || reps < 1 || ((uintptr_t)d_work % ALIGN) != 0) return PROP_E_ARG;
+  if (work_bytes < need) return PROP_E_WORKSPACE;
+  rc = precision == PROP_FP64 ? autotune_impl<double>(n, batch, reps, (char*)d_work, (cudaStream_t)stream, ms)
+                              : autotune_impl<float>(n, batch, reps, (char*)d_work, (cudaStream_t)stream, ms);
+  if (rc) return rc;
+  best->rows = (ms[1] >= 0.f && ms[1] < ms[0]) ? PROP_ROWS_WARP : PROP_ROWS_BLOCK;
+  int bc = -1;
+  for (int cv = 0; cv < 3; ++cv)
+    if (ms[2 + cv] >= 0.f && (bc < 0 || ms[2 + cv] < ms[2 + bc])) bc = cv;
+  best->cols = bc < 0 ? PROP_COLS_PLAIN : bc;
+  return PROP_OK;
 }
 
 }  // extern "C"

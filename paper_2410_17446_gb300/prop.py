@@ -31,11 +31,18 @@ class prop_grid(ct.Structure):
 class prop_opts(ct.Structure):
     _fields_ = [("ncomp", ct.c_int32), ("precision", ct.c_int32), ("restart", ct.c_int32),
                 ("max_restarts", ct.c_int32), ("tol", ct.c_double), ("guess", ct.c_int32),
-                ("precond", ct.c_int32)]
+                ("precond", ct.c_int32), ("form", ct.c_int32), ("substeps", ct.c_int32)]
 
 
 PROP_GUESS_ZERO, PROP_GUESS_LEARNED = 0, 1
+PROP_ROWS_BLOCK, PROP_ROWS_WARP = 0, 1
+PROP_COLS_TMA, PROP_COLS_PLAIN, PROP_COLS_WARP = 0, 1, 2
+
+
+class prop_fft_plan(ct.Structure):
+    _fields_ = [("rows", ct.c_int32), ("cols", ct.c_int32)]
 PROP_PRECOND_FREESPACE, PROP_PRECOND_MEAN = 0, 1
+PROP_FORM_EXPONENTIAL, PROP_FORM_PSEUDODIFF = 0, 1
 PROP_GUESS_CHANNELS = 16
 
 
@@ -70,6 +77,12 @@ _SIGS = {
     "prop_set_field": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "prop_get_field": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "prop_step": (ct.c_int, [ct.c_void_p]),
+    "prop_get_substeps": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
+    "prop_get_fft_plan": (ct.c_int, [ct.c_int32, ct.c_int32, ct.POINTER(prop_fft_plan)]),
+    "prop_set_fft_plan": (ct.c_int, [ct.c_int32, ct.c_int32, ct.POINTER(prop_fft_plan)]),
+    "prop_fft_autotune_workspace_size": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_size_t)]),
+    "prop_fft_autotune": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_size_t,
+                                     ct.c_void_p, ct.POINTER(prop_fft_plan), ct.POINTER(ct.c_float)]),
     "prop_get_e3": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "prop_run": (ct.c_int, [ct.c_void_p, ct.c_int32, MEDIUM_FN, ct.c_void_p]),
     "prop_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(prop_stats)]),
@@ -167,6 +180,32 @@ def prop_fft2(nx, ny, batch, precision, inverse, d_data, d_work, work_bytes, str
                           stream), "prop_fft2")
 
 
+def prop_get_fft_plan(n: int, precision: int) -> prop_fft_plan:
+    p = prop_fft_plan()
+    check(lib().prop_get_fft_plan(n, precision, ct.byref(p)), "prop_get_fft_plan")
+    return p
+
+
+def prop_set_fft_plan(n: int, precision: int, rows: int, cols: int) -> None:
+    p = prop_fft_plan(rows, cols)
+    check(lib().prop_set_fft_plan(n, precision, ct.byref(p)), "prop_set_fft_plan")
+
+
+def prop_fft_autotune_workspace_size(n: int, precision: int, batch: int) -> int:
+    b = ct.c_size_t()
+    check(lib().prop_fft_autotune_workspace_size(n, precision, batch, ct.byref(b)), "prop_fft_autotune_workspace_size")
+    return b.value
+
+
+def prop_fft_autotune(n, precision, batch, reps, d_work, work_bytes, stream=0):
+    """Returns (best plan, times in ms: rows block, rows warp, cols TMA, cols plain, cols warp)."""
+    best = prop_fft_plan()
+    ms = (ct.c_float * 5)()
+    check(lib().prop_fft_autotune(n, precision, batch, reps, _dptr(d_work), work_bytes, stream, ct.byref(best), ms),
+          "prop_fft_autotune")
+    return best, list(ms)
+
+
 def prop_fft2_noalloc(nx, ny, batch, precision, inverse, d_data, stream=0) -> None:
     """prop_fft2 without a caller workspace, for callers that cannot allocate device memory."""
     check(lib().prop_fft2_noalloc(nx, ny, batch, precision, inverse, _dptr(d_data), stream), "prop_fft2_noalloc")
@@ -178,7 +217,7 @@ class Propagator:
     def __init__(self, grids, k0: float, n0: float, dz: float, poles, residues, r0,
                  ncomp: int = 1, precision: int = PROP_FP32, restart: int = 20, max_restarts: Optional[int] = None,
                  tol: Optional[float] = None, device: str = "cuda", stream=None, guess: int = PROP_GUESS_ZERO,
-                 precond: Optional[int] = None):
+                 precond: Optional[int] = None, form: int = PROP_FORM_EXPONENTIAL, substeps: int = 0):
         import torch
         self.torch = torch
         self.grids = [prop_grid(int(g[0]), int(g[1]), float(g[2]), float(g[3])) if not isinstance(g, prop_grid)
@@ -194,6 +233,8 @@ class Propagator:
         self.opts.guess = guess
         if precond is not None:
             self.opts.precond = precond
+        self.opts.form = form
+        self.opts.substeps = substeps
         poles = np.asarray(poles, np.complex128)
         residues = np.asarray(residues, np.complex128)
         self.npoles = poles.size
@@ -243,6 +284,13 @@ class Propagator:
             out = np.empty((g.ny, g.nx), np.complex128)
         check(lib().prop_get_e3(self.h, beam, _dptr(out)), "prop_get_e3")
         return out
+
+    @property
+    def substeps(self) -> int:
+        """Runge-Kutta steps per dz of a pseudo-differential handle (0 for the exponential form)."""
+        v = ct.c_int32()
+        check(lib().prop_get_substeps(self.h, ct.byref(v)), "prop_get_substeps")
+        return v.value
 
     def step(self) -> None:
         check(lib().prop_step(self.h), "prop_step")

@@ -243,6 +243,78 @@ def multiwave_scalar_64(nsteps: int = 4) -> Workload:
                     [beam], "64x64 scalar, dz = 5 lambda, 28 poles")
 
 
+def axis_angle_matrix(axis, angle: float) -> np.ndarray:
+    """Rotation by `angle` about the unit vector along `axis` (Rodrigues' formula):
+    R = cos(a) I + sin(a) [u]_x + (1 - cos(a)) u u^T."""
+    u = np.asarray(axis, float)
+    u = u / np.linalg.norm(u)
+    K = np.array([[0.0, -u[2], u[1]], [u[2], 0.0, -u[0]], [-u[1], u[0], 0.0]])
+    return math.cos(angle) * np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * np.outer(u, u)
+
+
+SINEPROD_AXIS = (0.258, 0.312, 0.914)   # Sec. 5.3: rotation axis (normalised here) and angle
+SINEPROD_ANGLE = 0.128
+SINEPROD_N0, SINEPROD_DN = 1.2, 0.025
+
+
+def rotated_sine_product_n2(grid: Grid, q: float, z: float, border: int, sigma_max: float,
+                            n0: float = SINEPROD_N0, dn: float = SINEPROD_DN) -> np.ndarray:
+    """n^2 of Eq. eq_sineprod at plane z: n = n0 + dn sin(ks x~) sin(ks y~) sin(ks z~),
+    ks = k0 n0 / (sqrt(3) q), (x~, y~, z~) = R (x, y, z) with R the axis-angle
+    rotation of Sec. 5.3; plus i sigma of the absorbing border."""
+    X, Y = grid.mesh()
+    R = axis_angle_matrix(SINEPROD_AXIS, SINEPROD_ANGLE)
+    ks = K0 * n0 / (math.sqrt(3.0) * q)
+    xt = R[0, 0] * X + R[0, 1] * Y + R[0, 2] * z
+    yt = R[1, 0] * X + R[1, 1] * Y + R[1, 2] * z
+    zt = R[2, 0] * X + R[2, 1] * Y + R[2, 2] * z
+    n = n0 + dn * np.sin(ks * xt) * np.sin(ks * yt) * np.sin(ks * zt)
+    return (n * n).astype(np.complex128) + 1j * absorbing_sigma(grid, border, sigma_max)
+
+
+def sineprod_helmholtz(q: float, nsteps: Optional[int] = None, n: Optional[int] = None,
+                       range_lambda: float = 240.0) -> Workload:
+    """Sec. 5.3: a collimated Gaussian beam (1/e amplitude width 25 lambda, read as
+    the diameter: exp(-r^2/w^2), w = 12.5 lambda) through the rotated sine product
+    with n0 = 1.2, dn = 0.025, q in {0.5, 1, 2}; dz = a quarter of the index
+    field's wavelength 2 pi/ks; 240 lambda of range.  The paper's 481^2 and
+    961^2 grids over 120 lambda (dx = lambda/4, lambda/8) with 60- and
+    120-point PMLs become 512^2 and 1024^2 at the same dx (128 lambda) with
+    64- and 128-cell absorbing borders (16 lambda).  The medium is sampled at
+    the step midpoints.  `n` shrinks the grid at the same dx (tests)."""
+    fine = q < 0.75
+    dx = LAMBDA / 8 if fine else LAMBDA / 4
+    N = n or (1024 if fine else 512)
+    g = Grid(N, N, dx, dx)
+    width = max(8, N // 8)
+    ks = K0 * SINEPROD_N0 / (math.sqrt(3.0) * q)
+    dz = (2 * math.pi / ks) / 4
+    steps = nsteps if nsteps is not None else int(round(range_lambda / dz))
+
+    # sin(ks (R_i0 x + R_i1 y + R_i2 z)) = sin(A_i) cos(c_i) + cos(A_i) sin(c_i): the
+    # z-independent parts A_i are evaluated once (the same n^2 as rotated_sine_product_n2)
+    X, Y = g.mesh()
+    R = axis_angle_matrix(SINEPROD_AXIS, SINEPROD_ANGLE)
+    A = [ks * (R[i, 0] * X + R[i, 1] * Y) for i in range(3)]
+    SA, CA = [np.sin(a) for a in A], [np.cos(a) for a in A]
+    sig = absorbing_sigma(g, width, 0.2)
+
+    def med(s):
+        z = (s + 0.5) * dz
+        f = None
+        for i in range(3):
+            c = ks * R[i, 2] * z
+            t = SA[i] * math.cos(c) + CA[i] * math.sin(c)
+            f = t if f is None else f * t
+        nn = SINEPROD_N0 + SINEPROD_DN * f
+        return (nn * nn) + 1j * sig
+
+    beam = Beam(g, gaussian_beam(g, 12.5 * LAMBDA)[None], med, lambda s: True, width, 0.2)
+    tag = {0.5: "05", 1.0: "1", 2.0: "2"}.get(float(q), str(q))
+    return Workload(f"sineprod_q{tag}", K0, SINEPROD_N0, dz, steps, 16, 1, "fp32", 20, 1e-7, [beam],
+                    f"Sec. 5.3 rotated sine product, q = {q}, {N}^2, dx = {dx:g}, dz = {dz:.4f}")
+
+
 def small_scalar(n: int = 16, dx: float = LAMBDA / 4, border: int = 3, eps: float = 0.1,
                  seed: int = 0, waist: float = 1.0) -> Workload:
     """Tiny random-medium scalar case (dense-LU sized) for unit tests."""
@@ -276,4 +348,7 @@ WORKLOADS = {
     "vector_random_512": vector_random_512,
     "uneven_batch": uneven_batch,
     "multiwave_scalar_64": multiwave_scalar_64,
+    "sineprod_q2": lambda nsteps=None, n=None: sineprod_helmholtz(2.0, nsteps, n),
+    "sineprod_q1": lambda nsteps=None, n=None: sineprod_helmholtz(1.0, nsteps, n),
+    "sineprod_q05": lambda nsteps=None, n=None: sineprod_helmholtz(0.5, nsteps, n),
 }

@@ -45,3 +45,71 @@ def test_fft2_empty_batch_and_bad_size(P):
     P.prop_fft2(64, 64, 0, P.PROP_FP32, 0, d, work, work.numel(), 0)
     with pytest.raises(P.PropError):
         P.prop_fft2(100, 64, 1, P.PROP_FP32, 0, d, work, work.numel(), 0)
+
+
+PLANS = [("block", "plain"), ("block", "warp"), ("warp", "plain"), ("warp", "warp"), ("warp", "tma")]
+
+
+@pytest.fixture
+def restore_plans(P):
+    saved = {(n, p): P.prop_get_fft_plan(n, p) for n in (512, 1024) for p in (P.PROP_FP32, P.PROP_FP64)}
+    yield
+    for (n, p), pl in saved.items():
+        P.prop_set_fft_plan(n, p, pl.rows, pl.cols)
+
+
+@pytest.mark.parametrize("rows,cols", PLANS)
+@pytest.mark.parametrize("nx,ny", [(1024, 1024), (512, 1024), (1024, 512), (512, 512)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_fft2_every_plan(P, restore_plans, rows, cols, nx, ny, prec):
+    """The warp row and column transforms (N = 512, 1024) against numpy.fft, in
+    every combination with the block-wide ones (prop_fft2 has no tensor maps, so
+    'tma' there means the plain-load column pass)."""
+    import torch
+    p = P.PROP_FP32 if prec == "fp32" else P.PROP_FP64
+    R = {"block": P.PROP_ROWS_BLOCK, "warp": P.PROP_ROWS_WARP}[rows]
+    Cc = {"tma": P.PROP_COLS_TMA, "plain": P.PROP_COLS_PLAIN, "warp": P.PROP_COLS_WARP}[cols]
+    for n in {nx, ny}:
+        P.prop_set_fft_plan(n, p, R, Cc)
+    rng = np.random.default_rng(nx + 5 * ny)
+    x = rng.standard_normal((2, ny, nx)) + 1j * rng.standard_normal((2, ny, nx))
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
+    tol = 2e-6 if prec == "fp32" else 1e-13
+    wb = P.prop_fft2_workspace_size(nx, ny, p)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    d = torch.tensor(x, dtype=cdt, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    P.prop_fft2(nx, ny, 2, p, 0, d, work, wb, s)
+    ref = np.fft.fft2(x)
+    assert np.linalg.norm(d.cpu().numpy() - ref) / np.linalg.norm(ref) < tol
+    P.prop_fft2(nx, ny, 2, p, 1, d, work, wb, s)
+    assert np.linalg.norm(d.cpu().numpy() - x) / np.linalg.norm(x) < tol
+
+
+def test_plan_validation(P, restore_plans):
+    with pytest.raises(P.PropError) as e:
+        P.prop_set_fft_plan(256, P.PROP_FP32, P.PROP_ROWS_WARP, P.PROP_COLS_TMA)
+    assert e.value.status == P.PROP_E_UNSUPPORTED
+    with pytest.raises(P.PropError):
+        P.prop_set_fft_plan(100, P.PROP_FP32, P.PROP_ROWS_BLOCK, P.PROP_COLS_TMA)
+    P.prop_set_fft_plan(1024, P.PROP_FP32, P.PROP_ROWS_WARP, P.PROP_COLS_WARP)
+    pl = P.prop_get_fft_plan(1024, P.PROP_FP32)
+    assert (pl.rows, pl.cols) == (P.PROP_ROWS_WARP, P.PROP_COLS_WARP)
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_autotuner_times_every_variant(P, restore_plans, n):
+    """prop_fft_autotune times each variant that exists for n, returns the
+    fastest of each pass and leaves the installed plan unchanged."""
+    from paper_2410_17446_gb300 import autotune
+    before = P.prop_get_fft_plan(n, P.PROP_FP32)
+    rec = autotune.tune(n, P.PROP_FP32, reps=2, min_bytes=32 << 20)
+    after = P.prop_get_fft_plan(n, P.PROP_FP32)
+    assert (before.rows, before.cols) == (after.rows, after.cols)
+    assert rec["rows_ms"]["block"] > 0 and rec["cols_ms"]["plain"] > 0 and rec["cols_ms"]["tma"] > 0
+    if n == 1024:
+        assert rec["rows_ms"]["warp"] > 0 and rec["cols_ms"]["warp"] > 0
+        times = {k: v for k, v in rec["cols_ms"].items() if v is not None}
+        assert rec["cols"] == min(times, key=times.get)
+    else:
+        assert rec["rows_ms"]["warp"] is None and rec["cols_ms"]["warp"] is None and rec["rows"] == "block"

@@ -44,16 +44,28 @@ def test_rotated_pade_table_fp64(P):
     assert pr.iterations().shape[-1] == 10
 
 
-@pytest.mark.parametrize("prec,bar", [("fp64", 1e-10), ("fp32", 1e-5)])
-def test_multiwave_steps_28_poles(P, prec, bar):
+@pytest.mark.parametrize("prec,unit", [("fp64", 1e-12), ("fp32", 1e-7)])
+def test_multiwave_steps_28_poles(P, prec, unit):
+    """The bar is derived from the table: each side's per-pole relative residual
+    (about `unit`) reaches the field amplified by |r_k| ||(Z - p_k)^-1|| <=
+    |r_k| / |Im p_k| (the scalar Z has its numerical range in Im >= 0), so two
+    steps of two independent solvers differ by at most about
+    4 unit sum_k |r_k|/|Im p_k|.  For this table that sum is ~1.3e4 (residues up
+    to ~1.5e3 that cancel), against ~6 for the 64^2 workload's 12-pole table:
+    5-wavelength steps cost FP32 about four digits."""
     from oracle import aaa_lawson as al
     from paper_2410_17446_gb300 import tables, workloads as wl
     W = wl.multiwave_scalar_64(2)
+    T = al.PoleTable.from_json(tables.load("multiwave_scalar_64"))
+    amp = float(np.sum(np.abs(T.residues) / np.abs(T.poles.imag)))
+    bar = 4 * unit * amp
     pr = gpu_propagator(W, "multiwave_scalar_64", P.PROP_FP64 if prec == "fp64" else P.PROP_FP32,
                         **({"tol": 1e-12} if prec == "fp64" else {}))
     got = gpu_run(pr, W, 2)[0]
-    ref = _oracle(W, al.PoleTable.from_json(tables.load("multiwave_scalar_64")), 2)
-    assert rel_l2(got, ref) < bar
+    ref = _oracle(W, T, 2)
+    err = rel_l2(got, ref)
+    print(f"{prec}: rel L2 {err:.2e}, derived bar {bar:.2e} (amplification {amp:.3e})")
+    assert err < bar
     assert pr.iterations().shape[-1] == 28
 
 

@@ -113,8 +113,8 @@ def test_homogeneous_aperture_full_size_100_steps(P):
     assert rel_l2(got, ref) < FP32_TOL
 
 
-@pytest.mark.parametrize("n", [256, 1024])
-def test_batched_scalar_solutions_satisfy_the_shifted_systems(P, n):
+@pytest.mark.parametrize("n,plan", [(256, None), (1024, None), (1024, ("warp", "warp")), (1024, ("block", "plain"))])
+def test_batched_scalar_solutions_satisfy_the_shifted_systems(P, n, plan):
     """Full size (and a reduced one): after a GPU step the oracle rebuilds every
     pole's solution x_k = (Z_fs - p_k)^-1 w + e_k from the GPU's correction e_k,
     checks its residual ||w - (Z - p_k) x_k|| with the oracle's own operator,
@@ -122,12 +122,19 @@ def test_batched_scalar_solutions_satisfy_the_shifted_systems(P, n):
     GPU's new field."""
     from oracle import operators as ops
     from paper_2410_17446_gb300 import workloads as wl
+    saved = P.prop_get_fft_plan(n, P.PROP_FP32)
+    if plan is not None:   # FFT pass variants (same arithmetic): warp rows and columns, or plain-load columns
+        P.prop_set_fft_plan(n, P.PROP_FP32, {"block": P.PROP_ROWS_BLOCK, "warp": P.PROP_ROWS_WARP}[plan[0]],
+                            {"plain": P.PROP_COLS_PLAIN, "warp": P.PROP_COLS_WARP}[plan[1]])
     W = wl.batched_scalar_1024(1, n=n)
     T = oracle_table("batched_scalar_1024")
-    pr = gpu_propagator(W, "batched_scalar_1024", P.PROP_FP32)
+    try:
+        pr = gpu_propagator(W, "batched_scalar_1024", P.PROP_FP32)
+        got = gpu_run(pr, W, 1)[0]
+    finally:
+        P.prop_set_fft_plan(n, P.PROP_FP32, saved.rows, saved.cols)
     b = W.beams[0]
     w0 = b.w0
-    got = gpu_run(pr, W, 1)[0]
     med = ops.Medium(b.medium(0), b.grid.dx, b.grid.dy, W.k0, W.n0, 1)
     out = T.r0 * w0
     worst = 0.0
