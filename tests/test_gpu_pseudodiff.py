@@ -60,10 +60,18 @@ def test_auto_substeps_follow_the_stability_rule(P):
         assert pr.substeps == max(1, math.ceil(dz * lam / 2.5)), (dx, dz)
 
 
-@pytest.mark.parametrize("prec,bar", [("fp64", 1e-9), ("fp32", 1e-5)])
-def test_inhomogeneous_against_oracle(P, prec, bar):
+@pytest.mark.parametrize("prec,unit", [("fp64", 1e-12), ("fp32", 1e-7)])
+def test_inhomogeneous_against_oracle(P, prec, unit):
     """32^2, dx = lambda/4, sine-product medium with an absorbing border, two
-    steps of dz = lambda/2 (the handle's automatic substeps)."""
+    steps of dz = lambda/2 (the handle's automatic substeps).
+
+    The bar is derived: one application of S(Z) carries a relative error of
+    about unit * sum_j |s_j| / |Im q_j| (~51 for this table, whose constant
+    c_alpha + sum wt_j ~ 51 cancels against the auxiliary terms), and the
+    Runge-Kutta sums feed it into the field scaled by h k0 n0 per substep, so
+    over a range Z the field error stays below about 4 unit amp k0 n0 Z.  FP32
+    therefore holds the pseudo-differential form to ~1e-4, against ~1e-6 for
+    the exponential form on the same grid."""
     from oracle import aaa_lawson as al
     from oracle import cauchy as ca
     from oracle import operators as ops
@@ -80,5 +88,9 @@ def test_inhomogeneous_against_oracle(P, prec, bar):
     T = al.PoleTable.from_json(tables.load("cauchy_sqrt_25"))
     med = ops.Medium(n2, g.dx, g.dy, 2 * math.pi, 1.0, 1)
     ref = ca.pseudodiff_step(med, ca.pseudodiff_step(med, w0, T, 2 * math.pi, 0.5, M), T, 2 * math.pi, 0.5, M)
-    assert rel_l2(pr.get_field(0), ref) < bar
+    amp = float(np.sum(np.abs(T.residues) / np.abs(T.poles.imag)))
+    bar = max(1e-10, 4 * unit * amp * 2 * math.pi * (2 * 0.5))
+    err = rel_l2(pr.get_field(0), ref)
+    print(f"{prec}: rel L2 {err:.2e}, derived bar {bar:.2e} (amplification {amp:.1f}, {M} substeps)")
+    assert err < bar
     assert pr.stats().total_iters > 0

@@ -61,12 +61,26 @@ def test_sineprod_reduced_matches_oracle(P, q):
     assert rel_l2(got, ref) < 1e-5
 
 
-@pytest.mark.parametrize("q,key", [(2.0, "q2"), (1.0, "q1"), (0.5, "q05")])
-def test_sineprod_centroid_after_240_wavelengths(P, q, key):
+def test_sineprod_centroids_after_240_wavelengths(P):
+    """Full runs of the three fields.  What carries over from the paper's runs:
+    the direction of the centroid shift (the sign of each component) in all
+    three fields, the k0 n0 field (q = 1) shifting the beam most, and the 2 k0 n0
+    field (q = 0.5), whose scattering is evanescent, leaving it on the axis.  The
+    magnitudes do not: measured on GB300, (0.68, -0.76), (0.011, -0.010) and
+    (-0.0007, 0.0006) lambda against the paper's (9.96, -11.36), (0.217, -0.229)
+    and (-0.00007, 0.00005); the reading of the beam width (12.5 or 25 lambda
+    radius) and of the centroid weight (|w|^2 or |w|) change ours by less than 2x."""
     from paper_2410_17446_gb300 import workloads as wl
-    W = wl.sineprod_helmholtz(q)
-    w, pr = run(P, W, W.nsteps)
-    cx, cy = centroid(w, W.beams[0].grid)
-    px, py = GOLD[key]
-    print(f"q = {q}: centroid ({cx:.4f}, {cy:.4f}) lambda after {W.nsteps} steps of {W.dz:.4f}; paper ({px}, {py})")
-    assert np.isfinite(cx) and np.isfinite(cy)
+    c = {}
+    for q, key in ((2.0, "q2"), (1.0, "q1"), (0.5, "q05")):
+        W = wl.sineprod_helmholtz(q)
+        w, pr = run(P, W, W.nsteps)
+        c[key] = centroid(w, W.beams[0].grid)
+        pr.close()
+        px, py = GOLD[key]
+        print(f"q = {q}: centroid ({c[key][0]:.4f}, {c[key][1]:.4f}) lambda after {W.nsteps} steps of "
+              f"{W.dz:.4f}; paper ({px}, {py})")
+        assert np.sign(c[key][0]) == np.sign(px) and np.sign(c[key][1]) == np.sign(py), key
+    size = {k: math.hypot(*v) for k, v in c.items()}
+    assert size["q1"] > 10 * size["q2"] > 10 * size["q05"]
+    assert size["q05"] < 0.01
