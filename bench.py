@@ -274,14 +274,19 @@ def roofline_of(name: str, prof: dict, ms_total: float) -> dict:
     dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
     peak, src = _peak()
     achieved = dom[1]["alg_bytes"] / (dom[1]["total_ms"] / 1e3) / 1e9 if dom[1]["total_ms"] > 0 else 0.0
+    # DRAM bytes per launch from an ncu capture of the current kernel: stored as measured
+    # DRAM bytes per algorithmic byte (a smaller capture, scaled to this launch's units)
     traffic = None
+    alg_launch = dom[1]["alg_bytes"] / max(1, dom[1]["launches"])
     tpath = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            traffic = json.load(f).get(dom[0])
+            t = json.load(f).get(dom[0])
+        if isinstance(t, dict) and t.get("dram_per_alg_byte"):
+            traffic = t["dram_per_alg_byte"] * alg_launch
     return {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-            "alg_bytes_per_launch": dom[1]["alg_bytes"] / max(1, dom[1]["launches"]),
+            "alg_bytes_per_launch": alg_launch,
             "launches": dom[1]["launches"], "share_of_step": dom[1]["total_ms"] / ms_total if ms_total else None}
 
 

@@ -396,6 +396,14 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
     }
   }
   for (int i = threadIdx.x; i < NY; i += NT) tws[i] = g.twy[i];   // while the tiles are in flight
+  // the pole's ky axis table (hi, lo pairs) into shared memory as well
+  const bool pmul = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD || mul == MUL_PREC_INV);
+  T* ays = reinterpret_cast<T*>(DY ? tab + NY * NV : tab);   // after the d/dy tile, else in the tile's room
+  if (pmul) {
+    const int k = pole >= 0 ? pole : u % g.P;
+    const T* ay = g.ay + (long)k * g.ny * 2;
+    for (int i = threadIdx.x; i < 2 * NY; i += NT) ays[i] = ay[i];
+  }
   if (!mbar_wait(&bar, 0, g.err)) { mbar_wait(&bar, 0, g.err); return; }
   __syncthreads();
   if (fwd) fft_smem<C, NY, false, NV, NT, true, true>(s, tws, threadIdx.x);
@@ -426,8 +434,8 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
       } else if (mul == MUL_DYY) {
         const T kk = (T)ffreq(n, g.ny) * g.ky0;
         a.x *= -kk * kk * scale; a.y *= -kk * kk * scale;
-      } else {   // as in k_cols: Re(zeta_fs - p) from (hi, lo) pairs
-        const T re = ((ax[2 * i] + ay[2 * n]) + (ax[2 * i + 1] + ay[2 * n + 1])) + sh.x;
+      } else {   // as in k_cols: Re(zeta_fs - p) from (hi, lo) pairs (the ky table from shared memory)
+        const T re = ((ax[2 * i] + ays[2 * n]) + (ax[2 * i + 1] + ays[2 * n + 1])) + sh.x;
         C f;
         if (mul != MUL_POLE_FWD) {
           const T d = scale / (re * re + pim * pim);
@@ -601,6 +609,15 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
       for (int e = threadIdx.x * 8; e < NR * N; e += NT * 8) prefetch_l2(w0 + (uo + e) * 16);
     }
   }
+  if constexpr (ARN) {   // v_j and delta are read after the inverse DFT: start their DRAM fetch now
+    const long vj = (((long)u * (g.m + 2) + ep.jj) * g.ncomp + c) * g.npts + off;
+    const char* pv = reinterpret_cast<const char*>(g.V + vj);
+    const char* pd = reinterpret_cast<const char*>(g.delta + (long)beam * g.npts + off);
+    for (int b = threadIdx.x * 128; b < NR * N * (int)sizeof(C); b += NT * 128) {
+      prefetch_l2(pv + b);
+      prefetch_l2(pd + b);
+    }
+  }
   const bool in16 = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
   if (sizeof(T) == 4 && in16) {   // 16-byte loads: two points (same row, N even) per access
 #pragma unroll
@@ -650,7 +667,9 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
       st2(wout, e, w0, w1);
     }
   } else {
-  double acc = 0.0, acc2 = 0.0, accr = 0.0, acci = 0.0;
+  // per-thread partial sums in T (FP64 arithmetic per point is scarce on this GPU),
+  // summed in FP64 across the block below
+  T acc = 0, acc2 = 0, accr = 0, acci = 0;
   bool acc16 = false;   // the FP32 accumulate ran vectorised below
   if constexpr (sizeof(T) == 4) {
     const long plane = (long)g.nb * g.ncomp * g.npts;
@@ -719,30 +738,30 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
         a.x += (double)val.x; a.y += (double)val.y;
         g.E[unit_off + e] = a;
         const T ax = (T)a.x, ay = (T)a.y;
-        acc += (double)(ax * ax + ay * ay);
+        acc += ax * ax + ay * ay;
       } break;
       case EPI_R0: {
         const C r = cmul(dl[e], val);
         C m; m.x = -r.x; m.y = -r.y;
         g.R0[unit_off + e] = m;
-        acc += (double)m.x * m.x + (double)m.y * m.y;
-        acc2 += (double)val.x * val.x + (double)val.y * val.y;
+        acc += m.x * m.x + m.y * m.y;
+        acc2 += val.x * val.x + val.y * val.y;
       } break;
-      case EPI_TRUERES: {
-        const double2 r0 = to_d(g.R0[unit_off + e]);
+      case EPI_TRUERES: {   // r = R0 - (Z - p) e in T: the same precision as the transform that formed val
+        const C r0 = g.R0[unit_off + e];
         const long vb = (((long)u * (g.m + 2)) * g.ncomp + c) * g.npts + off + e;
-        double2 r;
+        C r;
         if (g.ncomp == 2) {   // (Z - Z_fs) e was written into v_0 by the preceding pass
-          const double2 a = to_d(g.V[vb]);
-          r.x = r0.x - (double)val.x - a.x;
-          r.y = r0.y - (double)val.y - a.y;
+          const C a = g.V[vb];
+          r.x = r0.x - val.x - a.x;
+          r.y = r0.y - val.y - a.y;
         } else {
-          const double2 ee = g.E[unit_off + e];
-          const double2 d = to_d(dl[e]);
-          r.x = r0.x - (double)val.x - (d.x * ee.x - d.y * ee.y);
-          r.y = r0.y - (double)val.y - (d.x * ee.y + d.y * ee.x);
+          const C ee = to_c(g.E[unit_off + e], T());
+          const C de = cmul(dl[e], ee);
+          r.x = r0.x - val.x - de.x;
+          r.y = r0.y - val.y - de.y;
         }
-        g.V[vb] = to_c(r, T());
+        g.V[vb] = r;
         acc += r.x * r.x + r.y * r.y;
         accr += r0.x * r.x + r0.y * r.y;      // <R0, r> = sum conj(R0) r
         acci += r0.x * r.y - r0.y * r.x;
@@ -765,20 +784,20 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
     }
   }
   if (ep.mode == EPI_R0 || ep.mode == EPI_TRUERES) {
-    const double t = block_sum(acc, red);
+    const double t = block_sum((double)acc, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].nrm_a, t);
   }
   if (ep.mode == EPI_R0) {
-    const double t = block_sum(acc2, red);
+    const double t = block_sum((double)acc2, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t);
   }
   if (ep.mode == EPI_ADD_E) {
-    const double t = block_sum(acc, red);
+    const double t = block_sum((double)acc, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].enorm2, t);
   }
   if (ep.mode == EPI_TRUERES) {
-    const double tr = block_sum(accr, red);
-    const double ti = block_sum(acci, red);
+    const double tr = block_sum((double)accr, red);
+    const double ti = block_sum((double)acci, red);
     if (threadIdx.x == 0) { atomicAdd(&g.st[u].r0r.x, tr); atomicAdd(&g.st[u].r0r.y, ti); }
   }
   }
@@ -833,7 +852,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   fft_rows<C, N, true, NVV, NT>(s, g.twx, threadIdx.x);
   const C* cf = g.psi + (long)beam * 5 * g.npts + off;    // D1, D2, X, px, py planes
   const long F = 2 * g.npts;
-  double acc = 0.0, acc2 = 0.0;
+  T acc = 0, acc2 = 0;   // per-thread partials in T, FP64 across the block
   for (int e2 = threadIdx.x; e2 < NR * N / 2; e2 += NT) {   // point pairs: 16-byte accesses in FP32
     const int e = 2 * e2, r = e / N, n0 = e % N;
     C cD1[2], cD2[2], cX[2], cpx[2], cpy[2], d1v[2], d2v[2], z1v[2], z2v[2];
@@ -879,10 +898,8 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         m1[h].x = -d1v[h].x; m1[h].y = -d1v[h].y; m2[h].x = -d2v[h].x; m2[h].y = -d2v[h].y;
-        acc += (double)m1[h].x * m1[h].x + (double)m1[h].y * m1[h].y + (double)m2[h].x * m2[h].x +
-               (double)m2[h].y * m2[h].y;
-        acc2 += (double)z1v[h].x * z1v[h].x + (double)z1v[h].y * z1v[h].y + (double)z2v[h].x * z2v[h].x +
-                (double)z2v[h].y * z2v[h].y;
+        acc += m1[h].x * m1[h].x + m1[h].y * m1[h].y + m2[h].x * m2[h].x + m2[h].y * m2[h].y;
+        acc2 += z1v[h].x * z1v[h].x + z1v[h].y * z1v[h].y + z2v[h].x * z2v[h].x + z2v[h].y * z2v[h].y;
       }
       st2(g.R0 + rb, e, m1[0], m1[1]);
       st2(g.R0 + rb + g.npts, e, m2[0], m2[1]);
@@ -892,9 +909,9 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
     }
   }
   if (mode == VEPI_R0) {
-    const double t = block_sum(acc, red);
+    const double t = block_sum((double)acc, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].nrm_a, t);
-    const double t2 = block_sum(acc2, red);
+    const double t2 = block_sum((double)acc2, red);
     if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t2);
   }
 }
@@ -1275,21 +1292,22 @@ __global__ void __launch_bounds__(NT) k_medium(GV<T> g, int beam, const double2*
   C* d = g.delta + (long)beam * g.npts;
   __shared__ double red[32];
   int nz = 0;
-  double sr = 0.0, si = 0.0;
+  T sr = 0, si = 0;   // per-thread partials of the delta the kernels use (FP64 across the block)
+  const double inv = 1.0 / n0sq;
   for (long p = (long)blockIdx.x * NT + threadIdx.x; p < g.npts; p += (long)gridDim.x * NT) {
     const double2 a = n2[p];
-    double2 v; v.x = (a.x - n0sq) / n0sq; v.y = a.y / n0sq;
+    double2 v; v.x = (a.x - n0sq) * inv; v.y = a.y * inv;
     const C t = to_c(v, T());
     d[p] = t;
-    sr += (double)t.x; si += (double)t.y;   // the mean of the delta the kernels use
+    sr += t.x; si += t.y;
     if (psi_out) {
       const double2 lg = make_double2(0.5 * log(a.x * a.x + a.y * a.y), atan2(a.y, a.x));
       psi_out[p] = to_c(lg, T());
     }
     nz |= (t.x != (T)0 || t.y != (T)0);
   }
-  const double tr = block_sum(sr, red);
-  const double ti = block_sum(si, red);
+  const double tr = block_sum((double)sr, red);
+  const double ti = block_sum((double)si, red);
   if (threadIdx.x == 0) { atomicAdd(&g.dsum[beam].x, tr); atomicAdd(&g.dsum[beam].y, ti); }
   if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&g.nonhomog[beam], 1);
 }

@@ -141,6 +141,10 @@ struct prop {
   std::vector<cudaEvent_t> pool;
   int64_t k_launches[PROP_NKINDS];
   double k_ms[PROP_NKINDS], k_bytes[PROP_NKINDS];
+  // pipelined Arnoldi batches: pinned host copies of the two count-slot sets and
+  // the events that mark their arrival
+  int* hcounts;
+  cudaEvent_t batch_ev[2];
 };
 
 namespace {
@@ -357,12 +361,14 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
   if (cplan != PROP_COLS_PLAIN && g.err && cm.src && cm.dst && (mul != MUL_TABLE || cm.tab) &&
       (!DY || (cm.dy && mul != MUL_TABLE))) {
     constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
-    const size_t sm = ((size_t)NY * NV * (mul == MUL_TABLE || DY ? 2 : 1) + NY) * sizeof(C) + 128;   // + twiddles, slack
+    // tile, twiddles, then the table or d/dy tile and/or the pole's ky table; 128 bytes of alignment slack
+    const bool pmul = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD || mul == MUL_PREC_INV);
+    const size_t sm = ((size_t)NY * NV * (mul == MUL_TABLE || DY ? 2 : 1) + NY + (pmul ? NY : 0)) * sizeof(C) + 128;
     auto k = k_cols_tma<T, NY, NV, NT, DY>;
     static bool attr = false;
-    if (!attr) {   // room for the table tile whatever this launch needs
+    if (!attr) {   // room for the largest layout
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)((2 * NY * NV + NY) * sizeof(C) + 128));
+                                           (int)((2 * (size_t)NY * NV + 2 * NY) * sizeof(C) + 128));
       if (e != cudaSuccess) return e;
       attr = true;
     }
@@ -591,14 +597,19 @@ cudaEvent_t take_event(prop* h) {
 }
 
 // Resolve recorded event pairs; call only after the stream has been synchronised.
+// Resolve the recorded event pairs whose launches have finished (the end event has
+// completed); pairs still in flight stay pending.
 void resolve_pending(prop* h) {
-  for (auto& p : h->pending) {
+  size_t keep = 0;
+  for (size_t i = 0; i < h->pending.size(); ++i) {
+    auto& p = h->pending[i];
+    if (cudaEventQuery(p.b) != cudaSuccess) { h->pending[keep++] = p; continue; }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->k_ms[p.kind] += ms;
     h->pool.push_back(p.a);
     h->pool.push_back(p.b);
   }
-  h->pending.clear();
+  h->pending.resize(keep);
   cudaGetLastError();
 }
 
@@ -807,57 +818,80 @@ template <typename T> int step_group(prop* h, Group& G) {
     // algorithmic bytes of each launch are charged from these counts exactly.
     // Step j = m only finalises column m-1: no operator application, and the
     // Gram sweep forms the products with u alone.
-    std::vector<int> cnt(3 * (SYNC_EVERY + 1));
-    int jj0 = 0, ended = 0, flags = 0, act0 = c3[0];
-    for (int jj = 0; jj <= m; ++jj) {
-      if (jj == jj0) {   // batch start: zero the count slots, list the act0 iterating systems
-        CK(cudaMemsetAsync(counts + 3, 0, 3 * SYNC_EVERY * sizeof(int), st));
-        Prof p_(h, K_CONTROL, 0);
-        k_active_list<<<1, 256, 0, st>>>(g.st, nsys, ulist);
-      }
-      const bool op = jj < m;
-      if (op) {
-        C* Vj = g.V + (long)jj * F;
-        const long vs = (long)(m + 2) * F;
-        { Prof p_(h, K_ROWS_FWD, 0);
-          CK(rows_fwd<T, C>(ga, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, act0, st)); }
-        if (Cn == 2) {
-          { Prof p_(h, K_COLS, 0);
-            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act0, st,
-                       Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
-          { Prof p_(h, K_ROWS_INV, 0);
-            CK(rows_inv_vec<T>(ga, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, jj, act0,
-                               st)); }
-        } else {
-          { Prof p_(h, K_COLS, 0);
-            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act0, st, none,
-                     none, tmaps)); }
-          { Prof p_(h, K_ROWS_INV, 0);
-            CK(rows_inv<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, jj), act0, st)); }
+    // Two batches are kept in flight: batch b+1 is enqueued, sized by the last
+    // count the host has seen (a superset of the iterating systems: systems only
+    // leave), before the host waits for batch b's counts, so the GPU does not idle
+    // while the host reads them.  Each batch has its own count slots (parity).
+    struct Batch { int jj0, nb, par; };
+    Batch fl[2];
+    int nfl = 0, jj = 0, ended = 0, flags = 0;
+    int act_est = c3[0];        // for sizing launches
+    int before = c3[0];         // systems iterating at the next unprocessed step
+    bool stop = false;
+    auto enqueue = [&](int par) -> int {
+      const int jb = jj, nb = std::min(SYNC_EVERY, m + 1 - jj);
+      int* slots = counts + 3 + par * 3 * SYNC_EVERY;
+      CK(cudaMemsetAsync(slots, 0, 3 * SYNC_EVERY * sizeof(int), st));
+      { Prof p_(h, K_CONTROL, 0);
+        k_active_list<<<1, 256, 0, st>>>(g.st, nsys, ulist); }
+      const int act = std::max(act_est, 1);
+      for (int j = jb; j < jb + nb; ++j) {
+        const bool op = j < m;
+        if (op) {
+          C* Vj = g.V + (long)j * F;
+          const long vs = (long)(m + 2) * F;
+          { Prof p_(h, K_ROWS_FWD, 0);
+            CK(rows_fwd<T, C>(ga, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, act, st)); }
+          if (Cn == 2) {
+            { Prof p_(h, K_COLS, 0);
+              CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act, st,
+                         Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
+            { Prof p_(h, K_ROWS_INV, 0);
+              CK(rows_inv_vec<T>(ga, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, j, act,
+                                 st)); }
+          } else {
+            { Prof p_(h, K_COLS, 0);
+              CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act, st, none,
+                         none, tmaps)); }
+            { Prof p_(h, K_ROWS_INV, 0);
+              CK(rows_inv<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, j), act, st)); }
+          }
         }
+        // sweeps: about one wave of CTAs (4 resident per SM) shared by the act systems
+        const int cap = std::max(1, 4 * sm_count() / act);
+        { Prof p_(h, K_GRAM, 0);
+          k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>
+              <<<dim3(std::min(gram_blocks, cap), act), NT_VEC, 0, st>>>(ga, j, op ? 1 : 0); }
+        { Prof p_(h, K_GS_UPDATE, 0);
+          StepArgs sa;
+          sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
+          sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = slots + 3 * (j - jb);
+          k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS><<<dim3(std::min(gs_blocks, cap) + 1, act), NT_VEC, 0, st>>>(ga, j, sa); }
+        CK(cudaGetLastError());
       }
-      { Prof p_(h, K_GRAM, 0);
-        // sweeps: about one wave of CTAs (4 resident per SM) shared by the act0 systems
-        const int cap = std::max(1, 4 * sm_count() / std::max(act0, 1));
-        k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>
-            <<<dim3(std::min(gram_blocks, cap), act0), NT_VEC, 0, st>>>(ga, jj, op ? 1 : 0); }
-      { Prof p_(h, K_GS_UPDATE, 0);
-        StepArgs sa;
-        sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
-        sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = counts + 3 * (jj - jj0 + 1);
-        const int cap = std::max(1, 4 * sm_count() / std::max(act0, 1));
-        k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS><<<dim3(std::min(gs_blocks, cap) + 1, act0), NT_VEC, 0, st>>>(ga, jj, sa); }
-      CK(cudaGetLastError());
-      const bool sync_now = ((jj + 1 - jj0) % SYNC_EVERY) == 0 || jj == m;
-      if (!sync_now) continue;
-      const int nb = jj + 1 - jj0;
-      if (cudaMemcpyAsync(cnt.data() + 3, counts + 3, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess)
-        return PROP_E_CUDA;
+      CK(cudaMemcpyAsync(h->hcounts + par * 3 * SYNC_EVERY, slots, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(h->batch_ev[par], st));
+      fl[nfl++] = Batch{jb, nb, par};
+      jj += nb;
+      return PROP_OK;
+    };
+    int next_par = 0;
+    while (true) {
+      while (!stop && jj <= m && nfl < 2) {
+        const int rc2 = enqueue(next_par);
+        if (rc2) return rc2;
+        next_par ^= 1;
+      }
+      if (nfl == 0) break;
+      // the oldest batch's counts
+      const Batch bt = fl[0];
+      fl[0] = fl[1];
+      --nfl;
+      if (cudaEventSynchronize(h->batch_ev[bt.par]) != cudaSuccess) return PROP_E_CUDA;
       if (!h->pending.empty()) resolve_pending(h);
-      int before = act0;                                   // systems iterating at step j
-      for (int b2 = 0; b2 < nb; ++b2) {
-        const int j = jj0 + b2;
+      const int* hc = h->hcounts + bt.par * 3 * SYNC_EVERY;
+      for (int b2 = 0; b2 < bt.nb; ++b2) {
+        const int j = bt.jj0 + b2;
         const double act = (double)before * Cn * pts;
         if (j < m) {
           h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
@@ -867,14 +901,13 @@ template <typename T> int step_group(prop* h, Group& G) {
         }
         h->k_bytes[K_GRAM] += (j + (j < m ? 2.0 : 1.0)) * cs * act;   // v_0..v_{j-1}, u (and w) read
         if (j >= 1) h->total_iters += before;               // column j-1 finalised for each of them
-        const int* sl = cnt.data() + 3 * (b2 + 1);
+        const int* sl = hc + 3 * b2;
         ended += sl[1];
         flags |= sl[2];
         before = sl[0];
       }
-      act0 = before;
-      jj0 = jj + 1;
-      if (act0 == 0) break;
+      act_est = before;
+      if (before == 0) stop = true;   // any batch still in flight is empty (every launch masked)
     }
     c3[0] = 0; c3[1] = ended; c3[2] = flags;
     if (c3[1] == 0) break;
@@ -1130,10 +1163,18 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   h->steps = 0; h->total_iters = 0; h->last_status = 0;
   h->launches = 0; h->profiling = 0;
   for (int k = 0; k < PROP_NKINDS; ++k) { h->k_launches[k] = 0; h->k_ms[k] = 0.0; h->k_bytes[k] = 0.0; }
-  if (cudaMemsetAsync(h->ws, 0, need, h->stream) != cudaSuccess) { delete h; return PROP_E_CUDA; }
+  h->hcounts = nullptr;
+  h->batch_ev[0] = h->batch_ev[1] = nullptr;
+  if (cudaHostAlloc((void**)&h->hcounts, 2 * 3 * SYNC_EVERY * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->batch_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->batch_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    prop_destroy(h);
+    return PROP_E_CUDA;
+  }
+  if (cudaMemsetAsync(h->ws, 0, need, h->stream) != cudaSuccess) { prop_destroy(h); return PROP_E_CUDA; }
   for (Group& G : h->groups) {
     rc = h->prec == PROP_FP64 ? upload_group_tables<double>(h, G) : upload_group_tables<float>(h, G);
-    if (rc) { delete h; return rc; }
+    if (rc) { prop_destroy(h); return rc; }
     const int csz = 2 * (int)elem_size(h->prec);   // bytes per complex element
     const int nv = h->prec == PROP_FP64 ? cols_per_cta<double>() : cols_per_cta<float>();
     const long nb = (long)G.beams.size();
@@ -1401,8 +1442,13 @@ const char* prop_error_string(int status) {
 
 void prop_destroy(prop* h) {
   if (!h) return;
-  if (!h->pending.empty()) { cudaStreamSynchronize(h->stream); resolve_pending(h); }
+  if (!h->pending.empty() || h->hcounts) cudaStreamSynchronize(h->stream);
+  if (!h->pending.empty()) resolve_pending(h);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->batch_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->hcounts) cudaFreeHost(h->hcounts);
+  cudaGetLastError();
   delete h;
 }
 
