@@ -237,24 +237,32 @@ int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t 
  * PROP_COLS_TMA. */
 enum prop_fft_rows { PROP_ROWS_BLOCK = 0, PROP_ROWS_WARP = 1 };
 enum prop_fft_cols { PROP_COLS_TMA = 0, PROP_COLS_PLAIN = 1, PROP_COLS_WARP = 2 };
-typedef struct prop_fft_plan { int32_t rows, cols; } prop_fft_plan;
+/* rows, cols: launches of more than PROP_FFT_SMALL_ITEMS arrays; *_small: launches of
+ * at most that many (the late Arnoldi steps, when few systems still iterate). */
+#define PROP_FFT_SMALL_ITEMS 2
+typedef struct prop_fft_plan { int32_t rows, cols, rows_small, cols_small; } prop_fft_plan;
 
 /* Current plan for size n (a supported size) and precision. */
 int prop_get_fft_plan(int32_t n, int32_t precision, prop_fft_plan* out);
 /* Install a plan; PROP_E_UNSUPPORTED if a variant does not exist for n. */
 int prop_set_fft_plan(int32_t n, int32_t precision, const prop_fft_plan* plan);
-/* Device bytes prop_fft_autotune needs for `batch` n x n arrays. */
+/* Device bytes prop_fft_autotune needs for `batch` n x n arrays (plus 256 MiB to
+ * flush L2 between timed runs when the arrays are smaller than that). */
 int prop_fft_autotune_workspace_size(int32_t n, int32_t precision, int32_t batch, size_t* bytes);
 /* Time every variant on `batch` n x n arrays in d_work (256-byte aligned,
  * contents overwritten): a row round trip (forward then inverse rows) per row
  * variant and a column pass (forward, scale, inverse) per column variant, best
- * of `reps` runs after one warm-up, CUDA events on `stream`.  ms[5] receives the
- * times in ms (rows block, rows warp, cols TMA, cols plain, cols warp; -1 for a
- * variant that does not exist) and *best the fastest of each pass.  Installs
- * nothing (call prop_set_fft_plan) and leaves the current plan unchanged.
- * Synchronises the stream. */
-int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps, void* d_work, size_t work_bytes,
-                      void* stream, prop_fft_plan* best, float* ms);
+ * of `reps` runs after one warm-up, CUDA events on `stream`.  l2cold = 1: L2 is
+ * flushed before each run when the data would fit in it (data read from HBM);
+ * 0: the data stay in L2 between runs, as the output of one pass stays for the
+ * next in a launch chain on few arrays.  ms[5] receives the times in ms (rows
+ * block, rows warp, cols TMA, cols plain, cols warp; -1 for a variant that does
+ * not exist) and *best the fastest of each pass at this batch (in both the
+ * large and the small fields); a variant replaces the default (block rows; TMA
+ * columns where tensor maps exist, else plain) only when more than 5 % faster.  Installs nothing (call prop_set_fft_plan) and
+ * leaves the current plan unchanged.  Synchronises the stream. */
+int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps, int32_t l2cold, void* d_work,
+                      size_t work_bytes, void* stream, prop_fft_plan* best, float* ms);
 
 /* Install the initial-guess network (include/prop_cnn.h) for PROP_GUESS_LEARNED.
  * The paper has no learned part: GMRES still runs to the same tolerance, the

@@ -27,27 +27,37 @@ def gpu_name() -> str:
     return torch.cuda.get_device_name()
 
 
-def tune(n: int, precision: int, reps: int = 5, min_bytes: int = 256 << 20) -> dict:
-    """Time every variant for size n; returns the record (times and the best plan)."""
+def _time(n: int, precision: int, batch: int, reps: int, l2cold: int):
     import torch
-    cs = 8 if precision == P.PROP_FP32 else 16
-    batch = max(1, -(-min_bytes // (n * n * cs)))
     nb = P.prop_fft_autotune_workspace_size(n, precision, batch)
     work = torch.empty(nb, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    best, ms = P.prop_fft_autotune(n, precision, batch, reps, work, nb, stream)
+    best, ms = P.prop_fft_autotune(n, precision, batch, reps, work, nb, stream, l2cold)
     del work
+    return best, ({"block": ms[0], "warp": ms[1] if ms[1] >= 0 else None},
+                  {"tma": ms[2] if ms[2] >= 0 else None, "plain": ms[3], "warp": ms[4] if ms[4] >= 0 else None})
+
+
+def tune(n: int, precision: int, reps: int = 5, min_bytes: int = 256 << 20) -> dict:
+    """Time every variant for size n at two launch sizes: a batch of at least
+    `min_bytes` read from HBM (the large class) and a single array left in L2
+    between runs (the small class: the late Arnoldi steps, whose few arrays pass
+    from one kernel to the next through L2); returns the record."""
+    cs = 8 if precision == P.PROP_FP32 else 16
+    batch = max(1 + P.PROP_FFT_SMALL_ITEMS, -(-min_bytes // (n * n * cs)))
+    big, (rows_ms, cols_ms) = _time(n, precision, batch, reps, 1)
+    small, (rows_ms1, cols_ms1) = _time(n, precision, 1, reps, 0)
     return {"n": n, "precision": PREC[precision], "batch": batch, "reps": reps,
-            "rows_ms": {"block": ms[0], "warp": ms[1] if ms[1] >= 0 else None},
-            "cols_ms": {"tma": ms[2] if ms[2] >= 0 else None, "plain": ms[3], "warp": ms[4] if ms[4] >= 0 else None},
-            "rows": ROWS[best.rows], "cols": COLS[best.cols]}
+            "rows_ms": rows_ms, "cols_ms": cols_ms, "rows_ms_small": rows_ms1, "cols_ms_small": cols_ms1,
+            "rows": ROWS[big.rows], "cols": COLS[big.cols],
+            "rows_small": ROWS[small.rows], "cols_small": COLS[small.cols]}
 
 
 def install(rec: dict) -> None:
     prec = {v: k for k, v in PREC.items()}[rec["precision"]]
-    rows = {v: k for k, v in ROWS.items()}[rec["rows"]]
-    cols = {v: k for k, v in COLS.items()}[rec["cols"]]
-    P.prop_set_fft_plan(rec["n"], prec, rows, cols)
+    R = {v: k for k, v in ROWS.items()}
+    Cc = {v: k for k, v in COLS.items()}
+    P.prop_set_fft_plan(rec["n"], prec, R[rec["rows"]], Cc[rec["cols"]], R[rec["rows_small"]], Cc[rec["cols_small"]])
 
 
 def _read(path: str) -> dict:
@@ -70,6 +80,8 @@ def load_or_tune(sizes: Iterable[int], precision: int = P.PROP_FP32, path: Optio
     for n in sorted(set(int(x) for x in sizes)):
         key = f"{PREC[precision]}:{n}"
         rec = None if retune else entry.get(key)
+        if rec is not None and "rows_small" not in rec:
+            rec = None                      # a record from before the small launch class
         source = "cache"
         if rec is None:
             rec = tune(n, precision)

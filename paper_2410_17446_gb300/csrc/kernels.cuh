@@ -82,9 +82,12 @@ template <typename T> struct GV {
 };
 
 // Unit and (unit, component) item of grid row y, through the optional unit list.
+// -1 for an empty row of the list (the caller returns).
 template <typename T> __device__ __forceinline__ int unit_of(const GV<T>& g, int y) { return g.ulist ? g.ulist[y] : y; }
 template <typename T> __device__ __forceinline__ int item_of(const GV<T>& g, int y) {
-  return g.ulist ? g.ulist[y / g.ncomp] * g.ncomp + y % g.ncomp : y;
+  if (!g.ulist) return y;
+  const int u = g.ulist[y / g.ncomp];
+  return u < 0 ? -1 : u * g.ncomp + y % g.ncomp;
 }
 
 // Signed FFT frequency index of position i on an n-point grid.
@@ -205,7 +208,9 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y);
+  if (item < 0) return;
+  const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   const int row0 = blockIdx.x * NR;
   const SRC* in = src.at(u, c, g.npts) + (long)row0 * N;
@@ -267,7 +272,9 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
   constexpr int W = DY ? 2 * NV : NV;     // tile width in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y);
+  if (item < 0) return;
+  const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   const int x0 = blockIdx.x * NV;
@@ -370,7 +377,9 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   C* tws = s + NY * NV;                       // twiddles
   C* tab = tws + NY;                          // multiplier tile (MUL_TABLE), or the d/dy tile (DY)
   __shared__ __align__(8) uint64_t bar;
-  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y);
+  if (item < 0) return;
+  const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   // once any CTA's copy has failed the step is void: issue no further copies, so
@@ -496,7 +505,9 @@ __global__ void __launch_bounds__(32 * CW_NV) k_cols_warp(GV<T> g, Buf<typename 
   constexpr int NT = 32 * CW_NV, L = NY / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y);
+  if (item < 0) return;
+  const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   if (skip_homog && !g.nonhomog[u / g.P]) return;
   const int x0 = blockIdx.x * CW_NV;
@@ -588,7 +599,9 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int item = item_of(g, (int)blockIdx.y), u = item / g.ncomp, c = item % g.ncomp;
+  const int item = item_of(g, (int)blockIdx.y);
+  if (item < 0) return;
+  const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   const bool sys = (ep.mode == EPI_R0 || ep.mode == EPI_ARNOLDI || ep.mode == EPI_TRUERES || ep.mode == EPI_ADD_E);
   const int beam = sys ? u / g.P : u;
@@ -826,7 +839,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
   const int u = unit_of(g, (int)blockIdx.y);
-  if (!unit_active(g.st, mask, u)) return;
+  if (u < 0 || !unit_active(g.st, mask, u)) return;
   const int beam = (mode == VEPI_OPDIFF && mask < 0) ? u : u / g.P;
   if (skip_homog && !g.nonhomog[beam]) return;
   const int row0 = blockIdx.x * NR;
@@ -978,7 +991,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   constexpr int NW = NT / 32;
   __shared__ double red[NW][4 * (MMAX + 1)];
   const int s = unit_of(g, (int)blockIdx.y);
-  if (g.st[s].state != ST_ITER) return;
+  if (s < 0 || g.st[s].state != ST_ITER) return;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long L = (long)g.ncomp * g.npts;
   const C* up = vslot(g, s, jj);
@@ -1611,6 +1624,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   __shared__ C ca[MMAX + 8], cg[MMAX + 8];
   __shared__ T ir_s;
   const int s = unit_of(g, (int)blockIdx.y), j = jj, tid = threadIdx.x;
+  if (s < 0) return;
   SysState& q = g.st[s];
   if (q.state != ST_ITER) return;
   const int par = j & 1;
@@ -1890,6 +1904,9 @@ __global__ void k_active_list(const SysState* st, int nsys, int* list) {
     if (threadIdx.x == 0) for (int k = 0; k < nw; ++k) base += wsum[k];
     __syncthreads();
   }
+  // the rest of the list marks empty grid rows: a launch sized for more systems
+  // than iterate (the host's count lags by a batch) skips them
+  for (int s = base + threadIdx.x; s < nsys; s += blockDim.x) list[s] = -1;
 }
 
 // counts[0] = systems iterating, counts[1] = at a cycle end, counts[2] = flags

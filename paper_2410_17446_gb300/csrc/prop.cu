@@ -77,11 +77,19 @@ int size_index(int n) {
     case 384: return 5; case 512: return 6; case 768: return 7; case 1024: return 8; default: return -1;
   }
 }
-std::atomic<int> g_plan_rows[2][NSIZES];
-std::atomic<int> g_plan_cols[2][NSIZES];
+// [precision][launch class: 0 large, 1 small (<= PROP_FFT_SMALL_ITEMS arrays)][size]
+std::atomic<int> g_plan_rows[2][2][NSIZES];
+std::atomic<int> g_plan_cols[2][2][NSIZES];
 bool warp_n(int n) { return n == 512 || n == 1024; }
-int plan_rows(int prec, int n) { const int i = size_index(n); return i < 0 ? PROP_ROWS_BLOCK : g_plan_rows[prec][i].load(std::memory_order_relaxed); }
-int plan_cols(int prec, int n) { const int i = size_index(n); return i < 0 ? PROP_COLS_TMA : g_plan_cols[prec][i].load(std::memory_order_relaxed); }
+int launch_class(long items) { return items <= PROP_FFT_SMALL_ITEMS ? 1 : 0; }
+int plan_rows(int prec, int n, long items) {
+  const int i = size_index(n);
+  return i < 0 ? PROP_ROWS_BLOCK : g_plan_rows[prec][launch_class(items)][i].load(std::memory_order_relaxed);
+}
+int plan_cols(int prec, int n, long items) {
+  const int i = size_index(n);
+  return i < 0 ? PROP_COLS_TMA : g_plan_cols[prec][launch_class(items)][i].load(std::memory_order_relaxed);
+}
 template <typename T> constexpr int prec_of() { return sizeof(T) == 4 ? PROP_FP32 : PROP_FP64; }
 template <typename T, int NY> constexpr int cols_nt() { return clamp_nt(NY * cols_per_cta<T>() / 16); }
 constexpr int NT_VEC = 256;
@@ -90,6 +98,10 @@ constexpr int GVEC_GS = 4;    // basis vectors per load group of the update swee
 constexpr int EPT_GRAM = 4;   // points per thread of the Gram sweep
 constexpr int GVEC_GRAM = 4;  // basis vectors per transpose-reduce of the Gram sweep
 constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host reads of the GMRES state
+// Arnoldi batches in flight: 1, the host reads each batch's counts before enqueuing the
+// next.  (Two deep was measured on GB300: within 2 % either way on the three
+// benchmark workloads, so the launches stay sized by exact counts.)
+constexpr int PIPE_DEPTH = 1;
 constexpr int ERR_SLOT = 3 * (MMAX + 2) - 1;   // int in the counts area: the asynchronous-copy error word
 
 struct Layout {
@@ -285,7 +297,7 @@ cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
                        int units, cudaStream_t st) {
   using C = typename Cx<T>::t;
   if constexpr (warp_n_c(N)) {
-    if (plan_rows(prec_of<T>(), N) == PROP_ROWS_WARP) {
+    if (plan_rows(prec_of<T>(), N, (long)units * g.ncomp) == PROP_ROWS_WARP) {
       const size_t sm = smem_elems<N, WROWS, false>() * sizeof(C);
       auto k = k_rows_fwd<T, N, WROWS, 32 * WROWS, SRC, true>;
       static bool attr = false;
@@ -313,7 +325,7 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
   using C = typename Cx<T>::t;
   const bool arn = ep.mode == EPI_ARNOLDI;
   if constexpr (warp_n_c(N)) {
-    if (plan_rows(prec_of<T>(), N) == PROP_ROWS_WARP) {
+    if (plan_rows(prec_of<T>(), N, (long)units * g.ncomp) == PROP_ROWS_WARP) {
       const size_t sm = smem_elems<N, WROWS, false>() * sizeof(C);
       auto k = arn ? k_rows_inv<T, N, WROWS, 32 * WROWS, true, true> : k_rows_inv<T, N, WROWS, 32 * WROWS, false, true>;
       static bool attr[2] = {false, false};
@@ -343,7 +355,7 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
                     int mul, int inv, int skip, int pole, T scale, int units, cudaStream_t st,
                     Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy, ColMaps cm) {
   using C = typename Cx<T>::t;
-  const int cplan = plan_cols(prec_of<T>(), NY);
+  const int cplan = plan_cols(prec_of<T>(), NY, (long)units * g.ncomp);
   if constexpr (warp_n_c(NY) && !DY) {
     // column pass by warps: every mode but the multiplier table and the spectrum output
     if (cplan == PROP_COLS_WARP && mul != MUL_TABLE && !spec.base && g.nx % CW_NV == 0) {
@@ -877,7 +889,7 @@ template <typename T> int step_group(prop* h, Group& G) {
     };
     int next_par = 0;
     while (true) {
-      while (!stop && jj <= m && nfl < 2) {
+      while (!stop && jj <= m && nfl < PIPE_DEPTH) {
         const int rc2 = enqueue(next_par);
         if (rc2) return rc2;
         next_par ^= 1;
@@ -1535,19 +1547,27 @@ int prop_fft2(int32_t nx, int32_t ny, int32_t batch, int32_t precision, int32_t 
 // FFT plan selection (prop_get/set_fft_plan, prop_fft_autotune)
 // ---------------------------------------------------------------------------
 static bool plan_valid(int n, int prec, const prop_fft_plan& p) {
-  if (p.rows != PROP_ROWS_BLOCK && p.rows != PROP_ROWS_WARP) return false;
-  if (p.cols != PROP_COLS_TMA && p.cols != PROP_COLS_PLAIN && p.cols != PROP_COLS_WARP) return false;
-  if (!warp_n(n) && (p.rows == PROP_ROWS_WARP || p.cols == PROP_COLS_WARP)) return false;
+  for (int r : {p.rows, p.rows_small})
+    if ((r != PROP_ROWS_BLOCK && r != PROP_ROWS_WARP) || (!warp_n(n) && r == PROP_ROWS_WARP)) return false;
+  for (int c : {p.cols, p.cols_small})
+    if ((c != PROP_COLS_TMA && c != PROP_COLS_PLAIN && c != PROP_COLS_WARP) || (!warp_n(n) && c == PROP_COLS_WARP))
+      return false;
   return prec == PROP_FP32 || prec == PROP_FP64;
 }
 
 // Times (CUDA events, best of reps) of one row round trip (forward rows, inverse
 // rows) and of one column pass (forward, scale, inverse) per variant, on `batch`
 // n x n arrays in the work buffer.
+// Below this many bytes of data the timed runs would stay in L2: a 256 MiB write
+// between them (outside the timed interval) flushes it.
+constexpr size_t TUNE_FLUSH_BYTES = (size_t)256 << 20;
+
 template <typename T>
-static int autotune_impl(int n, int batch, int reps, char* work, cudaStream_t st, float* ms) {
+static int autotune_impl(int n, int batch, int reps, int l2cold, char* work, cudaStream_t st, float* ms) {
   using C = typename Cx<T>::t;
   const size_t data_b = align_up((size_t)batch * n * n * sizeof(C));
+  const bool flush = l2cold && (size_t)batch * n * n * sizeof(C) < TUNE_FLUSH_BYTES;
+  char* flush_buf = work + data_b + align_up((size_t)n * sizeof(C)) + align_up(sizeof(int));
   std::vector<T> tw;
   twiddles<T>(n, tw);
   C* d = (C*)work;
@@ -1566,12 +1586,13 @@ static int autotune_impl(int n, int batch, int reps, char* work, cudaStream_t st
   const bool tma = make_col_map(&tm, d, n, n, batch, (int)sizeof(C), cols_per_cta<T>());
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return PROP_E_CUDA;
-  const int prec = prec_of<T>(), si = size_index(n);
-  const int rows_saved = g_plan_rows[prec][si].load(), cols_saved = g_plan_cols[prec][si].load();
+  const int prec = prec_of<T>(), si = size_index(n), cl = launch_class(batch);
+  const int rows_saved = g_plan_rows[prec][cl][si].load(), cols_saved = g_plan_cols[prec][cl][si].load();
   int rc = PROP_OK;
   auto time_it = [&](auto&& launch) -> float {
     float best = -1.f;
     for (int r = 0; r < reps + 1 && rc == PROP_OK; ++r) {   // the first run warms up
+      if (flush && cudaMemsetAsync(flush_buf, r & 1, TUNE_FLUSH_BYTES, st) != cudaSuccess) { rc = PROP_E_CUDA; break; }
       if (cudaEventRecord(a, st) != cudaSuccess) { rc = PROP_E_CUDA; break; }
       if (launch() != cudaSuccess) { rc = PROP_E_CUDA; break; }
       if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) { rc = PROP_E_CUDA; break; }
@@ -1584,7 +1605,7 @@ static int autotune_impl(int n, int batch, int reps, char* work, cudaStream_t st
   for (int v = 0; v < 5; ++v) ms[v] = -1.f;
   for (int rv = 0; rv < 2 && rc == PROP_OK; ++rv) {
     if (rv == PROP_ROWS_WARP && !warp_n(n)) continue;
-    g_plan_rows[prec][si].store(rv);
+    g_plan_rows[prec][cl][si].store(rv);
     ms[rv] = time_it([&]() {
       cudaError_t e = rows_fwd<T, C>(g, buf(d, F), buf(d, F), -1, nullptr, batch, st);
       return e != cudaSuccess ? e : rows_inv<T>(g, buf(d, F), buf(d, F), -1, 0, epi(EPI_STORE), batch, st);
@@ -1593,15 +1614,15 @@ static int autotune_impl(int n, int batch, int reps, char* work, cudaStream_t st
   for (int cv = 0; cv < 3 && rc == PROP_OK; ++cv) {
     if (cv == PROP_COLS_WARP && !warp_n(n)) continue;
     if (cv == PROP_COLS_TMA && !tma) continue;
-    g_plan_cols[prec][si].store(cv);
+    g_plan_cols[prec][cl][si].store(cv);
     const ColMaps cm = cv == PROP_COLS_TMA ? ColMaps{&tm, &tm, nullptr, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
     ms[2 + cv] = time_it([&]() {
       return cols<T>(g, buf(d, F), buf(d, F), -1, 1, MUL_SCALE, 1, 0, -1, scale, batch, st,
                      Buf<C>{nullptr, 0, 1}, Buf<C>{nullptr, 0, 1}, cm);
     });
   }
-  g_plan_rows[prec][si].store(rows_saved);
-  g_plan_cols[prec][si].store(cols_saved);
+  g_plan_rows[prec][cl][si].store(rows_saved);
+  g_plan_cols[prec][cl][si].store(cols_saved);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc == PROP_OK) {
@@ -1617,8 +1638,10 @@ extern "C" {
 int prop_get_fft_plan(int32_t n, int32_t precision, prop_fft_plan* out) {
   if (!out || (precision != PROP_FP32 && precision != PROP_FP64)) return PROP_E_ARG;
   if (size_index(n) < 0) return PROP_E_UNSUPPORTED;
-  out->rows = plan_rows(precision, n);
-  out->cols = plan_cols(precision, n);
+  out->rows = plan_rows(precision, n, PROP_FFT_SMALL_ITEMS + 1);
+  out->cols = plan_cols(precision, n, PROP_FFT_SMALL_ITEMS + 1);
+  out->rows_small = plan_rows(precision, n, 1);
+  out->cols_small = plan_cols(precision, n, 1);
   return PROP_OK;
 }
 
@@ -1626,8 +1649,10 @@ int prop_set_fft_plan(int32_t n, int32_t precision, const prop_fft_plan* plan) {
   if (!plan) return PROP_E_ARG;
   if (size_index(n) < 0) return PROP_E_UNSUPPORTED;
   if (!plan_valid(n, precision, *plan)) return PROP_E_UNSUPPORTED;
-  g_plan_rows[precision][size_index(n)].store(plan->rows);
-  g_plan_cols[precision][size_index(n)].store(plan->cols);
+  g_plan_rows[precision][0][size_index(n)].store(plan->rows);
+  g_plan_cols[precision][0][size_index(n)].store(plan->cols);
+  g_plan_rows[precision][1][size_index(n)].store(plan->rows_small);
+  g_plan_cols[precision][1][size_index(n)].store(plan->cols_small);
   return PROP_OK;
 }
 
@@ -1635,25 +1660,33 @@ int prop_fft_autotune_workspace_size(int32_t n, int32_t precision, int32_t batch
   if (!bytes || batch < 1 || (precision != PROP_FP32 && precision != PROP_FP64)) return PROP_E_ARG;
   if (size_index(n) < 0) return PROP_E_UNSUPPORTED;
   const size_t cs = 2 * elem_size(precision);
-  *bytes = align_up((size_t)batch * n * n * cs) + align_up((size_t)n * cs) + align_up(sizeof(int));
+  const size_t data = (size_t)batch * n * n * cs;
+  *bytes = align_up(data) + align_up((size_t)n * cs) + align_up(sizeof(int)) + (data < TUNE_FLUSH_BYTES ? TUNE_FLUSH_BYTES : 0);
   return PROP_OK;
 }
 
-int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps, void* d_work, size_t work_bytes,
-                      void* stream, prop_fft_plan* best, float* ms) {
+int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps, int32_t l2cold, void* d_work,
+                      size_t work_bytes, void* stream, prop_fft_plan* best, float* ms) {
   size_t need;
   int rc = prop_fft_autotune_workspace_size(n, precision, batch, &need);
   if (rc) return rc;
   if (!d_work || !best || !ms || reps < 1 || ((uintptr_t)d_work % ALIGN) != 0) return PROP_E_ARG;
   if (work_bytes < need) return PROP_E_WORKSPACE;
-  rc = precision == PROP_FP64 ? autotune_impl<double>(n, batch, reps, (char*)d_work, (cudaStream_t)stream, ms)
-                              : autotune_impl<float>(n, batch, reps, (char*)d_work, (cudaStream_t)stream, ms);
+  rc = precision == PROP_FP64 ? autotune_impl<double>(n, batch, reps, l2cold, (char*)d_work, (cudaStream_t)stream, ms)
+                              : autotune_impl<float>(n, batch, reps, l2cold, (char*)d_work, (cudaStream_t)stream, ms);
   if (rc) return rc;
-  best->rows = (ms[1] >= 0.f && ms[1] < ms[0]) ? PROP_ROWS_WARP : PROP_ROWS_BLOCK;
-  int bc = -1;
+  // a variant replaces the default (block rows, TMA columns, else plain columns) only
+  // when it is faster by more than TUNE_MARGIN: closer timings are within the run-to-run
+  // spread, and the Arnoldi chain's launches differ from the timed passes
+  constexpr float TUNE_MARGIN = 0.05f;
+  best->rows = (ms[1] >= 0.f && ms[1] < (1.f - TUNE_MARGIN) * ms[0]) ? PROP_ROWS_WARP : PROP_ROWS_BLOCK;
+  const int dflt = ms[2] >= 0.f ? PROP_COLS_TMA : PROP_COLS_PLAIN;
+  int bc = dflt;
   for (int cv = 0; cv < 3; ++cv)
-    if (ms[2 + cv] >= 0.f && (bc < 0 || ms[2 + cv] < ms[2 + bc])) bc = cv;
-  best->cols = bc < 0 ? PROP_COLS_PLAIN : bc;
+    if (ms[2 + cv] >= 0.f && ms[2 + cv] < (1.f - TUNE_MARGIN) * ms[2 + dflt] && ms[2 + cv] < ms[2 + bc]) bc = cv;
+  best->cols = bc;
+  best->rows_small = best->rows;   // the fastest at this batch, for either launch class
+  best->cols_small = best->cols;
   return PROP_OK;
 }
 

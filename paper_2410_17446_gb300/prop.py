@@ -39,8 +39,11 @@ PROP_ROWS_BLOCK, PROP_ROWS_WARP = 0, 1
 PROP_COLS_TMA, PROP_COLS_PLAIN, PROP_COLS_WARP = 0, 1, 2
 
 
+PROP_FFT_SMALL_ITEMS = 2
+
+
 class prop_fft_plan(ct.Structure):
-    _fields_ = [("rows", ct.c_int32), ("cols", ct.c_int32)]
+    _fields_ = [("rows", ct.c_int32), ("cols", ct.c_int32), ("rows_small", ct.c_int32), ("cols_small", ct.c_int32)]
 PROP_PRECOND_FREESPACE, PROP_PRECOND_MEAN = 0, 1
 PROP_FORM_EXPONENTIAL, PROP_FORM_PSEUDODIFF = 0, 1
 PROP_GUESS_CHANNELS = 16
@@ -81,8 +84,8 @@ _SIGS = {
     "prop_get_fft_plan": (ct.c_int, [ct.c_int32, ct.c_int32, ct.POINTER(prop_fft_plan)]),
     "prop_set_fft_plan": (ct.c_int, [ct.c_int32, ct.c_int32, ct.POINTER(prop_fft_plan)]),
     "prop_fft_autotune_workspace_size": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_size_t)]),
-    "prop_fft_autotune": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_size_t,
-                                     ct.c_void_p, ct.POINTER(prop_fft_plan), ct.POINTER(ct.c_float)]),
+    "prop_fft_autotune": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
+                                     ct.c_size_t, ct.c_void_p, ct.POINTER(prop_fft_plan), ct.POINTER(ct.c_float)]),
     "prop_get_e3": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "prop_run": (ct.c_int, [ct.c_void_p, ct.c_int32, MEDIUM_FN, ct.c_void_p]),
     "prop_get_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(prop_stats)]),
@@ -186,8 +189,11 @@ def prop_get_fft_plan(n: int, precision: int) -> prop_fft_plan:
     return p
 
 
-def prop_set_fft_plan(n: int, precision: int, rows: int, cols: int) -> None:
-    p = prop_fft_plan(rows, cols)
+def prop_set_fft_plan(n: int, precision: int, rows: int, cols: int, rows_small: Optional[int] = None,
+                      cols_small: Optional[int] = None) -> None:
+    """Large launches use (rows, cols); launches of at most PROP_FFT_SMALL_ITEMS arrays use
+    (rows_small, cols_small), by default the same."""
+    p = prop_fft_plan(rows, cols, rows if rows_small is None else rows_small, cols if cols_small is None else cols_small)
     check(lib().prop_set_fft_plan(n, precision, ct.byref(p)), "prop_set_fft_plan")
 
 
@@ -197,12 +203,12 @@ def prop_fft_autotune_workspace_size(n: int, precision: int, batch: int) -> int:
     return b.value
 
 
-def prop_fft_autotune(n, precision, batch, reps, d_work, work_bytes, stream=0):
+def prop_fft_autotune(n, precision, batch, reps, d_work, work_bytes, stream=0, l2cold=1):
     """Returns (best plan, times in ms: rows block, rows warp, cols TMA, cols plain, cols warp)."""
     best = prop_fft_plan()
     ms = (ct.c_float * 5)()
-    check(lib().prop_fft_autotune(n, precision, batch, reps, _dptr(d_work), work_bytes, stream, ct.byref(best), ms),
-          "prop_fft_autotune")
+    check(lib().prop_fft_autotune(n, precision, batch, reps, l2cold, _dptr(d_work), work_bytes, stream, ct.byref(best),
+                                  ms), "prop_fft_autotune")
     return best, list(ms)
 
 

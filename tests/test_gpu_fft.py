@@ -55,7 +55,7 @@ def restore_plans(P):
     saved = {(n, p): P.prop_get_fft_plan(n, p) for n in (512, 1024) for p in (P.PROP_FP32, P.PROP_FP64)}
     yield
     for (n, p), pl in saved.items():
-        P.prop_set_fft_plan(n, p, pl.rows, pl.cols)
+        P.prop_set_fft_plan(n, p, pl.rows, pl.cols, pl.rows_small, pl.cols_small)
 
 
 @pytest.mark.parametrize("rows,cols", PLANS)
@@ -92,9 +92,10 @@ def test_plan_validation(P, restore_plans):
     assert e.value.status == P.PROP_E_UNSUPPORTED
     with pytest.raises(P.PropError):
         P.prop_set_fft_plan(100, P.PROP_FP32, P.PROP_ROWS_BLOCK, P.PROP_COLS_TMA)
-    P.prop_set_fft_plan(1024, P.PROP_FP32, P.PROP_ROWS_WARP, P.PROP_COLS_WARP)
+    P.prop_set_fft_plan(1024, P.PROP_FP32, P.PROP_ROWS_WARP, P.PROP_COLS_WARP, P.PROP_ROWS_BLOCK, P.PROP_COLS_PLAIN)
     pl = P.prop_get_fft_plan(1024, P.PROP_FP32)
-    assert (pl.rows, pl.cols) == (P.PROP_ROWS_WARP, P.PROP_COLS_WARP)
+    assert (pl.rows, pl.cols, pl.rows_small, pl.cols_small) == (P.PROP_ROWS_WARP, P.PROP_COLS_WARP,
+                                                                P.PROP_ROWS_BLOCK, P.PROP_COLS_PLAIN)
 
 
 @pytest.mark.parametrize("n", [256, 1024])
@@ -104,12 +105,17 @@ def test_autotuner_times_every_variant(P, restore_plans, n):
     from paper_2410_17446_gb300 import autotune
     before = P.prop_get_fft_plan(n, P.PROP_FP32)
     rec = autotune.tune(n, P.PROP_FP32, reps=2, min_bytes=32 << 20)
+    assert rec["rows_small"] in ("block", "warp") and rec["cols_small"] in ("tma", "plain", "warp")
     after = P.prop_get_fft_plan(n, P.PROP_FP32)
-    assert (before.rows, before.cols) == (after.rows, after.cols)
+    assert (before.rows, before.cols, before.rows_small, before.cols_small) == \
+        (after.rows, after.cols, after.rows_small, after.cols_small)
     assert rec["rows_ms"]["block"] > 0 and rec["cols_ms"]["plain"] > 0 and rec["cols_ms"]["tma"] > 0
     if n == 1024:
         assert rec["rows_ms"]["warp"] > 0 and rec["cols_ms"]["warp"] > 0
         times = {k: v for k, v in rec["cols_ms"].items() if v is not None}
-        assert rec["cols"] == min(times, key=times.get)
+        # the default (TMA) stays unless another variant is more than 5 % faster
+        fastest = min(times, key=times.get)
+        want = fastest if times[fastest] < 0.95 * times["tma"] else "tma"
+        assert rec["cols"] == want
     else:
         assert rec["rows_ms"]["warp"] is None and rec["cols_ms"]["warp"] is None and rec["rows"] == "block"

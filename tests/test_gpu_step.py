@@ -132,7 +132,7 @@ def test_batched_scalar_solutions_satisfy_the_shifted_systems(P, n, plan):
         pr = gpu_propagator(W, "batched_scalar_1024", P.PROP_FP32)
         got = gpu_run(pr, W, 1)[0]
     finally:
-        P.prop_set_fft_plan(n, P.PROP_FP32, saved.rows, saved.cols)
+        P.prop_set_fft_plan(n, P.PROP_FP32, saved.rows, saved.cols, saved.rows_small, saved.cols_small)
     b = W.beams[0]
     w0 = b.w0
     med = ops.Medium(b.medium(0), b.grid.dx, b.grid.dy, W.k0, W.n0, 1)
