@@ -543,8 +543,8 @@ def ours(args) -> None:
                 "rel_err_vs_closed_form": acc,
                 "rel_err_steps": CONFIG_STEPS[args.workload] if acc is not None else None,
                 "legs": legs, "e2e": e2e,
-                "fft_plans": {str(n): {k: r.get(k) for k in ("rows", "cols", "rows_small", "cols_small", "rows_ms",
-                                                              "cols_ms", "rows_ms_small", "cols_ms_small", "source")}
+                "fft_plans": {str(n): {k: r.get(k) for k in ("rows", "cols", "rows_small", "cols_small",
+                                                              "round_trip_ms", "round_trip_ms_small", "source")}
                               for n, r in plans.items()}}
         if args.workload in cpu:
             c = cpu[args.workload]

@@ -249,18 +249,17 @@ int prop_set_fft_plan(int32_t n, int32_t precision, const prop_fft_plan* plan);
 /* Device bytes prop_fft_autotune needs for `batch` n x n arrays (plus 256 MiB to
  * flush L2 between timed runs when the arrays are smaller than that). */
 int prop_fft_autotune_workspace_size(int32_t n, int32_t precision, int32_t batch, size_t* bytes);
-/* Time every variant on `batch` n x n arrays in d_work (256-byte aligned,
- * contents overwritten): a row round trip (forward then inverse rows) per row
- * variant and a column pass (forward, scale, inverse) per column variant, best
- * of `reps` runs after one warm-up, CUDA events on `stream`.  l2cold = 1: L2 is
- * flushed before each run when the data would fit in it (data read from HBM);
- * 0: the data stay in L2 between runs, as the output of one pass stays for the
- * next in a launch chain on few arrays.  ms[5] receives the times in ms (rows
- * block, rows warp, cols TMA, cols plain, cols warp; -1 for a variant that does
- * not exist) and *best the fastest of each pass at this batch (in both the
- * large and the small fields); a variant replaces the default (block rows; TMA
- * columns where tensor maps exist, else plain) only when more than 5 % faster.  Installs nothing (call prop_set_fft_plan) and
- * leaves the current plan unchanged.  Synchronises the stream. */
+/* Time every combination of row and column variant on `batch` n x n arrays in
+ * d_work (256-byte aligned, contents overwritten): one 2-D round trip (forward
+ * rows, column pass with a scale, inverse rows) per combination, best of `reps`
+ * runs after one warm-up, CUDA events on `stream`.  l2cold = 1: L2 is flushed
+ * before each run when the data would fit in it; 0: the data stay in L2 between
+ * runs.  ms[6] receives the times in ms, index 3 rows + cols (rows: block, warp;
+ * cols: TMA, plain, warp; -1 where a variant does not exist), and *best the
+ * fastest (in both the large and the small fields); a combination replaces the
+ * default (block rows with TMA columns, else plain) only when more than 5 %
+ * faster.  Installs nothing (call prop_set_fft_plan) and leaves the current plan
+ * unchanged.  Synchronises the stream. */
 int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps, int32_t l2cold, void* d_work,
                       size_t work_bytes, void* stream, prop_fft_plan* best, float* ms);
 

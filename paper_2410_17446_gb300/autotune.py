@@ -34,21 +34,20 @@ def _time(n: int, precision: int, batch: int, reps: int, l2cold: int):
     stream = torch.cuda.current_stream().cuda_stream
     best, ms = P.prop_fft_autotune(n, precision, batch, reps, work, nb, stream, l2cold)
     del work
-    return best, ({"block": ms[0], "warp": ms[1] if ms[1] >= 0 else None},
-                  {"tma": ms[2] if ms[2] >= 0 else None, "plain": ms[3], "warp": ms[4] if ms[4] >= 0 else None})
+    return best, {f"{ROWS[v // 3]}+{COLS[v % 3]}": ms[v] for v in range(6) if ms[v] >= 0}
 
 
-def tune(n: int, precision: int, reps: int = 5, min_bytes: int = 256 << 20) -> dict:
-    """Time every variant for size n at two launch sizes: a batch of at least
-    `min_bytes` read from HBM (the large class) and a single array left in L2
-    between runs (the small class: the late Arnoldi steps, whose few arrays pass
-    from one kernel to the next through L2); returns the record."""
-    cs = 8 if precision == P.PROP_FP32 else 16
-    batch = max(1 + P.PROP_FFT_SMALL_ITEMS, -(-min_bytes // (n * n * cs)))
-    big, (rows_ms, cols_ms) = _time(n, precision, batch, reps, 1)
-    small, (rows_ms1, cols_ms1) = _time(n, precision, 1, reps, 0)
+def tune(n: int, precision: int, reps: int = 5, batch: int = 16) -> dict:
+    """Time every (rows, cols) combination for size n at two launch sizes: `batch`
+    arrays (the large class: the early Arnoldi steps, all poles iterating) and a
+    single array (the small class: the late steps), the data left in L2 between
+    runs as they pass from one pass to the next in the Arnoldi step; returns the
+    record."""
+    batch = max(1 + P.PROP_FFT_SMALL_ITEMS, batch)
+    big, ms_big = _time(n, precision, batch, reps, 0)
+    small, ms_small = _time(n, precision, 1, reps, 0)
     return {"n": n, "precision": PREC[precision], "batch": batch, "reps": reps,
-            "rows_ms": rows_ms, "cols_ms": cols_ms, "rows_ms_small": rows_ms1, "cols_ms_small": cols_ms1,
+            "round_trip_ms": ms_big, "round_trip_ms_small": ms_small,
             "rows": ROWS[big.rows], "cols": COLS[big.cols],
             "rows_small": ROWS[small.rows], "cols_small": COLS[small.cols]}
 
@@ -80,8 +79,8 @@ def load_or_tune(sizes: Iterable[int], precision: int = P.PROP_FP32, path: Optio
     for n in sorted(set(int(x) for x in sizes)):
         key = f"{PREC[precision]}:{n}"
         rec = None if retune else entry.get(key)
-        if rec is not None and "rows_small" not in rec:
-            rec = None                      # a record from before the small launch class
+        if rec is not None and "round_trip_ms" not in rec:
+            rec = None                      # a record of an earlier tuner
         source = "cache"
         if rec is None:
             rec = tune(n, precision)

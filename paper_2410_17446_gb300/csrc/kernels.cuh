@@ -202,17 +202,17 @@ template <typename T> __device__ __forceinline__ typename Cx<T>::t dbar_of(const
 // Pass 1: forward row DFTs.  grid = (ny/NR, units*ncomp).
 // ---------------------------------------------------------------------------
 template <typename T, int N, int NR, int NT, typename SRC, bool WF>
-__global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
+__device__ __forceinline__ void rows_fwd_body(int bx, int by, int gdx, GV<T> g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, double* norm_acc) {
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int item = item_of(g, (int)blockIdx.y);
+  const int item = item_of(g, (int)by);
   if (item < 0) return;
   const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
-  const int row0 = blockIdx.x * NR;
+  const int row0 = bx * NR;
   const SRC* in = src.at(u, c, g.npts) + (long)row0 * N;
   T acc = 0;
   C* out = dst.at(u, c, g.npts) + (long)row0 * N;
@@ -255,6 +255,11 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
     if (threadIdx.x == 0) atomicAdd(&norm_acc[u], t);
   }
 }
+template <typename T, int N, int NR, int NT, typename SRC, bool WF>
+__global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
+                                                 int mask, double* norm_acc) {
+  rows_fwd_body<T, N, NR, NT, SRC, WF>(blockIdx.x, blockIdx.y, gridDim.x, g, src, dst, mask, norm_acc);
+}
 
 // ---------------------------------------------------------------------------
 // Pass 2: column tile of NV columns: [column DFT] -> multiply -> [inverse column DFT].
@@ -265,19 +270,19 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
 // multiplied spectrum and leave through `dy` (the d/dy branch of the vector
 // operator), transformed in the same shared-memory FFT.
 template <typename T, int NY, int NV, int NT, bool DY>
-__global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
+__device__ __forceinline__ void cols_body(int bx, int by, int gdx, GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                              int mask, int fwd, int mul, int inv, int skip_homog, int pole,
                                              T scale, Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
   using C = typename Cx<T>::t;
   constexpr int W = DY ? 2 * NV : NV;     // tile width in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int item = item_of(g, (int)blockIdx.y);
+  const int item = item_of(g, (int)by);
   if (item < 0) return;
   const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   if (skip_homog && !g.nonhomog[u / g.P]) return;
-  const int x0 = blockIdx.x * NV;
+  const int x0 = bx * NV;
   const C* in = src.at(u, c, g.npts);
   if (mul == MUL_TABLE)   // the multiplier is read after the forward DFT: start its DRAM fetch now
     for (int n = threadIdx.x; n < NY; n += NT) prefetch_l2(g.basemul + (long)n * g.nx + x0);
@@ -349,6 +354,12 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
     }
   }
 }
+template <typename T, int NY, int NV, int NT, bool DY>
+__global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
+                                             int mask, int fwd, int mul, int inv, int skip_homog, int pole,
+                                             T scale, Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
+  cols_body<T, NY, NV, NT, DY>(blockIdx.x, blockIdx.y, gridDim.x, g, src, dst, mask, fwd, mul, inv, skip_homog, pole, scale, spec, dy);
+}
 
 // The column pass with its tiles moved by TMA: one thread issues the tensor
 // loads of the whole NY x NV tile (and of the multiplier tile for MUL_TABLE)
@@ -359,10 +370,10 @@ __global__ void __launch_bounds__(NT) k_cols(GV<T> g, Buf<typename Cx<T>::t> src
 // tile, stored through mdy; it uses the multiplier tile's room (no DY pass
 // multiplies by the table).
 template <typename T, int NY, int NV, int NT, bool DY>
-__global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant__ CUtensorMap msrc,
-                                                 const __grid_constant__ CUtensorMap mdst,
-                                                 const __grid_constant__ CUtensorMap mtab,
-                                                 const __grid_constant__ CUtensorMap mdy, int mask, int fwd, int mul,
+__device__ __forceinline__ void cols_tma_body(int bx, int by, int gdx, GV<T> g, const CUtensorMap& msrc,
+                                                 const CUtensorMap& mdst,
+                                                 const CUtensorMap& mtab,
+                                                 const CUtensorMap& mdy, int mask, int fwd, int mul,
                                                  int inv, int skip_homog, int pole, T scale,
                                                  Buf<typename Cx<T>::t> spec) {
   using C = typename Cx<T>::t;
@@ -377,7 +388,7 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   C* tws = s + NY * NV;                       // twiddles
   C* tab = tws + NY;                          // multiplier tile (MUL_TABLE), or the d/dy tile (DY)
   __shared__ __align__(8) uint64_t bar;
-  const int item = item_of(g, (int)blockIdx.y);
+  const int item = item_of(g, (int)by);
   if (item < 0) return;
   const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
@@ -385,7 +396,7 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
   // once any CTA's copy has failed the step is void: issue no further copies, so
   // the CTAs still to come return at once instead of each waiting out its bound
   if (g.err == nullptr || *reinterpret_cast<volatile const int*>(g.err) != 0) return;
-  const int x0 = blockIdx.x * NV;
+  const int x0 = bx * NV;
   // self-check of the TMA alignment rules: 128-byte shared destinations, 64-byte
   // tensor maps, 16-byte x offsets; on a violation record it and do nothing
   if ((smem_u32(s) & 127u) || (smem_u32(tab) & 127u) || (reinterpret_cast<uintptr_t>(&msrc) & 63u) ||
@@ -473,6 +484,15 @@ __global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant_
     bulk_commit();
     bulk_wait_read();
   }
+}
+template <typename T, int NY, int NV, int NT, bool DY>
+__global__ void __launch_bounds__(NT) k_cols_tma(GV<T> g, const __grid_constant__ CUtensorMap msrc,
+                                                 const __grid_constant__ CUtensorMap mdst,
+                                                 const __grid_constant__ CUtensorMap mtab,
+                                                 const __grid_constant__ CUtensorMap mdy, int mask, int fwd, int mul,
+                                                 int inv, int skip_homog, int pole, T scale,
+                                                 Buf<typename Cx<T>::t> spec) {
+  cols_tma_body<T, NY, NV, NT, DY>(blockIdx.x, blockIdx.y, gridDim.x, g, msrc, mdst, mtab, mdy, mask, fwd, mul, inv, skip_homog, pole, scale, spec);
 }
 
 // The column pass by warps (NY = 512 or 1024): a CTA of 8 warps takes 8 adjacent
@@ -593,20 +613,20 @@ struct EpiArgs {
 // ARN: the instantiation for the EPI_ARNOLDI epilogue (kept apart so that the
 // other epilogues do not carry its register footprint).
 template <typename T, int N, int NR, int NT, bool ARN, bool WF>
-__global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
+__device__ __forceinline__ void rows_inv_body(int bx, int by, int gdx, GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, int skip_homog, EpiArgs ep) {
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int item = item_of(g, (int)blockIdx.y);
+  const int item = item_of(g, (int)by);
   if (item < 0) return;
   const int u = item / g.ncomp, c = item % g.ncomp;
   if (!unit_active(g.st, mask, u)) return;
   const bool sys = (ep.mode == EPI_R0 || ep.mode == EPI_ARNOLDI || ep.mode == EPI_TRUERES || ep.mode == EPI_ADD_E);
   const int beam = sys ? u / g.P : u;
   if (skip_homog && !g.nonhomog[beam]) return;
-  const int row0 = blockIdx.x * NR;
+  const int row0 = bx * NR;
   const long off = (long)row0 * N;
   const C* in = src.at(u, c, g.npts) + off;
   if (ep.mode == EPI_ACCUM64) {   // the old field is read after the inverse DFT: start its DRAM fetch now
@@ -815,6 +835,11 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
   }
   }
 }
+template <typename T, int N, int NR, int NT, bool ARN, bool WF>
+__global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
+                                                 int mask, int skip_homog, EpiArgs ep) {
+  rows_inv_body<T, N, NR, NT, ARN, WF>(blockIdx.x, blockIdx.y, gridDim.x, g, src, dst, mask, skip_homog, ep);
+}
 
 // ---------------------------------------------------------------------------
 // Pass 3 of the vector operator (ncomp = 2), Eq. (Z_bar_eq).  A unit's two
@@ -829,7 +854,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t>
 enum VecEpi { VEPI_ARNOLDI = 0, VEPI_R0 = 1, VEPI_OPDIFF = 2 };
 
 template <typename T, int N, int NR, int NT>
-__global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
+__device__ __forceinline__ void rows_inv_vec_body(int bx, int by, int gdx, GV<T> g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
                                                      Buf<typename Cx<T>::t> out, int mask, int skip_homog,
                                                      int mode, int jj) {
   using C = typename Cx<T>::t;
@@ -838,11 +863,11 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   __shared__ double red[32];
-  const int u = unit_of(g, (int)blockIdx.y);
+  const int u = unit_of(g, (int)by);
   if (u < 0 || !unit_active(g.st, mask, u)) return;
   const int beam = (mode == VEPI_OPDIFF && mask < 0) ? u : u / g.P;
   if (skip_homog && !g.nonhomog[beam]) return;
-  const int row0 = blockIdx.x * NR;
+  const int row0 = bx * NR;
   const long off = (long)row0 * N;
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -928,6 +953,12 @@ __global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>
     if (threadIdx.x == 0) atomicAdd(&g.st[u].z0norm2, t2);
   }
 }
+template <typename T, int N, int NR, int NT>
+__global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
+                                                     Buf<typename Cx<T>::t> out, int mask, int skip_homog,
+                                                     int mode, int jj) {
+  rows_inv_vec_body<T, N, NR, NT>(blockIdx.x, blockIdx.y, gridDim.x, g, A, B, out, mask, skip_homog, mode, jj);
+}
 
 // psi coefficient planes, after psit_xx, psit_yy, psit_xy, psit_x, psit_y have
 // been written into planes 0..4: planes 0, 1 become delta + psit_xx, delta + psit_yy.
@@ -986,11 +1017,11 @@ template <int V, typename A> __device__ __forceinline__ void warp_transpose_redu
 // added to the striped accumulators (planes 2 (j % 2) + 0, 1; slot MMAX of the
 // second takes ||w||^2).
 template <typename T, int NT, int EPT, int GVEC>
-__global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
+__device__ __forceinline__ void dcgs_gram_body(int bx, int by, int gdx, GV<T> g, int jj, int with_w) {
   using C = typename Cx<T>::t;
   constexpr int NW = NT / 32;
   __shared__ double red[NW][4 * (MMAX + 1)];
-  const int s = unit_of(g, (int)blockIdx.y);
+  const int s = unit_of(g, (int)by);
   if (s < 0 || g.st[s].state != ST_ITER) return;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long L = (long)g.ncomp * g.npts;
@@ -998,7 +1029,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   const C* wpv = vslot(g, s, jj + 1);
   for (int t = lane; t < 4 * (jj + 1); t += 32) red[wp][t] = 0.0;   // each warp owns its row
   const long nchunks = (L + NT * EPT - 1) / (NT * EPT);
-  for (long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {   // persistent over chunks
+  for (long chunk = bx; chunk < nchunks; chunk += gdx) {   // persistent over chunks
   const long b0 = chunk * NT * EPT + threadIdx.x;
   C uv[EPT], wv[EPT];
   T uwr = 0, uwi = 0, uu = 0, ww = 0;
@@ -1040,8 +1071,8 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
   }
   }
   __syncthreads();
-  double2* pb = part_at(g.part, s, 2 * (jj & 1), blockIdx.x % NSTRIPE, 0);
-  double2* pa = part_at(g.part, s, 2 * (jj & 1) + 1, blockIdx.x % NSTRIPE, 0);
+  double2* pb = part_at(g.part, s, 2 * (jj & 1), bx % NSTRIPE, 0);
+  double2* pa = part_at(g.part, s, 2 * (jj & 1) + 1, bx % NSTRIPE, 0);
   for (int t = threadIdx.x; t < 4 * (jj + 1); t += NT) {
     double v = 0.0;
 #pragma unroll
@@ -1053,6 +1084,10 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
     else if (i < jj) atomicAdd(&pa[i].y, v);
     else atomicAdd(&pa[MMAX].x, v);   // ||w||^2
   }
+}
+template <typename T, int NT, int EPT, int GVEC>
+__global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
+  dcgs_gram_body<T, NT, EPT, GVEC>(blockIdx.x, blockIdx.y, gridDim.x, g, jj, with_w);
 }
 
 // v_0 *= scale (start of a cycle)
@@ -1617,13 +1652,13 @@ __device__ void dcgs_control(SysState& q, int s, int j, const double2* bs, const
 // grid.x = 1 + sweep CTAs: CTA 0 is the control, CTA x > 0 sweeps chunks
 // x - 1, x - 1 + (gridDim.x - 1), ... (one coefficient prologue per CTA).
 template <typename T, int NT, int EPT, int GVEC>
-__global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
+__device__ __forceinline__ void dcgs_step_body(int bx, int by, int gdx, GV<T> g, int jj, StepArgs A) {
   using C = typename Cx<T>::t;
   __shared__ double2 bs[MMAX + 1], as[MMAX + 1];
   __shared__ double nw_s;
   __shared__ C ca[MMAX + 8], cg[MMAX + 8];
   __shared__ T ir_s;
-  const int s = unit_of(g, (int)blockIdx.y), j = jj, tid = threadIdx.x;
+  const int s = unit_of(g, (int)by), j = jj, tid = threadIdx.x;
   if (s < 0) return;
   SysState& q = g.st[s];
   if (q.state != ST_ITER) return;
@@ -1643,7 +1678,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   }
   __syncthreads();
   // the control goes first in dispatch order, so its FP64 chain overlaps the sweep
-  if (blockIdx.x == 0) { dcgs_control(q, s, j, bs, as, nw_s, g.part, A); return; }
+  if (bx == 0) { dcgs_control(q, s, j, bs, as, nw_s, g.part, A); return; }
   if (j == A.m) return;   // the cycle ends at this step: nothing to sweep
   // coefficients, in the working precision (the sums themselves are FP64)
   if (tid < 32) {
@@ -1680,7 +1715,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
   C* uj = vslot(g, s, jj);
   C* wj = vslot(g, s, jj + 1);
   const long nchunks = (L + NT * EPT - 1) / (NT * EPT);
-  for (long chunk = blockIdx.x - 1; chunk < nchunks; chunk += gridDim.x - 1) {   // persistent over chunks
+  for (long chunk = bx - 1; chunk < nchunks; chunk += gdx - 1) {   // persistent over chunks
   const long b0 = chunk * NT * EPT + tid;
   C qv[EPT], x[EPT];
 #pragma unroll
@@ -1723,6 +1758,10 @@ __global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
     }
   }
   }
+}
+template <typename T, int NT, int EPT, int GVEC>
+__global__ void __launch_bounds__(NT) k_dcgs_step(GV<T> g, int jj, StepArgs A) {
+  dcgs_step_body<T, NT, EPT, GVEC>(blockIdx.x, blockIdx.y, gridDim.x, g, jj, A);
 }
 
 // ---------------------------------------------------------------------------

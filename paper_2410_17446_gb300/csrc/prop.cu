@@ -1602,24 +1602,26 @@ static int autotune_impl(int n, int batch, int reps, int l2cold, char* work, cud
     }
     return best;
   };
-  for (int v = 0; v < 5; ++v) ms[v] = -1.f;
+  // the whole 2-D round trip (forward rows, column pass, inverse rows) for every
+  // combination of row and column variant: the passes hand their data to each
+  // other through L2 as in the Arnoldi step, so they are timed together
+  for (int v = 0; v < 6; ++v) ms[v] = -1.f;
   for (int rv = 0; rv < 2 && rc == PROP_OK; ++rv) {
     if (rv == PROP_ROWS_WARP && !warp_n(n)) continue;
-    g_plan_rows[prec][cl][si].store(rv);
-    ms[rv] = time_it([&]() {
-      cudaError_t e = rows_fwd<T, C>(g, buf(d, F), buf(d, F), -1, nullptr, batch, st);
-      return e != cudaSuccess ? e : rows_inv<T>(g, buf(d, F), buf(d, F), -1, 0, epi(EPI_STORE), batch, st);
-    });
-  }
-  for (int cv = 0; cv < 3 && rc == PROP_OK; ++cv) {
-    if (cv == PROP_COLS_WARP && !warp_n(n)) continue;
-    if (cv == PROP_COLS_TMA && !tma) continue;
-    g_plan_cols[prec][cl][si].store(cv);
-    const ColMaps cm = cv == PROP_COLS_TMA ? ColMaps{&tm, &tm, nullptr, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
-    ms[2 + cv] = time_it([&]() {
-      return cols<T>(g, buf(d, F), buf(d, F), -1, 1, MUL_SCALE, 1, 0, -1, scale, batch, st,
-                     Buf<C>{nullptr, 0, 1}, Buf<C>{nullptr, 0, 1}, cm);
-    });
+    for (int cv = 0; cv < 3 && rc == PROP_OK; ++cv) {
+      if (cv == PROP_COLS_WARP && !warp_n(n)) continue;
+      if (cv == PROP_COLS_TMA && !tma) continue;
+      g_plan_rows[prec][cl][si].store(rv);
+      g_plan_cols[prec][cl][si].store(cv);
+      const ColMaps cm = cv == PROP_COLS_TMA ? ColMaps{&tm, &tm, nullptr, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
+      ms[3 * rv + cv] = time_it([&]() {
+        cudaError_t e = rows_fwd<T, C>(g, buf(d, F), buf(d, F), -1, nullptr, batch, st);
+        if (e == cudaSuccess)
+          e = cols<T>(g, buf(d, F), buf(d, F), -1, 1, MUL_SCALE, 1, 0, -1, scale, batch, st, Buf<C>{nullptr, 0, 1},
+                      Buf<C>{nullptr, 0, 1}, cm);
+        return e != cudaSuccess ? e : rows_inv<T>(g, buf(d, F), buf(d, F), -1, 0, epi(EPI_STORE), batch, st);
+      });
+    }
   }
   g_plan_rows[prec][cl][si].store(rows_saved);
   g_plan_cols[prec][cl][si].store(cols_saved);
@@ -1675,16 +1677,16 @@ int prop_fft_autotune(int32_t n, int32_t precision, int32_t batch, int32_t reps,
   rc = precision == PROP_FP64 ? autotune_impl<double>(n, batch, reps, l2cold, (char*)d_work, (cudaStream_t)stream, ms)
                               : autotune_impl<float>(n, batch, reps, l2cold, (char*)d_work, (cudaStream_t)stream, ms);
   if (rc) return rc;
-  // a variant replaces the default (block rows, TMA columns, else plain columns) only
-  // when it is faster by more than TUNE_MARGIN: closer timings are within the run-to-run
-  // spread, and the Arnoldi chain's launches differ from the timed passes
+  // a combination replaces the default (block rows with TMA columns, else plain columns)
+  // only when it is faster by more than TUNE_MARGIN: closer timings are within the
+  // run-to-run spread
   constexpr float TUNE_MARGIN = 0.05f;
-  best->rows = (ms[1] >= 0.f && ms[1] < (1.f - TUNE_MARGIN) * ms[0]) ? PROP_ROWS_WARP : PROP_ROWS_BLOCK;
-  const int dflt = ms[2] >= 0.f ? PROP_COLS_TMA : PROP_COLS_PLAIN;
-  int bc = dflt;
-  for (int cv = 0; cv < 3; ++cv)
-    if (ms[2 + cv] >= 0.f && ms[2 + cv] < (1.f - TUNE_MARGIN) * ms[2 + dflt] && ms[2 + cv] < ms[2 + bc]) bc = cv;
-  best->cols = bc;
+  const int dflt = ms[PROP_COLS_TMA] >= 0.f ? PROP_COLS_TMA : PROP_COLS_PLAIN;   // row variant block
+  int bv = dflt;
+  for (int v = 0; v < 6; ++v)
+    if (ms[v] >= 0.f && ms[v] < (1.f - TUNE_MARGIN) * ms[dflt] && ms[v] < ms[bv]) bv = v;
+  best->rows = bv / 3;
+  best->cols = bv % 3;
   best->rows_small = best->rows;   // the fastest at this batch, for either launch class
   best->cols_small = best->cols;
   return PROP_OK;

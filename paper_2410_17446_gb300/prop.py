@@ -204,9 +204,9 @@ def prop_fft_autotune_workspace_size(n: int, precision: int, batch: int) -> int:
 
 
 def prop_fft_autotune(n, precision, batch, reps, d_work, work_bytes, stream=0, l2cold=1):
-    """Returns (best plan, times in ms: rows block, rows warp, cols TMA, cols plain, cols warp)."""
+    """Returns (best plan, round-trip times in ms indexed 3 rows + cols)."""
     best = prop_fft_plan()
-    ms = (ct.c_float * 5)()
+    ms = (ct.c_float * 6)()
     check(lib().prop_fft_autotune(n, precision, batch, reps, l2cold, _dptr(d_work), work_bytes, stream, ct.byref(best),
                                   ms), "prop_fft_autotune")
     return best, list(ms)

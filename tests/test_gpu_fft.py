@@ -99,23 +99,23 @@ def test_plan_validation(P, restore_plans):
 
 
 @pytest.mark.parametrize("n", [256, 1024])
-def test_autotuner_times_every_variant(P, restore_plans, n):
-    """prop_fft_autotune times each variant that exists for n, returns the
-    fastest of each pass and leaves the installed plan unchanged."""
+def test_autotuner_times_every_combination(P, restore_plans, n):
+    """prop_fft_autotune times the round trip for each (rows, cols) combination
+    that exists for n, returns the fastest under the 5 % rule and leaves the
+    installed plan unchanged."""
     from paper_2410_17446_gb300 import autotune
     before = P.prop_get_fft_plan(n, P.PROP_FP32)
-    rec = autotune.tune(n, P.PROP_FP32, reps=2, min_bytes=32 << 20)
-    assert rec["rows_small"] in ("block", "warp") and rec["cols_small"] in ("tma", "plain", "warp")
+    rec = autotune.tune(n, P.PROP_FP32, reps=2, batch=4)
     after = P.prop_get_fft_plan(n, P.PROP_FP32)
     assert (before.rows, before.cols, before.rows_small, before.cols_small) == \
         (after.rows, after.cols, after.rows_small, after.cols_small)
-    assert rec["rows_ms"]["block"] > 0 and rec["cols_ms"]["plain"] > 0 and rec["cols_ms"]["tma"] > 0
+    t = rec["round_trip_ms"]
+    assert all(v > 0 for v in t.values())
     if n == 1024:
-        assert rec["rows_ms"]["warp"] > 0 and rec["cols_ms"]["warp"] > 0
-        times = {k: v for k, v in rec["cols_ms"].items() if v is not None}
-        # the default (TMA) stays unless another variant is more than 5 % faster
-        fastest = min(times, key=times.get)
-        want = fastest if times[fastest] < 0.95 * times["tma"] else "tma"
-        assert rec["cols"] == want
+        assert set(t) == {"block+tma", "block+plain", "block+warp", "warp+tma", "warp+plain", "warp+warp"}
     else:
-        assert rec["rows_ms"]["warp"] is None and rec["cols_ms"]["warp"] is None and rec["rows"] == "block"
+        assert set(t) == {"block+tma", "block+plain"} and rec["rows"] == "block"
+    fastest = min(t, key=t.get)
+    want = fastest if t[fastest] < 0.95 * t["block+tma"] else "block+tma"
+    assert f"{rec['rows']}+{rec['cols']}" == want
+    assert rec["rows_small"] in ("block", "warp") and rec["cols_small"] in ("tma", "plain", "warp")
