@@ -315,7 +315,8 @@ class Runner:
         with self.torch.cuda.stream(self.stream):
             pr = P.Propagator.from_table(grids, W.k0, W.n0, W.dz, self.tab, ncomp=W.ncomp, precision=P.PROP_FP32,
                                          restart=self.args.restart or W.restart, stream=self.stream,
-                                         guess=P.PROP_GUESS_LEARNED if guess == "learned" else P.PROP_GUESS_ZERO)
+                                         guess=P.PROP_GUESS_LEARNED if guess == "learned" else P.PROP_GUESS_ZERO,
+                                         multigroup=self.args.multigroup == "on")
             if guess == "learned":
                 net = self.load_net()
                 pr.set_guess_net(net["channels"], net["weights"], net["biases"])
@@ -535,6 +536,8 @@ def ours(args) -> None:
                            "ncomp": W.ncomp, "restart": pr.opts.restart, "tol": pr.opts.tol,
                            "precond": "mean n^2" if pr.opts.precond == P.PROP_PRECOND_MEAN else "free space",
                            "l2": "flushed (256 MiB write) between timed steps",
+                           "grids": len({(b.grid.nx, b.grid.ny, b.grid.dx, b.grid.dy) for b in W.beams}),
+                           "multigroup": args.multigroup,
                            "parallelism": f"replicas x{ws}"},
                 "roofline": d0["roofline"], "gpu_launches": d0["gpu_launches"], "clocks": r0["clk"],
                 "wall_s": r0["wall"],
@@ -573,6 +576,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="shrink the grid (profiling runs only; not a bench line)")
     ap.add_argument("--restart", type=int, default=0, help="GMRES restart length (default: the workload's)")
     ap.add_argument("--retune", action="store_true", help="time the FFT variants here even if plans are cached")
+    ap.add_argument("--multigroup", default="on", choices=["on", "off"],
+                    help="on: grids of different sizes advance in lockstep, one launch per Arnoldi pass")
     ap.add_argument("--guess", default="both", choices=["plain", "both"],
                     help="both: also time the learned initial guess (GMRES to the same tolerance)")
     args = ap.parse_args()

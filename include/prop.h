@@ -99,6 +99,11 @@ typedef struct prop_opts {
                               h k0 n0 (1 + sqrt(1.5 + |zeta_min|)) <= 2.5 on every grid, zeta_min =
                               -((pi/dx)^2 + (pi/dy)^2)/(k0 n0)^2 (inside RK4's stability region on
                               the operator's spectrum) */
+  int32_t multigroup;      /* 1 (default): when a handle holds 2..8 grids, every one of size 128,
+                              256, 384, 512, 768 or 1024 (complex FP32, PROP_FORM_EXPONENTIAL),
+                              prop_step advances all of them in lockstep and each Arnoldi pass is
+                              one kernel launch over every grid; 0: grid by grid.  The results
+                              are the same either way. */
 } prop_opts;
 
 enum prop_precond { PROP_PRECOND_FREESPACE = 0, PROP_PRECOND_MEAN = 1 };

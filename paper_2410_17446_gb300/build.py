@@ -11,8 +11,8 @@ import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
-SRC = [os.path.join(PKG, "csrc", "prop.cu"), os.path.join(PKG, "csrc", "cnn.cu")]
-DEPS = SRC + [os.path.join(PKG, "csrc", f) for f in ("fft.cuh", "kernels.cuh", "tma.cuh")] + [
+SRC = [os.path.join(PKG, "csrc", f) for f in ("prop.cu", "prop_mg.cu", "cnn.cu")]
+DEPS = SRC + [os.path.join(PKG, "csrc", f) for f in ("fft.cuh", "kernels.cuh", "mg.cuh", "tma.cuh")] + [
     os.path.join(ROOT, "include", h) for h in ("prop.h", "prop_cnn.h")]
 LIB = os.path.join(PKG, "libprop.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

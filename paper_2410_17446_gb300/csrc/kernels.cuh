@@ -380,11 +380,11 @@ __device__ __forceinline__ void cols_tma_body(int bx, int by, int gdx, GV<T> g, 
   constexpr int EW = sizeof(C) / 8;           // 8-byte words per element (tensor-map element size)
   constexpr int BR = tma_box_rows(NY);        // rows per TMA box
   static_assert(NY % BR == 0 && BR <= 256, "TMA boxes must tile the column");
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_tma[];
   // TMA writes shared memory at 128-byte aligned addresses: align the tile at
   // run time (the launch reserves 128 bytes of slack)
-  const uint32_t pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
-  C* s = reinterpret_cast<C*>(smem_raw + pad);
+  const uint32_t pad = (128u - (smem_u32(smem_tma) & 127u)) & 127u;
+  C* s = reinterpret_cast<C*>(smem_tma + pad);
   C* tws = s + NY * NV;                       // twiddles
   C* tab = tws + NY;                          // multiplier tile (MUL_TABLE), or the d/dy tile (DY)
   __shared__ __align__(8) uint64_t bar;
@@ -1381,7 +1381,7 @@ __device__ __forceinline__ double conv_threshold(const SysState& q, double tol, 
   return tol * anorm[P + k] * (wn + anorm[k] * (sqrt(q.z0norm2) + sqrt(q.enorm2)));
 }
 
-__global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm2, double tol,
+static __global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm2, double tol,
                               int from, int max_cycles, int first, const double* anorm, int backward) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     SysState& q = st[s];
@@ -1442,7 +1442,7 @@ __device__ __forceinline__ int rp(int row, int col) { return col * (col + 1) / 2
 // (column-oriented: after y_i is known every thread updates its rows), from a
 // shared-memory copy of R; ends the cycle.  Rs must hold columns 0..J-1 packed
 // and acc the right-hand side g[0..J-1].
-__device__ void end_cycle_block(SysState& q, int J, double2* Rs, double2* acc) {
+static __device__ void end_cycle_block(SysState& q, int J, double2* Rs, double2* acc) {
   // One warp, no block barriers: lane l holds rows l and l + 32 (J <= MMAX = 64)
   // and the reciprocals of their diagonal entries; at row i the owner lane forms
   // y_i and broadcasts it, every lane updates its rows above i.
@@ -1476,7 +1476,7 @@ __device__ void end_cycle_block(SysState& q, int J, double2* Rs, double2* acc) {
 // Stage rotated columns 0..J-1 of q.H (column c <= J-1 from global, except that
 // column `own` comes from `owncol`) and g[0..J-1] (g[ownrow..] overridden by
 // gown[]) for end_cycle_block.
-__device__ void stage_ls(const SysState& q, int J, int own, const double2* owncol, int ownrow, const double2* gown,
+static __device__ void stage_ls(const SysState& q, int J, int own, const double2* owncol, int ownrow, const double2* gown,
                          double2* Rs, double2* acc) {
   constexpr int L = MMAX + 1;
   for (int c = 0; c < J; ++c)
@@ -1526,7 +1526,7 @@ struct StepArgs {
   int* counts;   // this iteration's slot: [0] continuing, [1] ending the cycle, [2] flags
 };
 
-__device__ void dcgs_control(SysState& q, int s, int j, const double2* bs, const double2* as, double nw,
+static __device__ void dcgs_control(SysState& q, int s, int j, const double2* bs, const double2* as, double nw,
                              double2* part, const StepArgs& A) {
   constexpr int L = MMAX + 1;
   __shared__ double2 hu[MMAX + 1], col[MMAX + 1], tt[MMAX + 1], sn_s[MMAX], gout[2], gj_s, g0_s, ahb_s;
@@ -1684,8 +1684,8 @@ __device__ __forceinline__ void dcgs_step_body(int bx, int by, int gdx, GV<T> g,
   if (tid < 32) {
     T s2 = 0, hr = 0, hi = 0;
     for (int i = tid; i < j; i += 32) {
-      const T ax = (T)as[i].x, ay = (T)as[i].y, bx = (T)bs[i].x, by = (T)bs[i].y;
-      s2 += ax * ax + ay * ay; hr += ax * bx + ay * by; hi += ax * by - ay * bx;
+      const T ax = (T)as[i].x, ay = (T)as[i].y, br = (T)bs[i].x, bi = (T)bs[i].y;
+      s2 += ax * ax + ay * ay; hr += ax * br + ay * bi; hi += ax * bi - ay * br;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1830,7 +1830,7 @@ __global__ void __launch_bounds__(NT) k_guess_unpack(GV<T> g, const float* out) 
 // than x0 = 0; a guess that does not cut the residual by 10% is dropped (alpha = 0)
 // so that GMRES then runs exactly as without it.  One thread per system computes
 // alpha; the kernel below applies it.
-__global__ void k_guess_alpha(SysState* st, int nsys) {
+static __global__ void k_guess_alpha(SysState* st, int nsys) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     SysState& q = st[s];
     if (q.state != ST_CYCLE_END) continue;
@@ -1876,7 +1876,7 @@ __global__ void __launch_bounds__(NT) k_guess_apply(GV<T> g) {
 }
 
 // After the unpack: every system that received a guess becomes a cycle end.
-__global__ void k_guess_mark(SysState* st, int nsys) {
+static __global__ void k_guess_mark(SysState* st, int nsys) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x)
     if (st[s].state == ST_ITER) { st[s].state = ST_CYCLE_END; st[s].jend = 0; }
 }
@@ -1899,14 +1899,14 @@ __global__ void __launch_bounds__(NT) k_guess_target(GV<T> g, int s, float* tgt)
 }
 
 // zero the per-step accumulators of every system
-__global__ void k_step_reset(SysState* st, int nsys) {
+static __global__ void k_step_reset(SysState* st, int nsys) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     st[s].z0norm2 = 0.0; st[s].nrm_a = 0.0; st[s].enorm2 = 0.0;
   }
 }
 
 // compact per-system statistics for the host
-__global__ void k_collect(const SysState* st, int nsys, int* iters, int* cycles, double* resid, int* flags) {
+static __global__ void k_collect(const SysState* st, int nsys, int* iters, int* cycles, double* resid, int* flags) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     iters[s] = st[s].iters; cycles[s] = st[s].cycles; resid[s] = st[s].resid; flags[s] = st[s].flags;
   }
@@ -1915,7 +1915,7 @@ __global__ void k_collect(const SysState* st, int nsys, int* iters, int* cycles,
 // Self-test of the bounded wait: one thread announces 16 bytes of transaction
 // that no copy will deliver, every thread waits, the wait gives up after its
 // time limit and records the failure in *err.  No copy is ever in flight.
-__global__ void k_selftest_wait(int* err) {
+static __global__ void k_selftest_wait(int* err) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x == 0) { mbar_init(&bar, 1); fence_mbar_init(); }
   __syncthreads();
@@ -1925,7 +1925,7 @@ __global__ void k_selftest_wait(int* err) {
 
 // Compacted list of the systems in state ST_ITER, in index order (one block of
 // a multiple of 32 threads): the Arnoldi launches of a batch cover only these.
-__global__ void k_active_list(const SysState* st, int nsys, int* list) {
+static __global__ void k_active_list(const SysState* st, int nsys, int* list) {
   __shared__ int wsum[32], base;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) base = 0;
@@ -1949,7 +1949,7 @@ __global__ void k_active_list(const SysState* st, int nsys, int* list) {
 }
 
 // counts[0] = systems iterating, counts[1] = at a cycle end, counts[2] = flags
-__global__ void k_count(const SysState* st, int nsys, int* counts) {
+static __global__ void k_count(const SysState* st, int nsys, int* counts) {
   __shared__ int c0, c1, c2;
   if (threadIdx.x == 0) { c0 = 0; c1 = 0; c2 = 0; }
   __syncthreads();

@@ -13,7 +13,7 @@
 // field itself is accumulated in FP64.
 #include "../../include/prop.h"
 #include "../../include/prop_cnn.h"
-#include "kernels.cuh"
+#include "mg.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -102,7 +102,12 @@ constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host read
 // next.  (Two deep was measured on GB300: within 2 % either way on the three
 // benchmark workloads, so the launches stay sized by exact counts.)
 constexpr int PIPE_DEPTH = 1;
-constexpr int ERR_SLOT = 3 * (MMAX + 2) - 1;   // int in the counts area: the asynchronous-copy error word
+// The counts area: MAXG count-slot sets (one per group of a multi-group step; the
+// grid-by-grid step uses set 0), each 3 ints of cycle counts and two parities of
+// SYNC_EVERY step slots of 3 ints, then the asynchronous-copy error word.
+constexpr int CSLOT = 3 + 2 * 3 * SYNC_EVERY;
+constexpr int ERR_SLOT = MAXG * CSLOT;
+constexpr int COUNT_INTS = ERR_SLOT + 1;
 
 struct Layout {
   size_t V, R0, E, Tmp, W64a, W64b, What, Btmp, delta, basemul, ax, ay, pim, twx, twy, st, bnorm2, nonhomog, dsum,
@@ -129,7 +134,7 @@ struct Group {
 }  // namespace
 
 struct prop {
-  int nbeams, P, C, prec, m, max_restarts, precond, form, substeps;
+  int nbeams, P, C, prec, m, max_restarts, precond, form, substeps, multigroup;
   double tol, k0, n0, dz;
   std::vector<cplx> poles, res;
   cplx r0;
@@ -651,38 +656,81 @@ struct Prof {
 // 2 = a TMA kernel's alignment self-check failed (it skipped its work).
 int async_status(int e) { return e == 0 ? PROP_OK : (e == 2 ? PROP_E_WORKSPACE : PROP_E_TIMEOUT); }
 
-int read_counts(prop* h, int* c3) {
-  int buf[3 * (MMAX + 2)];
-  if (cudaMemcpyAsync(buf, h->ws + h->counts_off, sizeof(buf), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+int* count_slots(prop* h, int slot) { return (int*)(h->ws + h->counts_off) + slot * CSLOT; }
+
+// The whole counts area (every slot set and the error word) into buf[COUNT_INTS].
+int read_count_area(prop* h, int* buf) {
+  if (cudaMemcpyAsync(buf, h->ws + h->counts_off, COUNT_INTS * sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
+      cudaSuccess)
     return PROP_E_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PROP_E_CUDA;
   if (!h->pending.empty()) resolve_pending(h);
-  c3[0] = buf[0]; c3[1] = buf[1]; c3[2] = buf[2];
   return async_status(buf[ERR_SLOT]);
 }
 
-template <typename T> int step_group(prop* h, Group& G) {
-  using C = typename Cx<T>::t;
-  GV<T> g = view<T>(h, G);
-  cudaStream_t st = h->stream;
-  const int Cn = h->C, P = h->P, nb = g.nb, nsys = g.nsys, m = h->m;
-  const long F = (long)Cn * g.npts;                       // points of one field
-  const double cs = (double)sizeof(C), pts = (double)g.npts;
-  const T scale = (T)(1.0 / (double)g.npts);
-  int* counts = (int*)(h->ws + h->counts_off);
-  double2* Wn = (double2*)(h->ws + (G.cur == 0 ? G.off.W64b : G.off.W64a));
-  const int tb = 128, tg = (nsys + tb - 1) / tb;
-  const int vb = vec_blocks(F);
-  const int gs_blocks = (int)((F + NT_VEC * EPT_GS - 1) / (NT_VEC * EPT_GS));
-  const int gram_blocks = (int)((F + NT_VEC * EPT_GRAM - 1) / (NT_VEC * EPT_GRAM));
+int read_counts(prop* h, int* c3, int slot) {
+  int buf[COUNT_INTS];
+  const int rc = read_count_area(h, buf);
+  if (rc == PROP_E_CUDA) return rc;
+  c3[0] = buf[slot * CSLOT]; c3[1] = buf[slot * CSLOT + 1]; c3[2] = buf[slot * CSLOT + 2];
+  return rc;
+}
 
-  const ColMaps bmaps = G.tma ? ColMaps{&G.tm_btmp, &G.tm_btmp, &G.tm_tab, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
-  const ColMaps tmaps = G.tma ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr, nullptr} : ColMaps{nullptr, nullptr, nullptr, nullptr};
-  const ColMaps dmaps = G.tma_dy ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr, &G.tm_tmp2} : ColMaps{nullptr, nullptr, nullptr, nullptr};
-  const Buf<C> none{nullptr, 0, 1};
-  int* ulist = (int*)(h->ws + G.off.ulist);
-  GV<T> ga = g;            // the Arnoldi launches of a batch: grid rows = the listed iterating systems
-  ga.ulist = ulist;
+// One group's step, in parts, so that several groups can advance in lockstep:
+// begin() (free-space part, right-hand sides, first count of iterating systems),
+// init() (after that count is read: initial guess, v_0), arnoldi() (the Arnoldi
+// steps of one GMRES cycle, this group alone), cycle_end() (solution update, true
+// residual, restart; count not read) and finish() (residue sum, commit).  The
+// counts go to count-slot set `slot`.
+template <typename T> struct StepGroup {
+  using C = typename Cx<T>::t;
+  prop* h;
+  Group& G;
+  int slot;
+  GV<T> g, ga;             // ga: the Arnoldi launches (grid rows = the listed iterating systems)
+  cudaStream_t st;
+  int Cn, P, nb, nsys, m;
+  long F;                  // points of one field
+  double cs, pts;
+  T scale;
+  int* counts;
+  double2* Wn;             // the new field
+  int tb, tg, vb, gs_blocks, gram_blocks, bw;
+  double breakdown;
+  ColMaps bmaps, tmaps, dmaps;
+  Buf<C> none;
+  int* ulist;
+  int c3[3] = {0, 0, 0};   // last count read: iterating, ending their cycle, flags
+  int n_inh = 0;           // beams with a non-zero delta
+  bool any_used = false;   // some system runs GMRES this step
+  bool done = false;       // the step needed no GMRES (homogeneous medium)
+
+  StepGroup(prop* h_, Group& G_, int slot_) : h(h_), G(G_), slot(slot_) {
+    g = view<T>(h, G);
+    st = h->stream;
+    Cn = h->C; P = h->P; nb = g.nb; nsys = g.nsys; m = h->m;
+    F = (long)Cn * g.npts;
+    cs = (double)sizeof(C); pts = (double)g.npts;
+    scale = (T)(1.0 / (double)g.npts);
+    counts = count_slots(h, slot);
+    Wn = (double2*)(h->ws + (G.cur == 0 ? G.off.W64b : G.off.W64a));
+    tb = 128; tg = (nsys + tb - 1) / tb;
+    vb = vec_blocks(F);
+    gs_blocks = (int)((F + NT_VEC * EPT_GS - 1) / (NT_VEC * EPT_GS));
+    gram_blocks = (int)((F + NT_VEC * EPT_GRAM - 1) / (NT_VEC * EPT_GRAM));
+    bw = h->prec == PROP_FP32 ? 1 : 0;
+    breakdown = sizeof(T) == 4 ? 1e-6 : 1e-14;
+    const ColMaps nomaps{nullptr, nullptr, nullptr, nullptr};
+    bmaps = G.tma ? ColMaps{&G.tm_btmp, &G.tm_btmp, &G.tm_tab, nullptr} : nomaps;
+    tmaps = G.tma ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr, nullptr} : nomaps;
+    dmaps = G.tma_dy ? ColMaps{&G.tm_tmp, &G.tm_tmp, nullptr, &G.tm_tmp2} : nomaps;
+    none = Buf<C>{nullptr, 0, 1};
+    ulist = (int*)(h->ws + G.off.ulist);
+    ga = g;
+    ga.ulist = ulist;
+  }
+
+  int begin() {
   // which beams carry a non-zero delta (read back once per medium change)
   if (G.medium_dirty) {
     G.nonhomog_host.assign(nb, 0);
@@ -690,7 +738,7 @@ template <typename T> int step_group(prop* h, Group& G) {
     CK(cudaStreamSynchronize(st));
     G.medium_dirty = false;
   }
-  int n_inh = 0;
+  n_inh = 0;
   for (int b = 0; b < nb; ++b) n_inh += G.nonhomog_host[b] ? 1 : 0;
 
   // w_hat = FFT2(w); ||w||^2 per beam
@@ -719,7 +767,6 @@ template <typename T> int step_group(prop* h, Group& G) {
     Prof p_(h, K_ROWS_INV, (cs + 32) * pts * nb * Cn);   // read increment, old field (16 B), write new (16 B)
     CK(rows_inv<T>(g, buf(g.Btmp, F), buf(g.Btmp, F), -1, 0, epi(EPI_ACCUM64, 0, nullptr, Wn), nb, st));
   }
-  const int bw = h->prec == PROP_FP32 ? 1 : 0;
   if (n_inh == 0) {           // homogeneous medium: the free-space step is exact, no correction
     if (!G.stats_zero) {      // record zero iterations for every system (once)
       Prof p_(h, K_CONTROL, 0);
@@ -730,6 +777,7 @@ template <typename T> int step_group(prop* h, Group& G) {
     CK(cudaGetLastError());
     G.cur ^= 1;
     G.carry = true;
+    done = true;
     return PROP_OK;
   }
   G.stats_zero = false;
@@ -753,10 +801,11 @@ template <typename T> int step_group(prop* h, Group& G) {
     k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw);
     k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
   CK(cudaGetLastError());
-  int c3[3];
-  int rc = read_counts(h, c3);
-  if (rc) return rc;
-  const bool any_used = c3[0] > 0;
+  return PROP_OK;
+  }
+
+  int init() {
+  any_used = c3[0] > 0;
   if (any_used && h->guess == PROP_GUESS_LEARNED && h->net_layers > 0) {
     // x0 from the network: E = net(R0/rms, delta, p) * rms, then the true residual R0 - (Z - p) E
     // (the cycle-end pass) starts GMRES from it.
@@ -813,7 +862,7 @@ template <typename T> int step_group(prop* h, Group& G) {
     { Prof p_(h, K_CONTROL, 0);
       k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
     CK(cudaGetLastError());
-    rc = read_counts(h, c3);
+    const int rc = read_counts(h, c3, slot);
     if (rc) return rc;
   } else if (any_used) {
     { Prof p_(h, K_INIT, (cs + 16) * pts * c3[0] * Cn);
@@ -821,148 +870,153 @@ template <typename T> int step_group(prop* h, Group& G) {
     { Prof p_(h, K_SCALE, 2 * cs * pts * c3[0] * Cn);
       k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
   }
-  const double breakdown = sizeof(T) == 4 ? 1e-6 : 1e-14;
-  while (c3[0] > 0) {
-    // Steps are launched in batches of SYNC_EVERY between host reads: every
-    // kernel skips systems that have left ST_ITER, so launches past a cycle end
-    // are empty.  Each step's control adds its system to the step's count slot
-    // (continuing, ending the cycle, flags), zeroed at the batch start; the
-    // algorithmic bytes of each launch are charged from these counts exactly.
-    // Step j = m only finalises column m-1: no operator application, and the
-    // Gram sweep forms the products with u alone.
-    // Two batches are kept in flight: batch b+1 is enqueued, sized by the last
-    // count the host has seen (a superset of the iterating systems: systems only
-    // leave), before the host waits for batch b's counts, so the GPU does not idle
-    // while the host reads them.  Each batch has its own count slots (parity).
-    struct Batch { int jj0, nb, par; };
-    Batch fl[2];
-    int nfl = 0, jj = 0, ended = 0, flags = 0;
-    int act_est = c3[0];        // for sizing launches
-    int before = c3[0];         // systems iterating at the next unprocessed step
-    bool stop = false;
-    auto enqueue = [&](int par) -> int {
-      const int jb = jj, nb = std::min(SYNC_EVERY, m + 1 - jj);
-      int* slots = counts + 3 + par * 3 * SYNC_EVERY;
-      CK(cudaMemsetAsync(slots, 0, 3 * SYNC_EVERY * sizeof(int), st));
-      { Prof p_(h, K_CONTROL, 0);
-        k_active_list<<<1, 256, 0, st>>>(g.st, nsys, ulist); }
-      const int act = std::max(act_est, 1);
-      for (int j = jb; j < jb + nb; ++j) {
-        const bool op = j < m;
-        if (op) {
-          C* Vj = g.V + (long)j * F;
-          const long vs = (long)(m + 2) * F;
-          { Prof p_(h, K_ROWS_FWD, 0);
-            CK(rows_fwd<T, C>(ga, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, act, st)); }
-          if (Cn == 2) {
-            { Prof p_(h, K_COLS, 0);
-              CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act, st,
-                         Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
-            { Prof p_(h, K_ROWS_INV, 0);
-              CK(rows_inv_vec<T>(ga, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, j, act,
-                                 st)); }
-          } else {
-            { Prof p_(h, K_COLS, 0);
-              CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act, st, none,
-                         none, tmaps)); }
-            { Prof p_(h, K_ROWS_INV, 0);
-              CK(rows_inv<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, j), act, st)); }
-          }
+  return PROP_OK;
+  }
+
+  int arnoldi() {
+  // Steps are launched in batches of SYNC_EVERY between host reads: every
+  // kernel skips systems that have left ST_ITER, so launches past a cycle end
+  // are empty.  Each step's control adds its system to the step's count slot
+  // (continuing, ending the cycle, flags), zeroed at the batch start; the
+  // algorithmic bytes of each launch are charged from these counts exactly.
+  // Step j = m only finalises column m-1: no operator application, and the
+  // Gram sweep forms the products with u alone.
+  // Two batches are kept in flight: batch b+1 is enqueued, sized by the last
+  // count the host has seen (a superset of the iterating systems: systems only
+  // leave), before the host waits for batch b's counts, so the GPU does not idle
+  // while the host reads them.  Each batch has its own count slots (parity).
+  struct Batch { int jj0, nb, par; };
+  Batch fl[2];
+  int nfl = 0, jj = 0, ended = 0, flags = 0;
+  int act_est = c3[0];        // for sizing launches
+  int before = c3[0];         // systems iterating at the next unprocessed step
+  bool stop = false;
+  auto enqueue = [&](int par) -> int {
+    const int jb = jj, nb = std::min(SYNC_EVERY, m + 1 - jj);
+    int* slots = counts + 3 + par * 3 * SYNC_EVERY;
+    CK(cudaMemsetAsync(slots, 0, 3 * SYNC_EVERY * sizeof(int), st));
+    { Prof p_(h, K_CONTROL, 0);
+      k_active_list<<<1, 256, 0, st>>>(g.st, nsys, ulist); }
+    const int act = std::max(act_est, 1);
+    for (int j = jb; j < jb + nb; ++j) {
+      const bool op = j < m;
+      if (op) {
+        C* Vj = g.V + (long)j * F;
+        const long vs = (long)(m + 2) * F;
+        { Prof p_(h, K_ROWS_FWD, 0);
+          CK(rows_fwd<T, C>(ga, buf(Vj, vs), buf(g.Tmp, F), ST_ITER, nullptr, act, st)); }
+        if (Cn == 2) {
+          { Prof p_(h, K_COLS, 0);
+            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act, st,
+                       Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
+          { Prof p_(h, K_ROWS_INV, 0);
+            CK(rows_inv_vec<T>(ga, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.Tmp, F), ST_ITER, 0, VEPI_ARNOLDI, j, act,
+                               st)); }
+        } else {
+          { Prof p_(h, K_COLS, 0);
+            CK(cols<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 1, MUL_PREC_INV, 1, 0, -1, scale, act, st, none,
+                       none, tmaps)); }
+          { Prof p_(h, K_ROWS_INV, 0);
+            CK(rows_inv<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, j), act, st)); }
         }
-        // sweeps: about one wave of CTAs (4 resident per SM) shared by the act systems
-        const int cap = std::max(1, 4 * sm_count() / act);
-        { Prof p_(h, K_GRAM, 0);
-          k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>
-              <<<dim3(std::min(gram_blocks, cap), act), NT_VEC, 0, st>>>(ga, j, op ? 1 : 0); }
-        { Prof p_(h, K_GS_UPDATE, 0);
-          StepArgs sa;
-          sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
-          sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = slots + 3 * (j - jb);
-          k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS><<<dim3(std::min(gs_blocks, cap) + 1, act), NT_VEC, 0, st>>>(ga, j, sa); }
-        CK(cudaGetLastError());
       }
-      CK(cudaMemcpyAsync(h->hcounts + par * 3 * SYNC_EVERY, slots, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaEventRecord(h->batch_ev[par], st));
-      fl[nfl++] = Batch{jb, nb, par};
-      jj += nb;
-      return PROP_OK;
-    };
-    int next_par = 0;
-    while (true) {
-      while (!stop && jj <= m && nfl < PIPE_DEPTH) {
-        const int rc2 = enqueue(next_par);
-        if (rc2) return rc2;
-        next_par ^= 1;
-      }
-      if (nfl == 0) break;
-      // the oldest batch's counts
-      const Batch bt = fl[0];
-      fl[0] = fl[1];
-      --nfl;
-      if (cudaEventSynchronize(h->batch_ev[bt.par]) != cudaSuccess) return PROP_E_CUDA;
-      if (!h->pending.empty()) resolve_pending(h);
-      const int* hc = h->hcounts + bt.par * 3 * SYNC_EVERY;
-      for (int b2 = 0; b2 < bt.nb; ++b2) {
-        const int j = bt.jj0 + b2;
-        const double act = (double)before * Cn * pts;
-        if (j < m) {
-          h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
-          h->k_bytes[K_COLS] += (Cn == 2 ? 3 : 2) * cs * act;
-          h->k_bytes[K_ROWS_INV] += (Cn == 2 ? 6.5 : 4.0) * cs * act;
-          h->k_bytes[K_GS_UPDATE] += (j + 4.0) * cs * act;   // v_0..v_{j-1}, u, w read; q_j, u_{j+1} written
-        }
-        h->k_bytes[K_GRAM] += (j + (j < m ? 2.0 : 1.0)) * cs * act;   // v_0..v_{j-1}, u (and w) read
-        if (j >= 1) h->total_iters += before;               // column j-1 finalised for each of them
-        const int* sl = hc + 3 * b2;
-        ended += sl[1];
-        flags |= sl[2];
-        before = sl[0];
-      }
-      act_est = before;
-      if (before == 0) stop = true;   // any batch still in flight is empty (every launch masked)
+      // sweeps: about one wave of CTAs (4 resident per SM) shared by the act systems
+      const int cap = std::max(1, 4 * sm_count() / act);
+      { Prof p_(h, K_GRAM, 0);
+        k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>
+            <<<dim3(std::min(gram_blocks, cap), act), NT_VEC, 0, st>>>(ga, j, op ? 1 : 0); }
+      { Prof p_(h, K_GS_UPDATE, 0);
+        StepArgs sa;
+        sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
+        sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = slots + 3 * (j - jb);
+        k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS><<<dim3(std::min(gs_blocks, cap) + 1, act), NT_VEC, 0, st>>>(ga, j, sa); }
+      CK(cudaGetLastError());
     }
-    c3[0] = 0; c3[1] = ended; c3[2] = flags;
-    if (c3[1] == 0) break;
-    // cycle end: e += M^-1 (V y) (Tmp = V y, then a free-space solve round trip
-    // accumulating into E); true residual r = R0 - (Z - p) e
-    const double endp = (double)c3[1] * Cn * pts;
-    { Prof p_(h, K_COMBINE, (1 + m) * cs * endp);   // upper bound on the v_i read: J <= m
-      k_combine<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
-    { Prof p_(h, K_ROWS_FWD, 2 * cs * endp);
-      CK(rows_fwd<T, C>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
-    { Prof p_(h, K_COLS, 2 * cs * endp);
-      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_PREC_INV, 1, 0, -1, scale, nsys, st, none, none,
-                 tmaps)); }
-    { Prof p_(h, K_ROWS_INV, (cs + 32) * endp);
-      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_ADD_E), nsys, st)); }
-    if (Cn == 2) {   // (Z - Z_fs) e into v_0, from a derivative round trip of e
-      { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
-        CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
-      { Prof p_(h, K_COLS, 3 * cs * endp);
-        CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
-                   Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
-      { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
-        CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 2) * F), ST_CYCLE_END, 0,
-                           VEPI_OPDIFF, 0, nsys, st)); }
+    CK(cudaMemcpyAsync(h->hcounts + par * 3 * SYNC_EVERY, slots, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->batch_ev[par], st));
+    fl[nfl++] = Batch{jb, nb, par};
+    jj += nb;
+    return PROP_OK;
+  };
+  int next_par = 0;
+  while (true) {
+    while (!stop && jj <= m && nfl < PIPE_DEPTH) {
+      const int rc2 = enqueue(next_par);
+      if (rc2) return rc2;
+      next_par ^= 1;
     }
+    if (nfl == 0) break;
+    // the oldest batch's counts
+    const Batch bt = fl[0];
+    fl[0] = fl[1];
+    --nfl;
+    if (cudaEventSynchronize(h->batch_ev[bt.par]) != cudaSuccess) return PROP_E_CUDA;
+    if (!h->pending.empty()) resolve_pending(h);
+    const int* hc = h->hcounts + bt.par * 3 * SYNC_EVERY;
+    for (int b2 = 0; b2 < bt.nb; ++b2) {
+      const int j = bt.jj0 + b2;
+      const double act = (double)before * Cn * pts;
+      if (j < m) {
+        h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
+        h->k_bytes[K_COLS] += (Cn == 2 ? 3 : 2) * cs * act;
+        h->k_bytes[K_ROWS_INV] += (Cn == 2 ? 6.5 : 4.0) * cs * act;
+        h->k_bytes[K_GS_UPDATE] += (j + 4.0) * cs * act;   // v_0..v_{j-1}, u, w read; q_j, u_{j+1} written
+      }
+      h->k_bytes[K_GRAM] += (j + (j < m ? 2.0 : 1.0)) * cs * act;   // v_0..v_{j-1}, u (and w) read
+      if (j >= 1) h->total_iters += before;               // column j-1 finalised for each of them
+      const int* sl = hc + 3 * b2;
+      ended += sl[1];
+      flags |= sl[2];
+      before = sl[0];
+    }
+    act_est = before;
+    if (before == 0) stop = true;   // any batch still in flight is empty (every launch masked)
+  }
+  c3[0] = 0; c3[1] = ended; c3[2] = flags;
+  return PROP_OK;
+  }
+
+  int cycle_end() {
+  // cycle end: e += M^-1 (V y) (Tmp = V y, then a free-space solve round trip
+  // accumulating into E); true residual r = R0 - (Z - p) e
+  const double endp = (double)c3[1] * Cn * pts;
+  { Prof p_(h, K_COMBINE, (1 + m) * cs * endp);   // upper bound on the v_i read: J <= m
+    k_combine<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+  { Prof p_(h, K_ROWS_FWD, 2 * cs * endp);
+    CK(rows_fwd<T, C>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
+  { Prof p_(h, K_COLS, 2 * cs * endp);
+    CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_PREC_INV, 1, 0, -1, scale, nsys, st, none, none,
+               tmaps)); }
+  { Prof p_(h, K_ROWS_INV, (cs + 32) * endp);
+    CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_ADD_E), nsys, st)); }
+  if (Cn == 2) {   // (Z - Z_fs) e into v_0, from a derivative round trip of e
     { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
       CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
-    { Prof p_(h, K_COLS, 2 * cs * endp);
-      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st, none, none,
-                 tmaps)); }
-    { Prof p_(h, K_ROWS_INV, (4 * cs + 16) * endp);
-      CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st)); }
-    { Prof p_(h, K_CONTROL, 0);
-      k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw); }
-    { Prof p_(h, K_SCALE, 0);
-      k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
-    { Prof p_(h, K_CONTROL, 0);
-      k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
-    CK(cudaGetLastError());
-    rc = read_counts(h, c3);
-    if (rc) return rc;
-    h->k_bytes[K_SCALE] += 2 * cs * pts * Cn * c3[0];
+    { Prof p_(h, K_COLS, 3 * cs * endp);
+      CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_SCALE, 1, 0, -1, scale, nsys, st,
+                 Buf<C>{nullptr, 0, 1}, buf(g.Tmp2, F), dmaps)); }
+    { Prof p_(h, K_ROWS_INV, 5.5 * cs * endp);
+      CK(rows_inv_vec<T>(g, buf(g.Tmp, F), buf(g.Tmp2, F), buf(g.V, (long)(m + 2) * F), ST_CYCLE_END, 0,
+                         VEPI_OPDIFF, 0, nsys, st)); }
   }
+  { Prof p_(h, K_ROWS_FWD, (16 + cs) * endp);
+    CK(rows_fwd<T, double2>(g, buf(g.E, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
+  { Prof p_(h, K_COLS, 2 * cs * endp);
+    CK(cols<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 1, MUL_POLE_FWD, 1, 0, -1, scale, nsys, st, none, none,
+               tmaps)); }
+  { Prof p_(h, K_ROWS_INV, (4 * cs + 16) * endp);
+    CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st)); }
+  { Prof p_(h, K_CONTROL, 0);
+    k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw); }
+  { Prof p_(h, K_SCALE, 0);
+    k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+  { Prof p_(h, K_CONTROL, 0);
+    k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
+  CK(cudaGetLastError());
+  return PROP_OK;
+  }
+
+  int finish() {
   if (c3[2] & 1) return PROP_E_NAN;
   if (c3[2] & 2) return PROP_E_NOCONV;
   if (any_used) {
@@ -971,6 +1025,200 @@ template <typename T> int step_group(prop* h, Group& G) {
   }
   CK(cudaGetLastError());
   G.cur ^= 1;   // commit: the new field becomes current
+  return PROP_OK;
+  }
+};
+
+template <typename T> int step_group(prop* h, Group& G) {
+  StepGroup<T> S(h, G, 0);
+  int rc = S.begin();
+  if (rc || S.done) return rc;
+  rc = read_counts(h, S.c3, 0);
+  if (rc) return rc;
+  rc = S.init();
+  if (rc) return rc;
+  while (S.c3[0] > 0) {
+    rc = S.arnoldi();
+    if (rc) return rc;
+    if (S.c3[1] == 0) break;
+    rc = S.cycle_end();
+    if (rc) return rc;
+    rc = read_counts(h, S.c3, 0);
+    if (rc) return rc;
+    h->k_bytes[K_SCALE] += 2 * S.cs * S.pts * S.Cn * S.c3[0];
+  }
+  return S.finish();
+}
+
+// ---------------------------------------------------------------------------
+// Multi-group step: every group of the handle in lockstep, each Arnoldi pass one
+// launch over all groups (mg.cuh).  Complex FP32, 2..MAXG groups, every grid of a
+// size the multi-group kernels take.  Begin, init, cycle end and finish are each
+// group's own (StepGroup); their counts are read for all groups at once.
+// ---------------------------------------------------------------------------
+bool multigroup_ok(const prop* h) {
+  if (!h->multigroup || h->prec != PROP_FP32 || h->form != PROP_FORM_EXPONENTIAL) return false;
+  const int ng = (int)h->groups.size();
+  if (ng < 2 || ng > MAXG) return false;
+  for (const Group& G : h->groups) {
+    if (!mg_size(G.nx) || !mg_size(G.ny)) return false;
+    if (G.ny % mg_nr(G.nx) != 0 || G.ny % mg_nrv(G.nx) != 0) return false;
+  }
+  return true;
+}
+
+// The Arnoldi steps of one GMRES cycle of every live group; afterwards each live
+// group's c3 = {0, systems that ended the cycle, flags}.
+int arnoldi_multigroup(prop* h, std::vector<StepGroup<float>>& S, const std::vector<char>& live) {
+  const int ng = (int)S.size(), m = h->m;
+  cudaStream_t st = h->stream;
+  int before[MAXG], ended[MAXG], flags[MAXG];
+  for (int i = 0; i < ng; ++i) { before[i] = live[i] ? S[i].c3[0] : 0; ended[i] = 0; flags[i] = 0; }
+  MGroups mg;
+  std::memset(&mg, 0, sizeof(mg));
+  int jj = 0;
+  while (jj <= m) {
+    int idx[MAXG], n = 0;
+    for (int i = 0; i < ng; ++i)
+      if (before[i] > 0) idx[n++] = i;
+    if (n == 0) break;
+    const int jb = jj, nbt = std::min(SYNC_EVERY, m + 1 - jj);
+    mg.ng = n;
+    mg.nzero = 3 * SYNC_EVERY;
+    for (int k = 0; k < n; ++k) {
+      StepGroup<float>& s = S[idx[k]];
+      mg.g[k] = s.ga;
+      const bool vec = s.Cn == 2;
+      mg.tma[k] = vec ? (s.G.tma_dy ? 1 : 0) : (s.G.tma ? 1 : 0);
+      mg.tm[k] = s.G.tm_tmp;
+      mg.tm2[k] = s.G.tm_tmp2;
+      mg.zero[k] = s.counts + 3;
+      StepArgs& sa = mg.sa[k];
+      sa.m = m; sa.P = s.P; sa.backward = s.bw; sa.tol = h->tol; sa.breakdown = s.breakdown;
+      sa.bnorm2 = s.g.bnorm2; sa.anorm = s.g.anorm; sa.counts = nullptr;
+    }
+    // sweeps: about one wave of CTAs (4 resident per SM) shared by every listed
+    // system in proportion to its points, so that every CTA sweeps about as much
+    double work = 0;
+    for (int k = 0; k < n; ++k) work += (double)before[idx[k]] * S[idx[k]].F;
+    int cap[MAXG];
+    for (int k = 0; k < n; ++k)
+      cap[k] = std::max(1, (int)(4.0 * sm_count() * (double)S[idx[k]].F / std::max(work, 1.0)));
+    auto layout = [&](int pass) {
+      int c = 0;
+      for (int k = 0; k < n; ++k) {
+        mg.c0[k] = c;
+        mg.gx[k] = mg_gx(pass, mg.g[k], before[idx[k]], cap[k]);
+        c += mg.gx[k] * mg_rows(pass, mg.g[k], before[idx[k]]);
+      }
+      mg.c0[n] = c;
+    };
+    { Prof p_(h, K_CONTROL, 0);
+      CK(mg_launch(MG_ACTIVE, mg, 0, 0, st)); }
+    for (int j = jb; j < jb + nbt; ++j) {
+      const bool op = j < m;
+      if (op) {
+        layout(MG_ROWS_FWD);
+        { Prof p_(h, K_ROWS_FWD, 0);
+          CK(mg_launch(MG_ROWS_FWD, mg, j, 0, st)); }
+        layout(MG_COLS);
+        { Prof p_(h, K_COLS, 0);
+          CK(mg_launch(MG_COLS, mg, j, 0, st)); }
+        layout(MG_ROWS_INV);
+        { Prof p_(h, K_ROWS_INV, 0);
+          CK(mg_launch(MG_ROWS_INV, mg, j, 0, st)); }
+      }
+      layout(MG_GRAM);
+      { Prof p_(h, K_GRAM, 0);
+        CK(mg_launch(MG_GRAM, mg, j, op ? 1 : 0, st)); }
+      for (int k = 0; k < n; ++k) mg.sa[k].counts = S[idx[k]].counts + 3 + 3 * (j - jb);
+      layout(MG_STEP);
+      { Prof p_(h, K_GS_UPDATE, 0);
+        CK(mg_launch(MG_STEP, mg, j, 0, st)); }
+    }
+    CK(cudaMemcpyAsync(h->hcounts, h->ws + h->counts_off, COUNT_INTS * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(h->batch_ev[0], st));
+    if (cudaEventSynchronize(h->batch_ev[0]) != cudaSuccess) return PROP_E_CUDA;
+    if (!h->pending.empty()) resolve_pending(h);
+    // algorithmic bytes charged from the counts, as in the grid-by-grid step
+    for (int k = 0; k < n; ++k) {
+      const int i = idx[k];
+      const StepGroup<float>& s = S[i];
+      const int* hc = h->hcounts + i * CSLOT + 3;
+      const double cs = s.cs, Cn = s.Cn;
+      for (int b2 = 0; b2 < nbt; ++b2) {
+        const int j = jb + b2;
+        const double act = (double)before[i] * Cn * s.pts;
+        if (j < m) {
+          h->k_bytes[K_ROWS_FWD] += 2 * cs * act;
+          h->k_bytes[K_COLS] += (Cn == 2 ? 3 : 2) * cs * act;
+          h->k_bytes[K_ROWS_INV] += (Cn == 2 ? 6.5 : 4.0) * cs * act;
+          h->k_bytes[K_GS_UPDATE] += (j + 4.0) * cs * act;
+        }
+        h->k_bytes[K_GRAM] += (j + (j < m ? 2.0 : 1.0)) * cs * act;
+        if (j >= 1) h->total_iters += before[i];
+        const int* sl = hc + 3 * b2;
+        ended[i] += sl[1];
+        flags[i] |= sl[2];
+        before[i] = sl[0];
+      }
+    }
+    jj += nbt;
+  }
+  for (int i = 0; i < ng; ++i)
+    if (live[i]) { S[i].c3[0] = 0; S[i].c3[1] = ended[i]; S[i].c3[2] = flags[i]; }
+  return PROP_OK;
+}
+
+int step_multigroup(prop* h) {
+  const int ng = (int)h->groups.size();
+  std::vector<StepGroup<float>> S;
+  S.reserve(ng);
+  for (int i = 0; i < ng; ++i) S.emplace_back(h, h->groups[i], i);
+  bool any = false;
+  for (StepGroup<float>& s : S) {
+    const int rc = s.begin();
+    if (rc) return rc;
+    any = any || !s.done;
+  }
+  if (!any) return PROP_OK;
+  int buf[COUNT_INTS];
+  int rc = read_count_area(h, buf);
+  if (rc) return rc;
+  std::vector<char> live(ng, 0);
+  for (int i = 0; i < ng; ++i) {
+    if (S[i].done) continue;
+    for (int t = 0; t < 3; ++t) S[i].c3[t] = buf[i * CSLOT + t];
+    rc = S[i].init();
+    if (rc) return rc;
+    live[i] = S[i].c3[0] > 0;
+  }
+  while (std::find(live.begin(), live.end(), 1) != live.end()) {
+    rc = arnoldi_multigroup(h, S, live);
+    if (rc) return rc;
+    bool any_end = false;
+    for (int i = 0; i < ng; ++i) {
+      if (!live[i]) continue;
+      if (S[i].c3[1] == 0) { live[i] = 0; continue; }
+      rc = S[i].cycle_end();
+      if (rc) return rc;
+      any_end = true;
+    }
+    if (!any_end) break;
+    rc = read_count_area(h, buf);
+    if (rc) return rc;
+    for (int i = 0; i < ng; ++i) {
+      if (!live[i]) continue;
+      for (int t = 0; t < 3; ++t) S[i].c3[t] = buf[i * CSLOT + t];
+      h->k_bytes[K_SCALE] += 2 * S[i].cs * S[i].pts * S[i].Cn * S[i].c3[0];
+      live[i] = S[i].c3[0] > 0;
+    }
+  }
+  for (StepGroup<float>& s : S) {
+    if (s.done) continue;
+    rc = s.finish();
+    if (rc) return rc;
+  }
   return PROP_OK;
 }
 
@@ -1052,6 +1300,7 @@ int validate_opts(const prop_opts* o) {
   if (o->precond != PROP_PRECOND_FREESPACE && o->precond != PROP_PRECOND_MEAN) return PROP_E_ARG;
   if (o->form != PROP_FORM_EXPONENTIAL && o->form != PROP_FORM_PSEUDODIFF) return PROP_E_ARG;
   if (o->substeps < 0 || o->substeps > 100000) return PROP_E_ARG;
+  if (o->multigroup != 0 && o->multigroup != 1) return PROP_E_ARG;
   return PROP_OK;
 }
 
@@ -1089,7 +1338,7 @@ size_t total_layout(std::vector<Group>& groups, int P, int C, int m, int prec, i
   for (Group& G : groups) o = carve(G, o, P, C, m, prec, guess, form);
   *net_off = align_up(o);
   *counts_off = align_up(*net_off + NET_W_BYTES + NET_B_BYTES);
-  return *counts_off + align_up(3 * (MMAX + 2) * sizeof(int));
+  return *counts_off + align_up(COUNT_INTS * sizeof(int));
 }
 
 }  // namespace
@@ -1113,6 +1362,7 @@ int prop_default_opts(prop_opts* o, int32_t ncomp, int32_t precision) {
   o->precond = PROP_PRECOND_MEAN;
   o->form = PROP_FORM_EXPONENTIAL;
   o->substeps = 0;
+  o->multigroup = 1;
   return PROP_OK;
 }
 
@@ -1144,7 +1394,7 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   if (!h) return PROP_E_ARG;
   h->nbeams = nbeams; h->P = npoles; h->C = opts->ncomp; h->prec = opts->precision; h->m = opts->restart;
   h->max_restarts = opts->max_restarts; h->tol = opts->tol; h->precond = opts->precond;
-  h->form = opts->form; h->substeps = opts->substeps; h->k0 = k0; h->n0 = n0; h->dz = dz;
+  h->form = opts->form; h->substeps = opts->substeps; h->multigroup = opts->multigroup; h->k0 = k0; h->n0 = n0; h->dz = dz;
   h->poles.resize(npoles); h->res.resize(npoles);
   for (int k = 0; k < npoles; ++k) {
     h->poles[k] = cplx(poles[2 * k], poles[2 * k + 1]);
@@ -1177,7 +1427,7 @@ int prop_create(int32_t nbeams, const prop_grid* grids, double k0, double n0, do
   for (int k = 0; k < PROP_NKINDS; ++k) { h->k_launches[k] = 0; h->k_ms[k] = 0.0; h->k_bytes[k] = 0.0; }
   h->hcounts = nullptr;
   h->batch_ev[0] = h->batch_ev[1] = nullptr;
-  if (cudaHostAlloc((void**)&h->hcounts, 2 * 3 * SYNC_EVERY * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+  if (cudaHostAlloc((void**)&h->hcounts, COUNT_INTS * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->batch_ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->batch_ev[1], cudaEventDisableTiming) != cudaSuccess) {
     prop_destroy(h);
@@ -1339,6 +1589,12 @@ int prop_get_substeps(prop* h, int32_t* substeps) {
 
 int prop_step(prop* h) {
   if (!h) return PROP_E_ARG;
+  if (multigroup_ok(h)) {
+    const int rc = step_multigroup(h);
+    if (rc) { h->last_status = rc; return rc; }
+    h->steps += 1;
+    return PROP_OK;
+  }
   for (Group& G : h->groups) {
     int rc;
     if (h->form == PROP_FORM_PSEUDODIFF) rc = h->prec == PROP_FP64 ? rk4_group<double>(h, G) : rk4_group<float>(h, G);

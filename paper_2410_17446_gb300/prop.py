@@ -31,7 +31,8 @@ class prop_grid(ct.Structure):
 class prop_opts(ct.Structure):
     _fields_ = [("ncomp", ct.c_int32), ("precision", ct.c_int32), ("restart", ct.c_int32),
                 ("max_restarts", ct.c_int32), ("tol", ct.c_double), ("guess", ct.c_int32),
-                ("precond", ct.c_int32), ("form", ct.c_int32), ("substeps", ct.c_int32)]
+                ("precond", ct.c_int32), ("form", ct.c_int32), ("substeps", ct.c_int32),
+                ("multigroup", ct.c_int32)]
 
 
 PROP_GUESS_ZERO, PROP_GUESS_LEARNED = 0, 1
@@ -223,7 +224,8 @@ class Propagator:
     def __init__(self, grids, k0: float, n0: float, dz: float, poles, residues, r0,
                  ncomp: int = 1, precision: int = PROP_FP32, restart: int = 20, max_restarts: Optional[int] = None,
                  tol: Optional[float] = None, device: str = "cuda", stream=None, guess: int = PROP_GUESS_ZERO,
-                 precond: Optional[int] = None, form: int = PROP_FORM_EXPONENTIAL, substeps: int = 0):
+                 precond: Optional[int] = None, form: int = PROP_FORM_EXPONENTIAL, substeps: int = 0,
+                 multigroup: bool = True):
         import torch
         self.torch = torch
         self.grids = [prop_grid(int(g[0]), int(g[1]), float(g[2]), float(g[3])) if not isinstance(g, prop_grid)
@@ -241,6 +243,7 @@ class Propagator:
             self.opts.precond = precond
         self.opts.form = form
         self.opts.substeps = substeps
+        self.opts.multigroup = 1 if multigroup else 0
         poles = np.asarray(poles, np.complex128)
         residues = np.asarray(residues, np.complex128)
         self.npoles = poles.size

@@ -54,6 +54,10 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert P.lib().prop_workspace_size(1, good, 12, ct.byref(o2), ct.byref(n)) == P.PROP_E_ARG
     o3 = P.prop_default_opts(3, P.PROP_FP32)
     assert P.lib().prop_workspace_size(1, good, 12, ct.byref(o3), ct.byref(n)) != P.PROP_OK
+    o4 = P.prop_default_opts(1, P.PROP_FP32)
+    assert o4.multigroup == 1                        # lockstep grids by default
+    o4.multigroup = 2
+    assert P.lib().prop_workspace_size(1, good, 12, ct.byref(o4), ct.byref(n)) == P.PROP_E_ARG
     h = ct.c_void_p()
     d = (ct.c_double * 2)(0.0, 0.0)
     # null workspace is rejected before any device work
