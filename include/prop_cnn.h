@@ -11,7 +11,10 @@
  *   y[n, y, x, co] = b[co] + sum_{t, ci} W[t, co, ci] a[n, y + dy_t, x + dx_t, ci]
  * with tap t = 3 (dy + 1) + (dx + 1).  Activations are NHWC bfloat16 with 16 or
  * 32 channels; weights bfloat16 [9][Cout][Cin]; biases float32.  Convolutions
- * run on the BF16 tensor cores and accumulate in float32.
+ * run on the BF16 tensor cores and accumulate in float32: tcgen05 MMAs with
+ * the accumulator in tensor memory (128-pixel row tiles, persistent CTAs, when
+ * W is a multiple of 128; 128-pixel tiles when H W is), else warp-level
+ * mma.sync.
  *
  * All pointers are device pointers; calls are asynchronous on `stream` and
  * return PROP_CNN_OK (0) or an error code.  Grids need W a multiple of 16
@@ -27,7 +30,18 @@
 extern "C" {
 #endif
 
-enum { PROP_CNN_OK = 0, PROP_CNN_E_ARG = 1, PROP_CNN_E_CUDA = 3 };
+enum { PROP_CNN_OK = 0, PROP_CNN_E_ARG = 1, PROP_CNN_E_CUDA = 3, PROP_CNN_E_TIMEOUT = 4 };
+enum { PROP_CNN_PATH_AUTO = 0, PROP_CNN_PATH_MMA_SYNC = 1 };
+
+/* Convolution kernel choice for this process (default PROP_CNN_PATH_AUTO:
+ * tcgen05 where the tiles fit; PROP_CNN_PATH_MMA_SYNC: always warp-level
+ * mma.sync).  Both give the same sums up to float32 rounding order. */
+int prop_cnn_set_path(int32_t path);
+
+/* Synchronises `stream`; PROP_CNN_E_TIMEOUT if a tensor-core convolution since
+ * the last call gave up its bounded wait for its MMAs (its output is then
+ * undefined; the flag is cleared), else PROP_CNN_OK. */
+int prop_cnn_check(void* stream);
 enum { PROP_CNN_RELU_BF16 = 0, PROP_CNN_LINEAR_BF16 = 1, PROP_CNN_LINEAR_F32 = 2 };
 
 /* One convolution layer over N images of H x W.  mode: store relu(y) as bf16,

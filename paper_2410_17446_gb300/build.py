@@ -38,7 +38,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     from concurrent.futures import ThreadPoolExecutor
     objs = [os.path.join(PKG, "_obj_" + os.path.basename(s) + ".o") for s in SRC]
-    flags = ["-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC"]
+    # PROP_NVCC_FLAGS: extra nvcc flags (e.g. -DPROP_SYNC_EVERY=8 to try another batch length)
+    flags = ["-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+             *os.environ.get("PROP_NVCC_FLAGS", "").split()]
 
     def compile_one(pair):
         src, obj = pair

@@ -21,7 +21,14 @@
 #include <algorithm>
 #include <cmath>
 
+#include "tc.cuh"
+#include "tma.cuh"
+
 namespace {
+
+// Set by a tensor-core convolution whose bounded wait for its MMAs gave up
+// (read and cleared by prop_cnn_check).
+__device__ int g_cnn_err;
 
 __device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
@@ -94,6 +101,258 @@ __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16* __restrict__ 
       *o0 = __floats2bfloat162_rn(v[0], v[1]);
       *o1 = __floats2bfloat162_rn(v[2], v[3]);
     }
+  }
+}
+
+// The same convolution on the 5th-generation tensor cores (tcgen05).  A CTA of
+// 128 threads takes 128 consecutive pixels of one sample (MMA M = 128) and all
+// COUT channels (N = COUT); K runs over the 9 taps x CIN channels, 16 per MMA.
+// Shared memory holds, as K-major core matrices (8 rows x 16 bytes):
+//   A: 9 x CIN/8 planes of 128 pixels x 8 channels (2 KiB each), gathered with
+//      the circular wrap of each tap;  B: 9 x CIN/8 planes of COUT x 8 channels.
+// One thread issues the 9 CIN/16 MMAs into a 128 x COUT FP32 accumulator in
+// tensor memory and commits them to an mbarrier; warp w then reads lanes
+// 32 w .. 32 w + 31 (its pixels) for the bias / ReLU / store epilogue.
+template <int CIN, int COUT>
+constexpr size_t conv_tc_smem() { return (size_t)9 * (CIN / 8) * (128 + COUT) * 16; }
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict__ in,
+                                                 const __nv_bfloat16* __restrict__ w,
+                                                 const float* __restrict__ bias, void* out, int H, int W,
+                                                 const int* active, int astride, int want) {
+  constexpr int NPL = CIN / 8;                  // 16-byte channel planes
+  constexpr uint32_t A_PLANE = 128 * 16, B_PLANE = COUT * 16;
+  extern __shared__ __align__(128) unsigned char smem_tc[];
+  unsigned char* sa = smem_tc;
+  unsigned char* sb = smem_tc + 9 * NPL * A_PLANE;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int n = blockIdx.y;
+  if (active && active[(long)n * astride] != want) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long npix = (long)H * W, p0 = (long)blockIdx.x * 128;
+  const __nv_bfloat16* img = in + (long)n * npix * CIN;
+  if (warp == 0) prop_tc::tmem_alloc(&tmem_base, 32);
+  if (tid == 0) { prop_dev::mbar_init(&bar, 1); prop_dev::fence_mbar_init(); }
+  // weights: plane (t, c8), row co = w[t][co][8 c8 .. 8 c8 + 7]
+  for (int i = tid; i < 9 * NPL * COUT; i += 128) {
+    const int t = i / (NPL * COUT), r = i % (NPL * COUT), c8 = r / COUT, co = r % COUT;
+    *reinterpret_cast<uint4*>(sb + (size_t)i * 16) =
+        *reinterpret_cast<const uint4*>(w + ((size_t)t * COUT + co) * CIN + c8 * 8);
+  }
+  // activations: plane (t, c8), row m = pixel p0 + m shifted by tap t (circular)
+  for (int i = tid; i < 9 * 128 * NPL; i += 128) {
+    const int c8 = i % NPL, m = (i / NPL) % 128, t = i / (NPL * 128);
+    const long p = p0 + m;
+    const int y = (int)(p / W), x = (int)(p % W);
+    const int yy = wrap(y + t / 3 - 1, H), xx = wrap(x + t % 3 - 1, W);
+    *reinterpret_cast<uint4*>(sa + ((size_t)(t * NPL + c8) * 128 + m) * 16) =
+        *reinterpret_cast<const uint4*>(img + ((long)yy * W + xx) * CIN + c8 * 8);
+  }
+  prop_dev::fence_proxy_async_smem();   // the operand writes, before the tensor cores read them
+  prop_tc::tc_fence_before();
+  __syncthreads();
+  prop_tc::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    constexpr uint32_t idesc = prop_tc::idesc_bf16_f32(128, COUT);
+    const uint32_t a0 = prop_dev::smem_u32(sa), b0 = prop_dev::smem_u32(sb);
+    int k = 0;
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int kc = 0; kc < CIN / 16; ++kc, ++k) {
+        const int plane = t * NPL + 2 * kc;   // two planes = 16 channels = one MMA's K
+        const uint64_t a = prop_tc::smem_desc(a0 + plane * A_PLANE, A_PLANE, 128);
+        const uint64_t b = prop_tc::smem_desc(b0 + plane * B_PLANE, B_PLANE, 128);
+        prop_tc::mma_bf16(tmem, a, b, idesc, k > 0);
+      }
+    prop_tc::mma_commit(&bar);
+  }
+  const bool ok = prop_dev::mbar_wait(&bar, 0, &g_cnn_err);
+  prop_tc::tc_fence_after();
+  if (ok) {
+    const long p = (long)n * npix + p0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      float v[16];
+      prop_tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        v[i] += bias ? bias[c0 + i] : 0.f;
+        if (MODE == 0) v[i] = fmaxf(v[i], 0.f);
+      }
+      if (MODE == 2) {
+        float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + p * COUT + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+        uint32_t pk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+          pk[q] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + p * COUT + c0);
+        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+    }
+  }
+  prop_tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    prop_tc::tc_fence_after();
+    prop_tc::tmem_dealloc(tmem, 32);
+  }
+}
+
+// Row-tiled, persistent variant for W a multiple of 128 (every grid of the
+// propagator's workloads).  A tile is 128 pixels of one image row; the CTA
+// stages the tile's halo once (rows y-1, y, y+1 x 130 pixels, circular wrap)
+// as CIN/8 planes of 16-byte rows, and each tap's operand is the same halo
+// addressed at a row and a one-pixel shift (descriptor start = plane base +
+// 16 (dx + 1) bytes), so nothing is gathered nine times.  The halo is double
+// buffered with cp.async: the next tile's loads are in flight while the
+// current tile's MMAs and epilogue run.  Weights and biases are loaded once
+// per CTA; tensor memory is allocated once per CTA.
+template <int CIN, int COUT>
+constexpr size_t conv_row_smem() {
+  return (size_t)9 * (CIN / 8) * COUT * 16 + 2 * (size_t)3 * (CIN / 8) * 130 * 16;
+}
+
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(prop_dev::smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(128) k_conv_tc_row(const __nv_bfloat16* __restrict__ in,
+                                                     const __nv_bfloat16* __restrict__ w,
+                                                     const float* __restrict__ bias, void* out, int N, int H, int W,
+                                                     const int* active, int astride, int want) {
+  constexpr int NPL = CIN / 8;
+  constexpr int HPX = 130;                              // halo pixels per row
+  constexpr uint32_t H_PLANE = HPX * 16, B_PLANE = COUT * 16;
+  constexpr uint32_t HALO = 3 * NPL * H_PLANE;          // bytes of one halo buffer
+  extern __shared__ __align__(128) unsigned char smem_row[];
+  unsigned char* sb = smem_row;                         // weights
+  unsigned char* sh = smem_row + 9 * NPL * B_PLANE;     // two halo buffers
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sbias[COUT];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tpr = W / 128;                              // tiles per row
+  const long ntiles = (long)N * H * tpr;
+  // the tiles of this CTA: blockIdx.x, + gridDim.x, ...; skip inactive images
+  auto next_tile = [&](long t) -> long {
+    for (; t < ntiles; t += gridDim.x) {
+      const int n = (int)(t / ((long)H * tpr));
+      if (!active || active[(long)n * astride] == want) return t;
+    }
+    return -1;
+  };
+  auto gather = [&](long t, unsigned char* buf) {
+    const int n = (int)(t / ((long)H * tpr));
+    const int rem = (int)(t % ((long)H * tpr));
+    const int y = rem / tpr, x0 = (rem % tpr) * 128;
+    const __nv_bfloat16* img = in + (long)n * H * W * CIN;
+    for (int i = tid; i < 3 * HPX * NPL; i += 128) {
+      const int c8 = i % NPL, q = (i / NPL) % HPX, r = i / (NPL * HPX);
+      const int yy = wrap(y + r - 1, H), xx = wrap(x0 + q - 1, W);
+      cp_async_16(buf + ((size_t)(r * NPL + c8) * HPX + q) * 16, img + ((long)yy * W + xx) * CIN + c8 * 8);
+    }
+  };
+  long tile = next_tile(blockIdx.x);
+  if (tile < 0) return;
+  if (warp == 0) prop_tc::tmem_alloc(&tmem_base, 32);
+  if (tid == 0) { prop_dev::mbar_init(&bar, 1); prop_dev::fence_mbar_init(); }
+  for (int i = tid; i < 9 * NPL * COUT; i += 128) {
+    const int t = i / (NPL * COUT), r = i % (NPL * COUT), c8 = r / COUT, co = r % COUT;
+    cp_async_16(sb + (size_t)i * 16, w + ((size_t)t * COUT + co) * CIN + c8 * 8);
+  }
+  for (int i = tid; i < COUT; i += 128) sbias[i] = bias ? bias[i] : 0.f;
+  gather(tile, sh);
+  cp_async_commit();
+  prop_tc::tc_fence_before();
+  __syncthreads();
+  prop_tc::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = prop_tc::idesc_bf16_f32(128, COUT);
+  const uint32_t b0 = prop_dev::smem_u32(sb);
+  bool ok = true;
+  for (int k = 0; tile >= 0; ++k) {
+    unsigned char* cur = sh + (k & 1) * HALO;
+    const long nxt = next_tile(tile + gridDim.x);
+    if (nxt >= 0) {   // prefetch the next tile's halo into the other buffer
+      gather(nxt, sh + ((k + 1) & 1) * HALO);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    prop_dev::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && ok) {
+      prop_tc::tc_fence_after();
+      const uint32_t a0 = prop_dev::smem_u32(cur);
+      int kk = 0;
+#pragma unroll
+      for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc, ++kk) {
+          const int r = t / 3, dx = t % 3 - 1;
+          const uint64_t a = prop_tc::smem_desc(a0 + (uint32_t)(r * NPL + 2 * kc) * H_PLANE + (uint32_t)(dx + 1) * 16,
+                                                H_PLANE, 128);
+          const uint64_t b = prop_tc::smem_desc(b0 + (uint32_t)(t * NPL + 2 * kc) * B_PLANE, B_PLANE, 128);
+          prop_tc::mma_bf16(tmem, a, b, idesc, kk > 0);
+        }
+      prop_tc::mma_commit(&bar);
+    }
+    ok = ok && prop_dev::mbar_wait(&bar, (uint32_t)(k & 1), &g_cnn_err);
+    prop_tc::tc_fence_after();
+    if (ok) {
+      const int n = (int)(tile / ((long)H * tpr));
+      const int rem = (int)(tile % ((long)H * tpr));
+      const long p = ((long)n * H + rem / tpr) * W + (long)(rem % tpr) * 128 + warp * 32 + lane;
+#pragma unroll
+      for (int c0 = 0; c0 < COUT; c0 += 16) {
+        float v[16];
+        prop_tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          v[i] += sbias[c0 + i];
+          if (MODE == 0) v[i] = fmaxf(v[i], 0.f);
+        }
+        if (MODE == 2) {
+          float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + p * COUT + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+          uint32_t pk[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            pk[q] = *reinterpret_cast<const uint32_t*>(&hv);
+          }
+          uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + p * COUT + c0);
+          o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      }
+    }
+    prop_tc::tc_fence_before();
+    __syncthreads();   // accumulator read and halo buffer consumed before they are reused
+    tile = nxt;
+  }
+  cp_async_wait<0>();
+  if (warp == 0) {
+    prop_tc::tc_fence_after();
+    prop_tc::tmem_dealloc(tmem, 32);
   }
 }
 
@@ -211,9 +470,45 @@ __global__ void k_adam(float* p, const float* grad, float* m, float* v, long n, 
   }
 }
 
+int g_path = PROP_CNN_PATH_AUTO;
+
 template <int CIN, int COUT, int MODE>
 int launch_conv(const void* in, const void* w, const float* b, void* out, int N, int H, int W, const int* active,
                 int astride, int want, cudaStream_t st) {
+  const long npix = (long)H * W;
+  if (g_path == PROP_CNN_PATH_AUTO && W % 128 == 0) {
+    constexpr size_t sm = conv_row_smem<CIN, COUT>();
+    static int ctas_per_sm = 0;
+    if (!ctas_per_sm) {
+      if (cudaFuncSetAttribute(k_conv_tc_row<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_conv_tc_row<CIN, COUT, MODE>, 128, sm) !=
+              cudaSuccess)
+        return PROP_CNN_E_CUDA;
+      if (ctas_per_sm < 1) ctas_per_sm = 1;
+    }
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return PROP_CNN_E_CUDA;
+    const long ntiles = (long)N * H * (W / 128);
+    const int ctas = (int)std::min<long>(ntiles, (long)ctas_per_sm * sms);
+    k_conv_tc_row<CIN, COUT, MODE><<<ctas, 128, sm, st>>>((const __nv_bfloat16*)in, (const __nv_bfloat16*)w, b, out, N,
+                                                          H, W, active, astride, want);
+    return cudaGetLastError() == cudaSuccess ? 0 : PROP_CNN_E_CUDA;
+  }
+  if (g_path == PROP_CNN_PATH_AUTO && npix % 128 == 0 && npix / 128 <= 0x7FFFFFFF && N <= 65535) {
+    constexpr size_t sm = conv_tc_smem<CIN, COUT>();
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_conv_tc<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+          cudaSuccess)
+        return PROP_CNN_E_CUDA;
+      attr = true;
+    }
+    k_conv_tc<CIN, COUT, MODE><<<dim3((unsigned)(npix / 128), N), 128, sm, st>>>(
+        (const __nv_bfloat16*)in, (const __nv_bfloat16*)w, b, out, H, W, active, astride, want);
+    return cudaGetLastError() == cudaSuccess ? 0 : PROP_CNN_E_CUDA;
+  }
   dim3 grid((W / 16 + 3) / 4, H, N);
   k_conv<CIN, COUT, MODE><<<grid, 128, 0, st>>>((const __nv_bfloat16*)in, (const __nv_bfloat16*)w, b, out, H, W,
                                                 active, astride, want);
@@ -249,6 +544,22 @@ int prop_cnn_conv(int32_t cin, int32_t cout, int32_t mode, const void* d_in, con
   if (cin == 16 && cout == 32) return conv_mode<16, 32>(mode, d_in, d_w, d_bias, d_out, N, H, W, act, active_stride, active_want, st);
   if (cin == 32 && cout == 16) return conv_mode<32, 16>(mode, d_in, d_w, d_bias, d_out, N, H, W, act, active_stride, active_want, st);
   return conv_mode<32, 32>(mode, d_in, d_w, d_bias, d_out, N, H, W, act, active_stride, active_want, st);
+}
+
+int prop_cnn_set_path(int32_t path) {
+  if (path != PROP_CNN_PATH_AUTO && path != PROP_CNN_PATH_MMA_SYNC) return PROP_CNN_E_ARG;
+  g_path = path;
+  return PROP_CNN_OK;
+}
+
+int prop_cnn_check(void* stream) {
+  int e = 0;
+  const int zero = 0;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+      cudaMemcpyFromSymbol(&e, g_cnn_err, sizeof(int)) != cudaSuccess ||
+      (e && cudaMemcpyToSymbol(g_cnn_err, &zero, sizeof(int)) != cudaSuccess))
+    return PROP_CNN_E_CUDA;
+  return e ? PROP_CNN_E_TIMEOUT : PROP_CNN_OK;
 }
 
 int prop_cnn_wgrad_workspace(int32_t cin, int32_t cout, int32_t N, int32_t H, int32_t W, size_t* bytes) {

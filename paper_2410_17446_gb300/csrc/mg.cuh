@@ -51,4 +51,7 @@ cudaError_t mg_launch(int pass, const MGroups& mg, int jj, int with_w, cudaStrea
 int mg_gx(int pass, const GV<float>& g, int act, int cap);
 int mg_rows(int pass, const GV<float>& g, int act);
 
+// Resident CTAs per SM of the pass's kernel (MG_GRAM, MG_STEP), looked up once.
+int mg_resident(int pass);
+
 }  // namespace prop_dev

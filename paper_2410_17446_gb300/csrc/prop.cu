@@ -54,6 +54,18 @@ int sm_count() {   // SMs of the current device (looked up once)
   return n > 0 ? n : 1;
 }
 
+// Resident CTAs per SM of a kernel launched with `nt` threads and no dynamic
+// shared memory, looked up once into `cache`: the sweeps size one wave from it.
+template <typename K> int resident(K kernel, int nt, int& cache) {
+  if (!cache) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, nt, 0) != cudaSuccess || n < 1) n = 1;
+    cudaGetLastError();
+    cache = n;
+  }
+  return cache;
+}
+
 // Launch geometry of the FFT passes: small CTAs, so that one 1024^2 field still
 // spreads over several CTAs per SM and their load / transform / store phases overlap.
 template <typename T> constexpr int cols_per_cta() { return sizeof(T) == 4 ? 4 : 2; }   // 32-byte row segments
@@ -97,7 +109,10 @@ constexpr int EPT_GS = 4;     // points per thread of the update sweep
 constexpr int GVEC_GS = 4;    // basis vectors per load group of the update sweep
 constexpr int EPT_GRAM = 4;   // points per thread of the Gram sweep
 constexpr int GVEC_GRAM = 4;  // basis vectors per transpose-reduce of the Gram sweep
-constexpr int SYNC_EVERY = 4;   // Arnoldi iterations launched between host reads of the GMRES state
+#ifndef PROP_SYNC_EVERY
+#define PROP_SYNC_EVERY 4
+#endif
+constexpr int SYNC_EVERY = PROP_SYNC_EVERY;   // Arnoldi iterations launched between host reads of the GMRES state
 // Arnoldi batches in flight: 1, the host reads each batch's counts before enqueuing the
 // next.  (Two deep was measured on GB300: within 2 % either way on the three
 // benchmark workloads, so the launches stay sized by exact counts.)
@@ -920,11 +935,16 @@ template <typename T> struct StepGroup {
             CK(rows_inv<T>(ga, buf(g.Tmp, F), buf(g.Tmp, F), ST_ITER, 0, epi(EPI_ARNOLDI, j), act, st)); }
         }
       }
-      // sweeps: about one wave of CTAs (4 resident per SM) shared by the act systems
-      const int cap = std::max(1, 4 * sm_count() / act);
+      // sweeps: one wave of CTAs (as many as are resident at once) shared by the
+      // act systems; the update sweep keeps a slot per system for its control CTA
+      // (at most a quarter of the wave: the control CTAs are short)
+      static int occ_gram = 0, occ_step = 0;
+      const int wave_g = resident(k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>, NT_VEC, occ_gram) * sm_count();
+      const int wave_s = resident(k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS>, NT_VEC, occ_step) * sm_count();
+      const int cap_g = std::max(1, wave_g / act), cap = std::max(1, (wave_s - std::min(act, wave_s / 4)) / act);
       { Prof p_(h, K_GRAM, 0);
         k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>
-            <<<dim3(std::min(gram_blocks, cap), act), NT_VEC, 0, st>>>(ga, j, op ? 1 : 0); }
+            <<<dim3(std::min(gram_blocks, cap_g), act), NT_VEC, 0, st>>>(ga, j, op ? 1 : 0); }
       { Prof p_(h, K_GS_UPDATE, 0);
         StepArgs sa;
         sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
@@ -1097,18 +1117,35 @@ int arnoldi_multigroup(prop* h, std::vector<StepGroup<float>>& S, const std::vec
       sa.m = m; sa.P = s.P; sa.backward = s.bw; sa.tol = h->tol; sa.breakdown = s.breakdown;
       sa.bnorm2 = s.g.bnorm2; sa.anorm = s.g.anorm; sa.counts = nullptr;
     }
-    // sweeps: about one wave of CTAs (4 resident per SM) shared by every listed
-    // system in proportion to its points, so that every CTA sweeps about as much
+    // sweeps: the CTAs share the listed systems' points evenly.  Systems of one
+    // size get one wave (as many CTAs as are resident at once; the update sweep
+    // keeps a slot per system for its control CTA, at most a quarter of the
+    // wave); systems of several sizes get four waves of equal CTAs, so that the
+    // largest grid's CTAs do not form a tail.
     double work = 0;
-    for (int k = 0; k < n; ++k) work += (double)before[idx[k]] * S[idx[k]].F;
-    int cap[MAXG];
-    for (int k = 0; k < n; ++k)
-      cap[k] = std::max(1, (int)(4.0 * sm_count() * (double)S[idx[k]].F / std::max(work, 1.0)));
+    int tot = 0;
+    bool uniform = true;
+    for (int k = 0; k < n; ++k) {
+      work += (double)before[idx[k]] * S[idx[k]].F;
+      tot += before[idx[k]];
+      uniform = uniform && S[idx[k]].F == S[idx[0]].F;
+    }
+    const int waves = uniform ? 1 : 4;
+    const int wave1 = mg_resident(MG_STEP) * sm_count();
+    const double wave_g = (double)mg_resident(MG_GRAM) * sm_count() * waves;
+    const double wave_s = (double)(wave1 - (uniform ? std::min(tot, wave1 / 4) : 0)) * waves;
+    int cap_g[MAXG], cap_s[MAXG];
+    for (int k = 0; k < n; ++k) {
+      const double share = (double)S[idx[k]].F / std::max(work, 1.0);
+      // one wave: round down so that the CTAs fit; several: to nearest
+      cap_g[k] = std::max(1, uniform ? (int)(wave_g * share) : (int)std::lround(wave_g * share));
+      cap_s[k] = std::max(1, uniform ? (int)(wave_s * share) : (int)std::lround(wave_s * share));
+    }
     auto layout = [&](int pass) {
       int c = 0;
       for (int k = 0; k < n; ++k) {
         mg.c0[k] = c;
-        mg.gx[k] = mg_gx(pass, mg.g[k], before[idx[k]], cap[k]);
+        mg.gx[k] = mg_gx(pass, mg.g[k], before[idx[k]], pass == MG_STEP ? cap_s[k] : cap_g[k]);
         c += mg.gx[k] * mg_rows(pass, mg.g[k], before[idx[k]]);
       }
       mg.c0[n] = c;

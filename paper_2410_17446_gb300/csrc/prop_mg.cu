@@ -176,6 +176,20 @@ int mg_gx(int pass, const GV<float>& g, int act, int cap) {
   }
 }
 
+int mg_resident(int pass) {
+  static int occ[2] = {0, 0};
+  const int i = pass == MG_STEP ? 1 : 0;
+  if (!occ[i]) {
+    int n = 0;
+    const cudaError_t e = i ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mg_step, MG_NT, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mg_gram, MG_NT, 0);
+    if (e != cudaSuccess || n < 1) n = 1;
+    cudaGetLastError();
+    occ[i] = n;
+  }
+  return occ[i];
+}
+
 cudaError_t mg_launch(int pass, const MGroups& mg, int jj, int with_w, cudaStream_t st) {
   const int ctas = pass == MG_ACTIVE ? mg.ng : mg.c0[mg.ng];
   if (ctas <= 0) return cudaSuccess;

@@ -119,6 +119,8 @@ _SIGS = {
     "prop_cnn_to_bf16": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p]),
     "prop_cnn_mse": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_int32,
                                 ct.c_void_p, ct.c_void_p]),
+    "prop_cnn_set_path": (ct.c_int, [ct.c_int32]),
+    "prop_cnn_check": (ct.c_int, [ct.c_void_p]),
     "prop_cnn_adam": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_float,
                                  ct.c_float, ct.c_float, ct.c_float, ct.c_int32, ct.c_void_p, ct.c_void_p]),
 }

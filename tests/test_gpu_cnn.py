@@ -67,3 +67,45 @@ def test_training_reduces_loss(G):
         net.adam(dws, dbs, lr=3e-3)
         losses.append(loss.item())
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+@pytest.mark.parametrize("H,W", [(32, 128), (6, 256), (8, 64)])
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 16), (32, 32)])
+def test_tensor_core_paths_agree(G, cin, cout, H, W):
+    """The tcgen05 convolutions (persistent 128-pixel row tiles for W a multiple
+    of 128, else 128-pixel tiles; accumulator in tensor memory) and the
+    warp-level mma.sync one give the same layer, in all three output modes, and
+    an inactive image is left untouched; the bounded wait never gave up."""
+    import ctypes as ct
+    import torch
+    from oracle import cnn
+    from paper_2410_17446_gb300 import prop as P
+    L = P.lib()
+    rng = np.random.default_rng(cin + cout)
+    N = 3
+    x = torch.tensor(rng.standard_normal((N, H, W, cin)), dtype=torch.bfloat16, device="cuda")
+    w = torch.tensor(rng.standard_normal((9, cout, cin)) / np.sqrt(9 * cin), dtype=torch.bfloat16, device="cuda")
+    b = torch.tensor(rng.standard_normal(cout) * 0.1, dtype=torch.float32, device="cuda")
+    active = torch.tensor([1, 0, 1], dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    outs = {}
+    try:
+        for path in (0, 1):   # PROP_CNN_PATH_AUTO (tcgen05 here), PROP_CNN_PATH_MMA_SYNC
+            assert L.prop_cnn_set_path(path) == 0
+            for mode, dt in ((0, torch.bfloat16), (1, torch.bfloat16), (2, torch.float32)):
+                o = torch.full((N, H, W, cout), 7.0, dtype=dt, device="cuda")
+                assert L.prop_cnn_conv(cin, cout, mode, x.data_ptr(), w.data_ptr(), b.data_ptr(), o.data_ptr(), N, H,
+                                       W, active.data_ptr(), 1, 1, ct.c_void_p(st)) == 0
+                outs[path, mode] = o.float().cpu().numpy()
+        assert L.prop_cnn_check(ct.c_void_p(st)) == 0
+    finally:
+        L.prop_cnn_set_path(0)
+    ref = cnn.forward(x.float().cpu().numpy().astype(np.float64), [w.float().cpu().numpy().astype(np.float64)],
+                      [b.cpu().numpy().astype(np.float64)], bf16=False)[1][0]
+    for mode in (0, 1, 2):
+        tc, ms = outs[0, mode], outs[1, mode]
+        assert np.all(tc[1] == 7.0) and np.all(ms[1] == 7.0)   # the inactive image
+        tol = 1e-5 if mode == 2 else 1e-2
+        assert rel(tc[[0, 2]], ms[[0, 2]]) < tol, mode
+        r = np.maximum(ref, 0.0) if mode == 0 else ref
+        assert rel(tc[[0, 2]], r[[0, 2]]) < tol, mode
