@@ -268,7 +268,7 @@ def _peak():
     return (pk, "measured") if pk else (6800.0, "fallback")
 
 
-def roofline_of(name: str, prof: dict, ms_total: float) -> dict:
+def roofline_of(name: str, prof: dict) -> dict:
     """HBM roofline of the kernel kind with the largest device time in the timed region:
     summed algorithmic bytes / summed CUDA-event durations of its launches."""
     dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
@@ -287,7 +287,8 @@ def roofline_of(name: str, prof: dict, ms_total: float) -> dict:
     return {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_source": src,
             "alg_bytes_per_launch": alg_launch,
-            "launches": dom[1]["launches"], "share_of_step": dom[1]["total_ms"] / ms_total if ms_total else None}
+            "launches": dom[1]["launches"],
+            "share_of_kernel_time": dom[1]["total_ms"] / max(1e-12, sum(v["total_ms"] for v in prof.values()))}
 
 
 class Runner:
@@ -414,9 +415,11 @@ class Runner:
         prof = r["prof"]
         d = {"value": whole_job_value(self.ws, self.W.points, self.args.steps, ms / 1e3),
              "ms_per_step": ms / self.args.steps,
-             "roofline": dict(roofline_of(self.name, prof, r["kernel_pass_ms"]),
+             "roofline": dict(roofline_of(self.name, prof),
                               measured_in="kernel pass: the timed steps' media replayed with a CUDA-event pair "
-                                          "around every launch on the library stream"),
+                                          "around every launch on the library stream (a device spin heads each "
+                                          "run of launches the host enqueues after a wait, so that the events "
+                                          "time kernels, not submission)"),
              "arnoldi_steps_total": r["arnoldi"],
              "arnoldi_steps_per_solve": r["arnoldi"] / (self.args.steps * len(self.W.beams) * self.W.npoles),
              "gmres_last_step": {"sum": int(r["iters"].sum()), "max": int(r["iters"].max())},

@@ -673,6 +673,24 @@ int async_status(int e) { return e == 0 ? PROP_OK : (e == 2 ? PROP_E_WORKSPACE :
 
 int* count_slots(prop* h, int slot) { return (int*)(h->ws + h->counts_off) + slot * CSLOT; }
 
+// Profiling only: a device spin heads each run of launches that the host enqueues
+// after waiting on the device, so that the GPU does not reach a launch's opening
+// event before the host has submitted the launch itself; the event pairs then time
+// the kernels, not the host's submission of them.  Bounded by the global timer
+// and by an iteration count.
+constexpr long long PROF_GATE_NS = 200000;
+__global__ void k_spin(long long ns) {
+  long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int it = 0; it < (1 << 24); ++it) {
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 >= ns) break;
+  }
+}
+void profile_gate(prop* h) {
+  if (h->profiling) k_spin<<<1, 32, 0, h->stream>>>(PROF_GATE_NS);
+}
+
 // The whole counts area (every slot set and the error word) into buf[COUNT_INTS].
 int read_count_area(prop* h, int* buf) {
   if (cudaMemcpyAsync(buf, h->ws + h->counts_off, COUNT_INTS * sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
@@ -680,6 +698,7 @@ int read_count_area(prop* h, int* buf) {
     return PROP_E_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PROP_E_CUDA;
   if (!h->pending.empty()) resolve_pending(h);
+  profile_gate(h);
   return async_status(buf[ERR_SLOT]);
 }
 
@@ -751,6 +770,7 @@ template <typename T> struct StepGroup {
     G.nonhomog_host.assign(nb, 0);
     CK(cudaMemcpyAsync(G.nonhomog_host.data(), g.nonhomog, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    profile_gate(h);
     G.medium_dirty = false;
   }
   n_inh = 0;
@@ -972,6 +992,7 @@ template <typename T> struct StepGroup {
     --nfl;
     if (cudaEventSynchronize(h->batch_ev[bt.par]) != cudaSuccess) return PROP_E_CUDA;
     if (!h->pending.empty()) resolve_pending(h);
+    profile_gate(h);
     const int* hc = h->hcounts + bt.par * 3 * SYNC_EVERY;
     for (int b2 = 0; b2 < bt.nb; ++b2) {
       const int j = bt.jj0 + b2;
@@ -1177,6 +1198,7 @@ int arnoldi_multigroup(prop* h, std::vector<StepGroup<float>>& S, const std::vec
     CK(cudaEventRecord(h->batch_ev[0], st));
     if (cudaEventSynchronize(h->batch_ev[0]) != cudaSuccess) return PROP_E_CUDA;
     if (!h->pending.empty()) resolve_pending(h);
+    profile_gate(h);
     // algorithmic bytes charged from the counts, as in the grid-by-grid step
     for (int k = 0; k < n; ++k) {
       const int i = idx[k];
