@@ -954,7 +954,7 @@ __device__ __forceinline__ void rows_inv_vec_body(int bx, int by, int gdx, GV<T>
   }
 }
 template <typename T, int N, int NR, int NT>
-__global__ void __launch_bounds__(NT) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_rows_inv_vec(GV<T> g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
                                                      Buf<typename Cx<T>::t> out, int mask, int skip_homog,
                                                      int mode, int jj) {
   rows_inv_vec_body<T, N, NR, NT>(blockIdx.x, blockIdx.y, gridDim.x, g, A, B, out, mask, skip_homog, mode, jj);

@@ -261,3 +261,14 @@ def test_mean_and_freespace_preconditioners_agree(P):
     assert rel_l2(fields[P.PROP_PRECOND_FREESPACE], ref) < FP64_TOL
     print("Arnoldi steps: mean", its[P.PROP_PRECOND_MEAN], "free space", its[P.PROP_PRECOND_FREESPACE])
     assert its[P.PROP_PRECOND_MEAN] < its[P.PROP_PRECOND_FREESPACE]
+
+
+def test_repeat_runs_agree_to_rounding(P):
+    """The FP64 Gram sums and norms are accumulated with atomics into 16 stripes,
+    so the summation order, and with it the last bits, may change from run to
+    run: two runs of the same 3 FP32 steps agree far inside the FP32 bar."""
+    from paper_2410_17446_gb300 import workloads as wl
+    W = wl.batched_scalar_1024(3, n=256)
+    a = gpu_run(gpu_propagator(W, "batched_scalar_1024", P.PROP_FP32), W, 3)[0]
+    b = gpu_run(gpu_propagator(W, "batched_scalar_1024", P.PROP_FP32), W, 3)[0]
+    assert rel_l2(a, b) < 1e-6
