@@ -15,6 +15,7 @@
 // so the free-space solve (Z_fs - p I)^-1 of Sec. 4.2 -- diagonal in Fourier
 // space on the periodic grid -- and the operator Z of Eq. (Z_bar_eq) share them.
 #pragma once
+#include <utility>
 #include <cuda_bf16.h>
 #include "fft.cuh"
 #include "tma.cuh"
@@ -198,12 +199,45 @@ template <typename T> __device__ __forceinline__ typename Cx<T>::t dbar_of(const
   return to_c(make_double2(a.x * inv, a.y * inv), T());
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization is scheduled as its predecessor in the stream drains (the
+// predecessor's CTAs trigger it when they exit) and waits here for the
+// predecessor's completion and memory before it touches anything.  A no-op for
+// a kernel launched without the attribute.  (Triggering the successor at entry
+// instead let waiting CTAs hold SM slots that multi-wave predecessors needed:
+// 3 % slower on the batched-scalar step.)
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+#ifndef PROP_PDL
+#define PROP_PDL 1
+#endif
+// Host side: launch `k` with programmatic stream serialization, so that it can be
+// scheduled while its predecessor drains (the kernel must begin with pdl_enter).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = PROP_PDL ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Pass 1: forward row DFTs.  grid = (ny/NR, units*ncomp).
 // ---------------------------------------------------------------------------
 template <typename T, int N, int NR, int NT, typename SRC, bool WF>
 __device__ __forceinline__ void rows_fwd_body(int bx, int by, int gdx, GV<T> g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, double* norm_acc) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -273,6 +307,7 @@ template <typename T, int NY, int NV, int NT, bool DY>
 __device__ __forceinline__ void cols_body(int bx, int by, int gdx, GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                              int mask, int fwd, int mul, int inv, int skip_homog, int pole,
                                              T scale, Buf<typename Cx<T>::t> spec, Buf<typename Cx<T>::t> dy) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   constexpr int W = DY ? 2 * NV : NV;     // tile width in shared memory
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -376,6 +411,7 @@ __device__ __forceinline__ void cols_tma_body(int bx, int by, int gdx, GV<T> g, 
                                                  const CUtensorMap& mdy, int mask, int fwd, int mul,
                                                  int inv, int skip_homog, int pole, T scale,
                                                  Buf<typename Cx<T>::t> spec) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   constexpr int EW = sizeof(C) / 8;           // 8-byte words per element (tensor-map element size)
   constexpr int BR = tma_box_rows(NY);        // rows per TMA box
@@ -521,6 +557,7 @@ template <typename T, int NY>
 __global__ void __launch_bounds__(32 * CW_NV) k_cols_warp(GV<T> g, Buf<typename Cx<T>::t> src,
                                                         Buf<typename Cx<T>::t> dst, int mask, int fwd, int mul,
                                                         int inv, int skip_homog, int pole, T scale) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   constexpr int NT = 32 * CW_NV, L = NY / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -615,6 +652,7 @@ struct EpiArgs {
 template <typename T, int N, int NR, int NT, bool ARN, bool WF>
 __device__ __forceinline__ void rows_inv_body(int bx, int by, int gdx, GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, int skip_homog, EpiArgs ep) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -857,6 +895,7 @@ template <typename T, int N, int NR, int NT>
 __device__ __forceinline__ void rows_inv_vec_body(int bx, int by, int gdx, GV<T> g, Buf<typename Cx<T>::t> A, Buf<typename Cx<T>::t> B,
                                                      Buf<typename Cx<T>::t> out, int mask, int skip_homog,
                                                      int mode, int jj) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   constexpr int NVV = 6 * NR;                 // vectors: (c, {z, dx, dy}) x NR rows
   constexpr int TPT = NR * N / NT;
@@ -1018,6 +1057,7 @@ template <int V, typename A> __device__ __forceinline__ void warp_transpose_redu
 // second takes ||w||^2).
 template <typename T, int NT, int EPT, int GVEC>
 __device__ __forceinline__ void dcgs_gram_body(int bx, int by, int gdx, GV<T> g, int jj, int with_w) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   constexpr int NW = NT / 32;
   __shared__ double red[NW][4 * (MMAX + 1)];
@@ -1653,6 +1693,7 @@ static __device__ void dcgs_control(SysState& q, int s, int j, const double2* bs
 // x - 1, x - 1 + (gridDim.x - 1), ... (one coefficient prologue per CTA).
 template <typename T, int NT, int EPT, int GVEC>
 __device__ __forceinline__ void dcgs_step_body(int bx, int by, int gdx, GV<T> g, int jj, StepArgs A) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   __shared__ double2 bs[MMAX + 1], as[MMAX + 1];
   __shared__ double nw_s;
@@ -1926,6 +1967,7 @@ static __global__ void k_selftest_wait(int* err) {
 // Compacted list of the systems in state ST_ITER, in index order (one block of
 // a multiple of 32 threads): the Arnoldi launches of a batch cover only these.
 static __global__ void k_active_list(const SysState* st, int nsys, int* list) {
+  pdl_enter();
   __shared__ int wsum[32], base;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) base = 0;

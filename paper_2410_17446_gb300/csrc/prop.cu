@@ -324,8 +324,7 @@ cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
       cudaError_t e = set_smem_once(k, sm, attr);
       if (e != cudaSuccess) return e;
       dim3 grid(g.ny / WROWS, units * g.ncomp);
-      k<<<grid, 32 * WROWS, sm, st>>>(g, src, dst, mask, nacc);
-      return cudaGetLastError();
+      return launch_pdl(k, grid, dim3(32 * WROWS), sm, st, g, src, dst, mask, nacc);
     }
   }
   constexpr int NR = rows_nr<N>(), NT = rows_nt<N>();
@@ -335,8 +334,7 @@ cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units * g.ncomp);
-  k<<<grid, NT, sm, st>>>(g, src, dst, mask, nacc);
-  return cudaGetLastError();
+  return launch_pdl(k, grid, dim3(NT), sm, st, g, src, dst, mask, nacc);
 }
 
 template <typename T, int N>
@@ -352,8 +350,7 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
       cudaError_t e = set_smem_once(k, sm, attr[arn ? 1 : 0]);
       if (e != cudaSuccess) return e;
       dim3 grid(g.ny / WROWS, units * g.ncomp);
-      k<<<grid, 32 * WROWS, sm, st>>>(g, src, dst, mask, skip, ep);
-      return cudaGetLastError();
+      return launch_pdl(k, grid, dim3(32 * WROWS), sm, st, g, src, dst, mask, skip, ep);
     }
   }
   constexpr int NR = rows_nr<N>(), NT = rows_nt<N>();
@@ -363,8 +360,7 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
   cudaError_t e = set_smem_once(k, sm, attr[arn ? 1 : 0]);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units * g.ncomp);
-  k<<<grid, NT, sm, st>>>(g, src, dst, mask, skip, ep);
-  return cudaGetLastError();
+  return launch_pdl(k, grid, dim3(NT), sm, st, g, src, dst, mask, skip, ep);
 }
 
 // Tensor maps for a column pass: source, destination and (MUL_TABLE) multiplier.
@@ -385,8 +381,7 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
       cudaError_t e = set_smem_once(k, sm, attr);
       if (e != cudaSuccess) return e;
       dim3 grid(g.nx / CW_NV, units * g.ncomp);
-      k<<<grid, 32 * CW_NV, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale);
-      return cudaGetLastError();
+      return launch_pdl(k, grid, dim3(32 * CW_NV), sm, st, g, src, dst, mask, fwd, mul, inv, skip, pole, scale);
     }
   }
   // the TMA pass reports failed copies through g.err: it runs only with an error word
@@ -405,9 +400,8 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
       attr = true;
     }
     dim3 grid(g.nx / NV, units * g.ncomp);
-    k<<<grid, NT, sm, st>>>(g, *cm.src, *cm.dst, cm.tab ? *cm.tab : *cm.src, cm.dy ? *cm.dy : *cm.src, mask, fwd, mul,
-                            inv, skip, pole, scale, spec);
-    return cudaGetLastError();
+    return launch_pdl(k, grid, dim3(NT), sm, st, g, *cm.src, *cm.dst, cm.tab ? *cm.tab : *cm.src,
+                      cm.dy ? *cm.dy : *cm.src, mask, fwd, mul, inv, skip, pole, scale, spec);
   }
   constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>() * (DY ? 2 : 1) > 256 ? 256 : cols_nt<T, NY>() * (DY ? 2 : 1);
   const size_t sm = smem_elems<NY, DY ? 2 * NV : NV, true>() * sizeof(C);
@@ -416,8 +410,7 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.nx / NV, units * g.ncomp);
-  k<<<grid, NT, sm, st>>>(g, src, dst, mask, fwd, mul, inv, skip, pole, scale, spec, dy);
-  return cudaGetLastError();
+  return launch_pdl(k, grid, dim3(NT), sm, st, g, src, dst, mask, fwd, mul, inv, skip, pole, scale, spec, dy);
 }
 template <typename T, int NY>
 cudaError_t cols_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst, int mask, int fwd,
@@ -443,8 +436,7 @@ cudaError_t rows_inv_vec_n(const GV<T>& g, Buf<typename Cx<T>::t> A, Buf<typenam
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ny / NR, units);
-  k<<<grid, NT, sm, st>>>(g, A, B, out, mask, skip, mode, jj);
-  return cudaGetLastError();
+  return launch_pdl(k, grid, dim3(NT), sm, st, g, A, B, out, mask, skip, mode, jj);
 }
 
 #define PROP_SIZE_SWITCH(n, CALL)                      \
@@ -931,7 +923,7 @@ template <typename T> struct StepGroup {
     int* slots = counts + 3 + par * 3 * SYNC_EVERY;
     CK(cudaMemsetAsync(slots, 0, 3 * SYNC_EVERY * sizeof(int), st));
     { Prof p_(h, K_CONTROL, 0);
-      k_active_list<<<1, 256, 0, st>>>(g.st, nsys, ulist); }
+      CK(launch_pdl(k_active_list, dim3(1), dim3(256), 0, st, (const SysState*)g.st, nsys, ulist)); }
     const int act = std::max(act_est, 1);
     for (int j = jb; j < jb + nb; ++j) {
       const bool op = j < m;
@@ -963,13 +955,14 @@ template <typename T> struct StepGroup {
       const int wave_s = resident(k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS>, NT_VEC, occ_step) * sm_count();
       const int cap_g = std::max(1, wave_g / act), cap = std::max(1, (wave_s - std::min(act, wave_s / 4)) / act);
       { Prof p_(h, K_GRAM, 0);
-        k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>
-            <<<dim3(std::min(gram_blocks, cap_g), act), NT_VEC, 0, st>>>(ga, j, op ? 1 : 0); }
+        CK(launch_pdl(k_dcgs_gram<T, NT_VEC, EPT_GRAM, GVEC_GRAM>, dim3(std::min(gram_blocks, cap_g), act),
+                      dim3(NT_VEC), 0, st, ga, j, op ? 1 : 0)); }
       { Prof p_(h, K_GS_UPDATE, 0);
         StepArgs sa;
         sa.m = m; sa.P = P; sa.backward = bw; sa.tol = h->tol; sa.breakdown = breakdown;
         sa.bnorm2 = g.bnorm2; sa.anorm = g.anorm; sa.counts = slots + 3 * (j - jb);
-        k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS><<<dim3(std::min(gs_blocks, cap) + 1, act), NT_VEC, 0, st>>>(ga, j, sa); }
+        CK(launch_pdl(k_dcgs_step<T, NT_VEC, EPT_GS, GVEC_GS>, dim3(std::min(gs_blocks, cap) + 1, act), dim3(NT_VEC),
+                      0, st, ga, j, sa)); }
       CK(cudaGetLastError());
     }
     CK(cudaMemcpyAsync(h->hcounts + par * 3 * SYNC_EVERY, slots, 3 * nb * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(MG_NT, 3) k_mg_step(const __grid_constant__ MG
 // the list of iterating systems of every group (one CTA a group), padded with -1,
 // and the group's count slots of the coming batch zeroed
 __global__ void __launch_bounds__(MG_NT) k_mg_active(const __grid_constant__ MGroups mg) {
+  pdl_enter();
   const GV<float>& g = mg.g[blockIdx.x];
   int* list = const_cast<int*>(g.ulist);
   for (int i = threadIdx.x; i < mg.nzero; i += blockDim.x) mg.zero[blockIdx.x][i] = 0;
@@ -208,12 +209,12 @@ cudaError_t mg_launch(int pass, const MGroups& mg, int jj, int with_w, cudaStrea
   switch (pass) {
     case MG_ROWS_FWD:
       e = raise(k_mg_rows_fwd, 0);
-      if (e == cudaSuccess) k_mg_rows_fwd<<<ctas, MG_NT, sm, st>>>(mg, jj);
+      if (e == cudaSuccess) e = launch_pdl(k_mg_rows_fwd, dim3(ctas), dim3(MG_NT), sm, st, mg, jj);
       break;
     case MG_COLS:
 #define COLS(DY, TMA, SLOT)                                                  \
       e = raise(k_mg_cols<DY, TMA>, SLOT);                                   \
-      if (e == cudaSuccess) k_mg_cols<DY, TMA><<<ctas, MG_NT, sm, st>>>(mg);
+      if (e == cudaSuccess) e = launch_pdl(k_mg_cols<DY, TMA>, dim3(ctas), dim3(MG_NT), sm, st, mg);
       if (vec) {
         if (tma_all) { COLS(true, true, 1) } else { COLS(true, false, 2) }
       } else {
@@ -224,15 +225,15 @@ cudaError_t mg_launch(int pass, const MGroups& mg, int jj, int with_w, cudaStrea
     case MG_ROWS_INV:
       if (vec) {
         e = raise(k_mg_rows_inv_vec, 5);
-        if (e == cudaSuccess) k_mg_rows_inv_vec<<<ctas, MG_NT, sm, st>>>(mg, jj);
+        if (e == cudaSuccess) e = launch_pdl(k_mg_rows_inv_vec, dim3(ctas), dim3(MG_NT), sm, st, mg, jj);
       } else {
         e = raise(k_mg_rows_inv, 6);
-        if (e == cudaSuccess) k_mg_rows_inv<<<ctas, MG_NT, sm, st>>>(mg, jj);
+        if (e == cudaSuccess) e = launch_pdl(k_mg_rows_inv, dim3(ctas), dim3(MG_NT), sm, st, mg, jj);
       }
       break;
-    case MG_GRAM: k_mg_gram<<<ctas, MG_NT, 0, st>>>(mg, jj, with_w); break;
-    case MG_STEP: k_mg_step<<<ctas, MG_NT, 0, st>>>(mg, jj); break;
-    case MG_ACTIVE: k_mg_active<<<ctas, MG_NT, 0, st>>>(mg); break;
+    case MG_GRAM: e = launch_pdl(k_mg_gram, dim3(ctas), dim3(MG_NT), 0, st, mg, jj, with_w); break;
+    case MG_STEP: e = launch_pdl(k_mg_step, dim3(ctas), dim3(MG_NT), 0, st, mg, jj); break;
+    case MG_ACTIVE: e = launch_pdl(k_mg_active, dim3(ctas), dim3(MG_NT), 0, st, mg); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
