@@ -1133,6 +1133,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_gram(GV<T> g, int jj, int with_w) {
 // v_0 *= scale (start of a cycle)
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_scale_v0(GV<T> g) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   const int s = blockIdx.y;
   if (g.st[s].state != ST_ITER || g.st[s].j != 0) return;
@@ -1149,6 +1150,7 @@ __global__ void __launch_bounds__(NT) k_scale_v0(GV<T> g) {
 // v_0 = R0 and E = 0 for the systems that start iterating (the others keep E unused).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_init_systems(GV<T> g) {
+  pdl_enter();
   const int s = blockIdx.y;
   if (g.st[s].state != ST_ITER) return;
   const long L = (long)g.ncomp * g.npts;
@@ -1166,6 +1168,7 @@ __global__ void __launch_bounds__(NT) k_init_systems(GV<T> g) {
 // follow as an FFT round trip with the EPI_ADD_E epilogue).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_combine(GV<T> g) {
+  pdl_enter();
   using C = typename Cx<T>::t;
   __shared__ C ys[MMAX];
   const int s = blockIdx.y;
@@ -1190,6 +1193,7 @@ __global__ void __launch_bounds__(NT) k_combine(GV<T> g) {
 // Wn[b] += sum_k r_k E[b, k]  (the residue sum of Eq. approx_prop, correction part).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_residue_sum(GV<T> g, double2* Wn) {
+  pdl_enter();
   const int b = blockIdx.y;
   const long L = (long)g.ncomp * g.npts;
   const long plane = (long)g.nb * L;
@@ -1423,6 +1427,7 @@ __device__ __forceinline__ double conv_threshold(const SysState& q, double tol, 
 
 static __global__ void k_begin_cycle(SysState* st, int nsys, int P, const double* bnorm2, double tol,
                               int from, int max_cycles, int first, const double* anorm, int backward) {
+  pdl_enter();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     SysState& q = st[s];
     if (!first && q.state != from) continue;
@@ -1941,6 +1946,7 @@ __global__ void __launch_bounds__(NT) k_guess_target(GV<T> g, int s, float* tgt)
 
 // zero the per-step accumulators of every system
 static __global__ void k_step_reset(SysState* st, int nsys) {
+  pdl_enter();
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     st[s].z0norm2 = 0.0; st[s].nrm_a = 0.0; st[s].enorm2 = 0.0;
   }
@@ -1992,6 +1998,7 @@ static __global__ void k_active_list(const SysState* st, int nsys, int* list) {
 
 // counts[0] = systems iterating, counts[1] = at a cycle end, counts[2] = flags
 static __global__ void k_count(const SysState* st, int nsys, int* counts) {
+  pdl_enter();
   __shared__ int c0, c1, c2;
   if (threadIdx.x == 0) { c0 = 0; c1 = 0; c2 = 0; }
   __syncthreads();

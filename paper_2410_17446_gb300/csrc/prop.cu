@@ -797,8 +797,8 @@ template <typename T> struct StepGroup {
   if (n_inh == 0) {           // homogeneous medium: the free-space step is exact, no correction
     if (!G.stats_zero) {      // record zero iterations for every system (once)
       Prof p_(h, K_CONTROL, 0);
-      k_step_reset<<<tg, tb, 0, st>>>(g.st, nsys);
-      k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw);
+      CK(launch_pdl(k_step_reset, dim3(tg), dim3(tb), 0, st, g.st, nsys));
+      CK(launch_pdl(k_begin_cycle, dim3(tg), dim3(tb), 0, st, g.st, nsys, P, (const double*)g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw));
       G.stats_zero = true;
     }
     CK(cudaGetLastError());
@@ -809,7 +809,7 @@ template <typename T> struct StepGroup {
   }
   G.stats_zero = false;
   { Prof p_(h, K_CONTROL, 0);
-    k_step_reset<<<tg, tb, 0, st>>>(g.st, nsys); }
+    CK(launch_pdl(k_step_reset, dim3(tg), dim3(tb), 0, st, g.st, nsys)); }
   const int sys_inh = n_inh * P;
   // correction right-hand sides: R0_k = -delta * IFFT2[w_hat/(zeta - p_k)]
   if (Cn == 2) {   // vector: R0 = -(Z - Z_fs) z_k with the psi and cross-polarisation terms
@@ -825,8 +825,8 @@ template <typename T> struct StepGroup {
       CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), -1, 1, epi(EPI_R0), nsys, st)); }
   }
   { Prof p_(h, K_CONTROL, 0);
-    k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw);
-    k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
+    CK(launch_pdl(k_begin_cycle, dim3(tg), dim3(tb), 0, st, g.st, nsys, P, (const double*)g.bnorm2, h->tol, -1, h->max_restarts, 1, g.anorm, bw));
+    CK(launch_pdl(k_count, dim3(1), dim3(256), 0, st, (const SysState*)g.st, nsys, counts)); }
   CK(cudaGetLastError());
   return PROP_OK;
   }
@@ -883,19 +883,19 @@ template <typename T> struct StepGroup {
     { Prof p_(h, K_GUESS, (4.0 * cs + 32.0) * endp);
       k_guess_apply<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
     { Prof p_(h, K_CONTROL, 0);
-      k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw); }
+      CK(launch_pdl(k_begin_cycle, dim3(tg), dim3(tb), 0, st, g.st, nsys, P, (const double*)g.bnorm2, h->tol, (int)ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw)); }
     { Prof p_(h, K_SCALE, 2 * cs * endp);
-      k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+      CK(launch_pdl(k_scale_v0<T, NT_VEC>, dim3(vb, nsys), dim3(NT_VEC), 0, st, g)); }
     { Prof p_(h, K_CONTROL, 0);
-      k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
+      CK(launch_pdl(k_count, dim3(1), dim3(256), 0, st, (const SysState*)g.st, nsys, counts)); }
     CK(cudaGetLastError());
     const int rc = read_counts(h, c3, slot);
     if (rc) return rc;
   } else if (any_used) {
     { Prof p_(h, K_INIT, (cs + 16) * pts * c3[0] * Cn);
-      k_init_systems<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+      CK(launch_pdl(k_init_systems<T, NT_VEC>, dim3(vb, nsys), dim3(NT_VEC), 0, st, g)); }
     { Prof p_(h, K_SCALE, 2 * cs * pts * c3[0] * Cn);
-      k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+      CK(launch_pdl(k_scale_v0<T, NT_VEC>, dim3(vb, nsys), dim3(NT_VEC), 0, st, g)); }
   }
   return PROP_OK;
   }
@@ -1015,7 +1015,7 @@ template <typename T> struct StepGroup {
   // accumulating into E); true residual r = R0 - (Z - p) e
   const double endp = (double)c3[1] * Cn * pts;
   { Prof p_(h, K_COMBINE, (1 + m) * cs * endp);   // upper bound on the v_i read: J <= m
-    k_combine<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    CK(launch_pdl(k_combine<T, NT_VEC>, dim3(vb, nsys), dim3(NT_VEC), 0, st, g)); }
   { Prof p_(h, K_ROWS_FWD, 2 * cs * endp);
     CK(rows_fwd<T, C>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, nullptr, nsys, st)); }
   { Prof p_(h, K_COLS, 2 * cs * endp);
@@ -1041,11 +1041,11 @@ template <typename T> struct StepGroup {
   { Prof p_(h, K_ROWS_INV, (4 * cs + 16) * endp);
     CK(rows_inv<T>(g, buf(g.Tmp, F), buf(g.Tmp, F), ST_CYCLE_END, 0, epi(EPI_TRUERES), nsys, st)); }
   { Prof p_(h, K_CONTROL, 0);
-    k_begin_cycle<<<tg, tb, 0, st>>>(g.st, nsys, P, g.bnorm2, h->tol, ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw); }
+    CK(launch_pdl(k_begin_cycle, dim3(tg), dim3(tb), 0, st, g.st, nsys, P, (const double*)g.bnorm2, h->tol, (int)ST_CYCLE_END, h->max_restarts, 0, g.anorm, bw)); }
   { Prof p_(h, K_SCALE, 0);
-    k_scale_v0<T, NT_VEC><<<dim3(vb, nsys), NT_VEC, 0, st>>>(g); }
+    CK(launch_pdl(k_scale_v0<T, NT_VEC>, dim3(vb, nsys), dim3(NT_VEC), 0, st, g)); }
   { Prof p_(h, K_CONTROL, 0);
-    k_count<<<1, 256, 0, st>>>(g.st, nsys, counts); }
+    CK(launch_pdl(k_count, dim3(1), dim3(256), 0, st, (const SysState*)g.st, nsys, counts)); }
   CK(cudaGetLastError());
   return PROP_OK;
   }
@@ -1055,7 +1055,7 @@ template <typename T> struct StepGroup {
   if (c3[2] & 2) return PROP_E_NOCONV;
   if (any_used) {
     Prof p_(h, K_RESIDUE, (32.0 + 16.0 * P) * pts * Cn * n_inh);   // upper bound: every pole used
-    k_residue_sum<T, NT_VEC><<<dim3(vb, nb), NT_VEC, 0, st>>>(g, Wn);
+    CK(launch_pdl(k_residue_sum<T, NT_VEC>, dim3(vb, nb), dim3(NT_VEC), 0, st, g, Wn));
   }
   CK(cudaGetLastError());
   G.cur ^= 1;   // commit: the new field becomes current
