@@ -431,7 +431,7 @@ cudaError_t rows_inv_vec_n(const GV<T>& g, Buf<typename Cx<T>::t> A, Buf<typenam
   constexpr int NR = vrows_nr<N>(), NT = vrows_nt<N>();
   static_assert((NR * N) % NT == 0, "vector epilogue needs a whole number of points per thread");
   const size_t sm = smem_elems<N, 6 * NR, false>() * sizeof(C);
-  auto k = k_rows_inv_vec<T, N, NR, NT>;
+  auto k = sizeof(T) == 4 ? k_rows_inv_vec_occ<T, N, NR, NT> : k_rows_inv_vec<T, N, NR, NT>;
   static bool attr = false;
   cudaError_t e = set_smem_once(k, sm, attr);
   if (e != cudaSuccess) return e;
