@@ -387,7 +387,9 @@ cudaError_t cols_nd(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename Cx<
   // the TMA pass reports failed copies through g.err: it runs only with an error word
   if (cplan != PROP_COLS_PLAIN && g.err && cm.src && cm.dst && (mul != MUL_TABLE || cm.tab) &&
       (!DY || (cm.dy && mul != MUL_TABLE))) {
-    constexpr int NV = cols_per_cta<T>(), NT = cols_nt<T, NY>();
+    // the d/dy variant transforms two tiles back: twice the threads (at most 256)
+    constexpr int NV = cols_per_cta<T>(),
+                  NT = DY ? (2 * cols_nt<T, NY>() > 256 ? 256 : 2 * cols_nt<T, NY>()) : cols_nt<T, NY>();
     // tile, twiddles, then the table or d/dy tile and/or the pole's ky table; 128 bytes of alignment slack
     const bool pmul = (mul == MUL_POLE_INV || mul == MUL_POLE_FWD || mul == MUL_PREC_INV);
     const size_t sm = ((size_t)NY * NV * (mul == MUL_TABLE || DY ? 2 : 1) + NY + (pmul ? NY : 0)) * sizeof(C) + 128;
