@@ -114,8 +114,9 @@ constexpr int GVEC_GRAM = 4;  // basis vectors per transpose-reduce of the Gram 
 #endif
 constexpr int SYNC_EVERY = PROP_SYNC_EVERY;   // Arnoldi iterations launched between host reads of the GMRES state
 // Arnoldi batches in flight: 1, the host reads each batch's counts before enqueuing the
-// next.  (Two deep was measured on GB300: within 2 % either way on the three
-// benchmark workloads, so the launches stay sized by exact counts.)
+// next.  (Two deep was measured on GB300: within 2 % either way before the kernels
+// were launched with programmatic dependent launch, 4.5 % slower after it on the
+// batched-scalar step, so the launches stay sized by exact counts.)
 constexpr int PIPE_DEPTH = 1;
 // The counts area: MAXG count-slot sets (one per group of a multi-group step; the
 // grid-by-grid step uses set 0), each 3 ints of cycle counts and two parities of
