@@ -294,6 +294,17 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(GV<T> g, Buf<SRC> src, Buf<type
                                                  int mask, double* norm_acc) {
   rows_fwd_body<T, N, NR, NT, SRC, WF>(blockIdx.x, blockIdx.y, gridDim.x, g, src, dst, mask, norm_acc);
 }
+// The warp-row variant at N = 1024 (complex FP32) with four resident CTAs per SM
+// asked of the compiler: unbounded, the forward pass takes 132 registers and only
+// three CTAs fit (measured: forward row pass 43.0 -> 39.7 ms per 20 batched-scalar
+// steps; five or six CTAs spill and lose).
+constexpr int WROWS_MINB = 4;
+template <typename T, int N, int NR, int NT, typename SRC, bool WF>
+__global__ void __launch_bounds__(NT, WROWS_MINB) k_rows_fwd_w(GV<T> g, Buf<SRC> src,
+                                                                    Buf<typename Cx<T>::t> dst, int mask,
+                                                                    double* norm_acc) {
+  rows_fwd_body<T, N, NR, NT, SRC, WF>(blockIdx.x, blockIdx.y, gridDim.x, g, src, dst, mask, norm_acc);
+}
 
 
 // ---------------------------------------------------------------------------
@@ -877,6 +888,12 @@ __device__ __forceinline__ void rows_inv_body(int bx, int by, int gdx, GV<T> g, 
 template <typename T, int N, int NR, int NT, bool ARN, bool WF>
 __global__ void __launch_bounds__(NT) k_rows_inv(GV<T> g, Buf<typename Cx<T>::t> src, Buf<typename Cx<T>::t> dst,
                                                  int mask, int skip_homog, EpiArgs ep) {
+  rows_inv_body<T, N, NR, NT, ARN, WF>(blockIdx.x, blockIdx.y, gridDim.x, g, src, dst, mask, skip_homog, ep);
+}
+template <typename T, int N, int NR, int NT, bool ARN, bool WF>
+__global__ void __launch_bounds__(NT, WROWS_MINB) k_rows_inv_w(GV<T> g, Buf<typename Cx<T>::t> src,
+                                                                    Buf<typename Cx<T>::t> dst, int mask,
+                                                                    int skip_homog, EpiArgs ep) {
   rows_inv_body<T, N, NR, NT, ARN, WF>(blockIdx.x, blockIdx.y, gridDim.x, g, src, dst, mask, skip_homog, ep);
 }
 

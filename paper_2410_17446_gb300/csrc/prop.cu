@@ -320,7 +320,8 @@ cudaError_t rows_fwd_n(const GV<T>& g, Buf<SRC> src, Buf<typename Cx<T>::t> dst,
   if constexpr (warp_n_c(N)) {
     if (plan_rows(prec_of<T>(), N, (long)units * g.ncomp) == PROP_ROWS_WARP) {
       const size_t sm = smem_elems<N, WROWS, false>() * sizeof(C);
-      auto k = k_rows_fwd<T, N, WROWS, 32 * WROWS, SRC, true>;
+      auto k = (N == 1024 && sizeof(T) == 4) ? k_rows_fwd_w<T, N, WROWS, 32 * WROWS, SRC, true>
+                                             : k_rows_fwd<T, N, WROWS, 32 * WROWS, SRC, true>;
       static bool attr = false;
       cudaError_t e = set_smem_once(k, sm, attr);
       if (e != cudaSuccess) return e;
@@ -346,7 +347,9 @@ cudaError_t rows_inv_n(const GV<T>& g, Buf<typename Cx<T>::t> src, Buf<typename 
   if constexpr (warp_n_c(N)) {
     if (plan_rows(prec_of<T>(), N, (long)units * g.ncomp) == PROP_ROWS_WARP) {
       const size_t sm = smem_elems<N, WROWS, false>() * sizeof(C);
-      auto k = arn ? k_rows_inv<T, N, WROWS, 32 * WROWS, true, true> : k_rows_inv<T, N, WROWS, 32 * WROWS, false, true>;
+      auto k = (N == 1024 && sizeof(T) == 4)
+                   ? (arn ? k_rows_inv_w<T, N, WROWS, 32 * WROWS, true, true> : k_rows_inv_w<T, N, WROWS, 32 * WROWS, false, true>)
+                   : (arn ? k_rows_inv<T, N, WROWS, 32 * WROWS, true, true> : k_rows_inv<T, N, WROWS, 32 * WROWS, false, true>);
       static bool attr[2] = {false, false};
       cudaError_t e = set_smem_once(k, sm, attr[arn ? 1 : 0]);
       if (e != cudaSuccess) return e;
