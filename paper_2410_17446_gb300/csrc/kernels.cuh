@@ -565,8 +565,10 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// complex FP32 at 512 / 1024: four / three CTAs per SM asked of the compiler (64 / 80
+// registers, against 80 / 106 unbounded); FP64 keeps the counts it takes unbounded
 template <typename T, int NY>
-__global__ void __launch_bounds__(32 * CW_NV) k_cols_warp(GV<T> g, Buf<typename Cx<T>::t> src,
+__global__ void __launch_bounds__(32 * CW_NV, sizeof(T) == 4 ? (NY == 512 ? 4 : 3) : (NY == 512 ? 2 : 1)) k_cols_warp(GV<T> g, Buf<typename Cx<T>::t> src,
                                                         Buf<typename Cx<T>::t> dst, int mask, int fwd, int mul,
                                                         int inv, int skip_homog, int pole, T scale) {
   pdl_enter();
