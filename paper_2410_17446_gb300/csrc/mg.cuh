@@ -5,9 +5,10 @@
 // with the Arnoldi epilogue, Gram sweep, update sweep) is one launch over all
 // groups: the 1-D grid is cut into one CTA range per group, and a CTA runs its
 // group's code for that grid size (the size-templated pass bodies of
-// kernels.cuh, selected by a switch), so no CTA is launched without work.  Every multi-group kernel has 256 threads;
-// the row passes take mg_nr(N) rows a CTA (4096 points, or 3072 for the radix-3
-// sizes).  Complex FP32 only; sizes 128 ... 1024.
+// kernels.cuh, selected by a switch), so no CTA is launched without work.
+// Every multi-group kernel has 256 threads; the row passes take mg_nr(N) rows a
+// CTA (4096 points, or 3072 for the radix-3 sizes).  Complex FP32 only; sizes
+// 128 ... 1024.
 #pragma once
 #include "kernels.cuh"
 
@@ -25,7 +26,7 @@ __host__ __device__ constexpr bool mg_size(int n) {
 
 // Everything one multi-group launch needs, passed by value (a __grid_constant__
 // kernel parameter): per group its Arnoldi view (with its list of iterating
-// systems), its row range and x extent, the update sweep's arguments and the
+// systems), its CTA range and x extent, the update sweep's arguments and the
 // column tensor maps.
 struct MGroups {
   CUtensorMap tm[MAXG];    // Tmp  [nsys*ncomp][ny][nx], 4-column boxes
