@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(MG_NT, MG_ROWS_MINB) k_mg_rows_inv(const __gri
 }
 
 // vector operator: six inverse row DFTs and the psi / cross-polarisation epilogue
-__global__ void __launch_bounds__(MG_NT) k_mg_rows_inv_vec(const __grid_constant__ MGroups mg, int jj) {
+// (two CTAs per SM asked of the compiler: unbounded it takes 164 registers, one)
+__global__ void __launch_bounds__(MG_NT, 2) k_mg_rows_inv_vec(const __grid_constant__ MGroups mg, int jj) {
   const MgCta t = mg_cta(mg, blockIdx.x);
   const GV<float>& g = mg.g[t.gi];
   const long F = (long)g.ncomp * g.npts;
