@@ -236,6 +236,9 @@ def reference_arm(args) -> None:
     if rank != 0:
         return
     steps = max(1, int(getattr(args, "steps", 1) or 1))
+    warmup = max(0, int(getattr(args, "warmup", 0) or 0))
+    for _ in range(warmup):   # untimed samples first, as for the GPU arm
+        run_oracle_sample(args.workload, 1)
     secs, pts, its, d = 0.0, 0, [], None
     for _ in range(steps):
         d = run_oracle_sample(args.workload, 1)
@@ -246,7 +249,7 @@ def reference_arm(args) -> None:
     W = make_workload(args.workload, 1)
     sample = f"{steps} x [{d['sample']}]"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * secs / steps,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * secs / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "points_per_step": W.points,
                                             "poles": W.npoles, "sample_grid": d["grid"]},
