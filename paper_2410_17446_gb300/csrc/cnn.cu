@@ -480,11 +480,22 @@ int launch_conv(const void* in, const void* w, const float* b, void* out, int N,
     constexpr size_t sm = conv_row_smem<CIN, COUT>();
     static int ctas_per_sm = 0;
     if (!ctas_per_sm) {
+      // the whole shared-memory carveout for this kernel, so that several CTAs fit.
+      // The occupancy query answers one CTA per SM for this kernel on GB300 while
+      // the profiler reports three (shared memory the limit), so the CTAs that fit
+      // by shared memory (at most 8; registers allow more) size the grid as well.
+      int dev = 0, smem_sm = 0;
       if (cudaFuncSetAttribute(k_conv_tc_row<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
               cudaSuccess ||
+          cudaFuncSetAttribute(k_conv_tc_row<CIN, COUT, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_conv_tc_row<CIN, COUT, MODE>, 128, sm) !=
-              cudaSuccess)
+              cudaSuccess ||
+          cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
         return PROP_CNN_E_CUDA;
+      const int fit = smem_sm / (int)(sm + 2048);   // dynamic + static + the per-CTA reserve
+      ctas_per_sm = std::max(ctas_per_sm, std::min(fit, 8));
       if (ctas_per_sm < 1) ctas_per_sm = 1;
     }
     int dev = 0, sms = 1;

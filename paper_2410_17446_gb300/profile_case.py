@@ -30,6 +30,7 @@ def main(argv=None) -> None:
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--beams", type=int, default=0, help="first N beams (0: all)")
     ap.add_argument("--multigroup", default="on", choices=["on", "off"])
+    ap.add_argument("--learned", action="store_true", help="the learned initial guess (committed network)")
     args = ap.parse_args(argv)
     import torch
     build.build()
@@ -40,7 +41,13 @@ def main(argv=None) -> None:
     tab["residues"] = tab["residues"][:args.poles]
     grids = [(b.grid.nx, b.grid.ny, b.grid.dx, b.grid.dy) for b in beams]
     pr = P.Propagator.from_table(grids, W.k0, W.n0, W.dz, tab, ncomp=W.ncomp, precision=P.PROP_FP32,
-                                 multigroup=args.multigroup == "on")
+                                 multigroup=args.multigroup == "on",
+                                 guess=P.PROP_GUESS_LEARNED if args.learned else P.PROP_GUESS_ZERO)
+    if args.learned:
+        from . import guess_train
+        fam = "vector" if W.ncomp == 2 else "scalar"
+        net = guess_train.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "nets", f"guess_{fam}.npz"))
+        pr.set_guess_net(net["channels"], net["weights"], net["biases"])
     for i, b in enumerate(beams):
         pr.set_field(i, b.w0)
     for s in range(args.steps):
