@@ -12,7 +12,7 @@
  * with tap t = 3 (dy + 1) + (dx + 1).  Activations are NHWC bfloat16 with 16 or
  * 32 channels; weights bfloat16 [9][Cout][Cin]; biases float32.  Convolutions
  * run on the BF16 tensor cores and accumulate in float32: tcgen05 MMAs with
- * the accumulator in tensor memory (128-pixel row tiles, persistent CTAs, when
+ * the accumulator in tensor memory (strips of 128-pixel row tiles, two accumulators, when
  * W is a multiple of 128; 128-pixel tiles when H W is), else warp-level
  * mma.sync.
  *

@@ -208,18 +208,19 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
   }
 }
 
-// Row-tiled, persistent variant for W a multiple of 128 (every grid of the
-// propagator's workloads).  A tile is 128 pixels of one image row; the CTA
-// stages the tile's halo once (rows y-1, y, y+1 x 130 pixels, circular wrap)
-// as CIN/8 planes of 16-byte rows, and each tap's operand is the same halo
-// addressed at a row and a one-pixel shift (descriptor start = plane base +
-// 16 (dx + 1) bytes), so nothing is gathered nine times.  The halo is double
-// buffered with cp.async: the next tile's loads are in flight while the
-// current tile's MMAs and epilogue run.  Weights and biases are loaded once
-// per CTA; tensor memory is allocated once per CTA.
+// Row-strip variant for W a multiple of 128 (every grid of the propagator's
+// workloads).  A tile is 128 pixels of one image row; a CTA walks down a strip
+// of consecutive rows y0 .. y1-1 at one x offset.  Input rows are staged as
+// CIN/8 planes of 130 16-byte pixels (x0-1 .. x0+128, circular wrap) in a ring
+// of RING row slots, so each tile loads one new row and reuses two; each tap's
+// operand is a slot addressed at a plane and a one-pixel shift (descriptor
+// start = plane base + 16 (dx + 1) bytes), so nothing is gathered nine times.
+// Two tensor-memory accumulators let tile i's MMAs run while tile i-1's
+// epilogue reads the other one back.  Row loads run two tiles ahead by cp.async.
+// Weights and biases are loaded once per CTA; tensor memory is allocated once.
 template <int CIN, int COUT>
 constexpr size_t conv_row_smem() {
-  return (size_t)9 * (CIN / 8) * COUT * 16 + 2 * (size_t)3 * (CIN / 8) * 130 * 16;
+  return (size_t)9 * (CIN / 8) * COUT * 16 + (size_t)5 * (CIN / 8) * 130 * 16;
 }
 
 __device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
@@ -230,129 +231,136 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// grid: one CTA per (image, x tile, chunk of rows); cps chunks per strip
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(128) k_conv_tc_row(const __nv_bfloat16* __restrict__ in,
                                                      const __nv_bfloat16* __restrict__ w,
                                                      const float* __restrict__ bias, void* out, int N, int H, int W,
-                                                     const int* active, int astride, int want) {
+                                                     int cps, const int* active, int astride, int want) {
   constexpr int NPL = CIN / 8;
   constexpr int HPX = 130;                              // halo pixels per row
+  constexpr int RING = 5;                               // rows i .. i+2 in use, i+3 landed or landing, i+4 loading
   constexpr uint32_t H_PLANE = HPX * 16, B_PLANE = COUT * 16;
-  constexpr uint32_t HALO = 3 * NPL * H_PLANE;          // bytes of one halo buffer
+  constexpr uint32_t ROW = NPL * H_PLANE;               // bytes of one staged row
   extern __shared__ __align__(128) unsigned char smem_row[];
   unsigned char* sb = smem_row;                         // weights
-  unsigned char* sh = smem_row + 9 * NPL * B_PLANE;     // two halo buffers
-  __shared__ __align__(8) uint64_t bar;
+  unsigned char* sh = smem_row + 9 * NPL * B_PLANE;     // ring of staged rows
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ float sbias[COUT];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tpr = W / 128;                              // tiles per row
-  const long ntiles = (long)N * H * tpr;
-  // the tiles of this CTA: blockIdx.x, + gridDim.x, ...; skip inactive images
-  auto next_tile = [&](long t) -> long {
-    for (; t < ntiles; t += gridDim.x) {
-      const int n = (int)(t / ((long)H * tpr));
-      if (!active || active[(long)n * astride] == want) return t;
-    }
-    return -1;
-  };
-  auto gather = [&](long t, unsigned char* buf) {
-    const int n = (int)(t / ((long)H * tpr));
-    const int rem = (int)(t % ((long)H * tpr));
-    const int y = rem / tpr, x0 = (rem % tpr) * 128;
-    const __nv_bfloat16* img = in + (long)n * H * W * CIN;
-    for (int i = tid; i < 3 * HPX * NPL; i += 128) {
-      const int c8 = i % NPL, q = (i / NPL) % HPX, r = i / (NPL * HPX);
-      const int yy = wrap(y + r - 1, H), xx = wrap(x0 + q - 1, W);
-      cp_async_16(buf + ((size_t)(r * NPL + c8) * HPX + q) * 16, img + ((long)yy * W + xx) * CIN + c8 * 8);
+  const int tpr = W / 128;
+  const int chunk = blockIdx.x % cps, strip = blockIdx.x / cps;
+  const int n = strip / tpr, x0 = (strip - n * tpr) * 128;
+  const int y0 = (int)((long)chunk * H / cps), y1 = (int)((long)(chunk + 1) * H / cps);
+  if (n >= N || y0 >= y1) return;
+  if (active && active[(long)n * astride] != want) return;
+  const int nt = y1 - y0;                               // tiles of this CTA
+  const __nv_bfloat16* img = in + (long)n * H * W * CIN;
+  // staged row j holds image row y0 - 1 + j (wrapped) in slot j % RING
+  auto load_row = [&](int j) {
+    const __nv_bfloat16* row = img + (long)wrap(y0 - 1 + j, H) * W * CIN;
+    unsigned char* dst = sh + (size_t)(j % RING) * ROW;
+    for (int i = tid; i < HPX * NPL; i += 128) {
+      const int q = i / NPL, c8 = i % NPL;
+      cp_async_16(dst + ((size_t)c8 * HPX + q) * 16, row + (long)wrap(x0 + q - 1, W) * CIN + c8 * 8);
     }
   };
-  long tile = next_tile(blockIdx.x);
-  if (tile < 0) return;
-  if (warp == 0) prop_tc::tmem_alloc(&tmem_base, 32);
-  if (tid == 0) { prop_dev::mbar_init(&bar, 1); prop_dev::fence_mbar_init(); }
+  if (warp == 0) prop_tc::tmem_alloc(&tmem_base, 64);
+  if (tid == 0) {
+    prop_dev::mbar_init(&bar[0], 1);
+    prop_dev::mbar_init(&bar[1], 1);
+    prop_dev::fence_mbar_init();
+  }
   for (int i = tid; i < 9 * NPL * COUT; i += 128) {
     const int t = i / (NPL * COUT), r = i % (NPL * COUT), c8 = r / COUT, co = r % COUT;
     cp_async_16(sb + (size_t)i * 16, w + ((size_t)t * COUT + co) * CIN + c8 * 8);
   }
   for (int i = tid; i < COUT; i += 128) sbias[i] = bias ? bias[i] : 0.f;
-  gather(tile, sh);
-  cp_async_commit();
+  load_row(0);
+  load_row(1);
+  load_row(2);
+  cp_async_commit();                                    // group: weights and rows 0..2 (tile 0)
+  if (nt > 1) load_row(3);
+  cp_async_commit();                                    // group: row 3 (tile 1)
   prop_tc::tc_fence_before();
   __syncthreads();
   prop_tc::tc_fence_after();
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = prop_tc::idesc_bf16_f32(128, COUT);
-  const uint32_t b0 = prop_dev::smem_u32(sb);
+  const uint32_t b0 = prop_dev::smem_u32(sb), a0 = prop_dev::smem_u32(sh);
   bool ok = true;
-  for (int k = 0; tile >= 0; ++k) {
-    unsigned char* cur = sh + (k & 1) * HALO;
-    const long nxt = next_tile(tile + gridDim.x);
-    if (nxt >= 0) {   // prefetch the next tile's halo into the other buffer
-      gather(nxt, sh + ((k + 1) & 1) * HALO);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+  // accumulator of tile i: columns 32 (i & 1); read back, bias, activation, store
+  auto epilogue = [&](int i) {
+    const long p = ((long)n * H + y0 + i) * W + x0 + warp * 32 + lane;
+    const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i & 1) * 32);
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      float v[16];
+      prop_tc::tmem_ld16(acc + (uint32_t)c0, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        v[e] += sbias[c0 + e];
+        if (MODE == 0) v[e] = fmaxf(v[e], 0.f);
+      }
+      if (MODE == 2) {
+        float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + p * COUT + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+        uint32_t pk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+          pk[q] = *reinterpret_cast<const uint32_t*>(&hv);
+        }
+        uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + p * COUT + c0);
+        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
     }
+  };
+  for (int i = 0; i < nt; ++i) {
+    cp_async_wait<1>();                                 // rows i .. i+2 landed (row i+3 may be in flight)
     prop_dev::fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0 && ok) {
       prop_tc::tc_fence_after();
-      const uint32_t a0 = prop_dev::smem_u32(cur);
       int kk = 0;
 #pragma unroll
       for (int t = 0; t < 9; ++t)
 #pragma unroll
         for (int kc = 0; kc < CIN / 16; ++kc, ++kk) {
           const int r = t / 3, dx = t % 3 - 1;
-          const uint64_t a = prop_tc::smem_desc(a0 + (uint32_t)(r * NPL + 2 * kc) * H_PLANE + (uint32_t)(dx + 1) * 16,
+          const uint32_t slot = (uint32_t)((i + r) % RING);
+          const uint64_t a = prop_tc::smem_desc(a0 + slot * ROW + (uint32_t)(2 * kc) * H_PLANE + (uint32_t)(dx + 1) * 16,
                                                 H_PLANE, 128);
           const uint64_t b = prop_tc::smem_desc(b0 + (uint32_t)(t * NPL + 2 * kc) * B_PLANE, B_PLANE, 128);
-          prop_tc::mma_bf16(tmem, a, b, idesc, kk > 0);
+          prop_tc::mma_bf16(tmem + (uint32_t)((i & 1) * 32), a, b, idesc, kk > 0);
         }
-      prop_tc::mma_commit(&bar);
+      prop_tc::mma_commit(&bar[i & 1]);
     }
-    ok = ok && prop_dev::mbar_wait(&bar, (uint32_t)(k & 1), &g_cnn_err);
-    prop_tc::tc_fence_after();
-    if (ok) {
-      const int n = (int)(tile / ((long)H * tpr));
-      const int rem = (int)(tile % ((long)H * tpr));
-      const long p = ((long)n * H + rem / tpr) * W + (long)(rem % tpr) * 128 + warp * 32 + lane;
-#pragma unroll
-      for (int c0 = 0; c0 < COUT; c0 += 16) {
-        float v[16];
-        prop_tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          v[i] += sbias[c0 + i];
-          if (MODE == 0) v[i] = fmaxf(v[i], 0.f);
-        }
-        if (MODE == 2) {
-          float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + p * COUT + c0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
-          uint32_t pk[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-            pk[q] = *reinterpret_cast<const uint32_t*>(&hv);
-          }
-          uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + p * COUT + c0);
-          o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-        }
-      }
+    if (i > 0) {   // tile i-1's MMAs done: its accumulator is ready and row slot (i-1) % RING is free
+      ok = ok && prop_dev::mbar_wait(&bar[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), &g_cnn_err);
+      prop_tc::tc_fence_after();
     }
+    if (i + 4 < nt + 2) load_row(i + 4);               // the row tile i+2 needs last
+    cp_async_commit();
+    if (i > 0 && ok) epilogue(i - 1);
     prop_tc::tc_fence_before();
-    __syncthreads();   // accumulator read and halo buffer consumed before they are reused
-    tile = nxt;
+    __syncthreads();   // accumulator i-1 read before tile i+1's MMAs overwrite it
+  }
+  if (ok) {
+    ok = prop_dev::mbar_wait(&bar[(nt - 1) & 1], (uint32_t)(((nt - 1) >> 1) & 1), &g_cnn_err);
+    prop_tc::tc_fence_after();
+    if (ok) epilogue(nt - 1);
   }
   cp_async_wait<0>();
+  prop_tc::tc_fence_before();
+  __syncthreads();
   if (warp == 0) {
     prop_tc::tc_fence_after();
-    prop_tc::tmem_dealloc(tmem, 32);
+    prop_tc::tmem_dealloc(tmem, 64);
   }
 }
 
@@ -476,7 +484,7 @@ template <int CIN, int COUT, int MODE>
 int launch_conv(const void* in, const void* w, const float* b, void* out, int N, int H, int W, const int* active,
                 int astride, int want, cudaStream_t st) {
   const long npix = (long)H * W;
-  if (g_path == PROP_CNN_PATH_AUTO && W % 128 == 0) {
+  if (g_path == PROP_CNN_PATH_AUTO && W % 128 == 0 && npix * N / 128 < 0x7FF00000L) {   // 32-bit strip indices
     constexpr size_t sm = conv_row_smem<CIN, COUT>();
     static int ctas_per_sm = 0;
     if (!ctas_per_sm) {
@@ -501,10 +509,13 @@ int launch_conv(const void* in, const void* w, const float* b, void* out, int N,
     int dev = 0, sms = 1;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return PROP_CNN_E_CUDA;
-    const long ntiles = (long)N * H * (W / 128);
-    const int ctas = (int)std::min<long>(ntiles, (long)ctas_per_sm * sms);
-    k_conv_tc_row<CIN, COUT, MODE><<<ctas, 128, sm, st>>>((const __nv_bfloat16*)in, (const __nv_bfloat16*)w, b, out, N,
-                                                          H, W, active, astride, want);
+    // strips of 128 pixels x H rows, each cut into cps chunks of consecutive rows:
+    // one wave of the CTAs that fit, or one CTA per strip when strips outnumber them
+    const long strips = (long)N * (W / 128);
+    const long slots = (long)ctas_per_sm * sms;
+    const int cps = (int)std::max<long>(1, std::min<long>(H, slots / strips));
+    k_conv_tc_row<CIN, COUT, MODE><<<(unsigned)(strips * cps), 128, sm, st>>>(
+        (const __nv_bfloat16*)in, (const __nv_bfloat16*)w, b, out, N, H, W, cps, active, astride, want);
     return cudaGetLastError() == cudaSuccess ? 0 : PROP_CNN_E_CUDA;
   }
   if (g_path == PROP_CNN_PATH_AUTO && npix % 128 == 0 && npix / 128 <= 0x7FFFFFFF && N <= 65535) {

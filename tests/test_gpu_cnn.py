@@ -69,11 +69,12 @@ def test_training_reduces_loss(G):
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
 
 
-@pytest.mark.parametrize("H,W", [(32, 128), (6, 256), (8, 64)])
+@pytest.mark.parametrize("H,W", [(32, 128), (6, 256), (37, 256), (120, 1024), (8, 64)])
 @pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 16), (32, 32)])
 def test_tensor_core_paths_agree(G, cin, cout, H, W):
-    """The tcgen05 convolutions (persistent 128-pixel row tiles for W a multiple
-    of 128, else 128-pixel tiles; accumulator in tensor memory) and the
+    """The tcgen05 convolutions (strips of 128-pixel row tiles for W a multiple
+    of 128, one row chunk per CTA, down to chunks of one row; else 128-pixel
+    tiles; accumulators in tensor memory) and the
     warp-level mma.sync one give the same layer, in all three output modes, and
     an inactive image is left untouched; the bounded wait never gave up."""
     import ctypes as ct
