@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16* __restrict
 // operand is a slot addressed at a plane and a one-pixel shift (descriptor
 // start = plane base + 16 (dx + 1) bytes), so nothing is gathered nine times.
 // Two tensor-memory accumulators let tile i's MMAs run while tile i-1's
-// epilogue reads the other one back.  Row loads run two tiles ahead by cp.async.
+// epilogue reads the other one back: warp 4 issues the MMAs, warps 0-3 load
+// rows (two tiles ahead, by cp.async) and run the epilogue.
 // Weights and biases are loaded once per CTA; tensor memory is allocated once.
 template <int CIN, int COUT>
 constexpr size_t conv_row_smem() {
@@ -233,7 +234,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 // grid: one CTA per (image, x tile, chunk of rows); cps chunks per strip
 template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(128) k_conv_tc_row(const __nv_bfloat16* __restrict__ in,
+__global__ void __launch_bounds__(160) k_conv_tc_row(const __nv_bfloat16* __restrict__ in,
                                                      const __nv_bfloat16* __restrict__ w,
                                                      const float* __restrict__ bias, void* out, int N, int H, int W,
                                                      int cps, const int* active, int astride, int want) {
@@ -272,16 +273,19 @@ __global__ void __launch_bounds__(128) k_conv_tc_row(const __nv_bfloat16* __rest
     prop_dev::mbar_init(&bar[1], 1);
     prop_dev::fence_mbar_init();
   }
-  for (int i = tid; i < 9 * NPL * COUT; i += 128) {
-    const int t = i / (NPL * COUT), r = i % (NPL * COUT), c8 = r / COUT, co = r % COUT;
-    cp_async_16(sb + (size_t)i * 16, w + ((size_t)t * COUT + co) * CIN + c8 * 8);
+  const bool mma_warp = warp == 4;
+  if (!mma_warp) {
+    for (int i = tid; i < 9 * NPL * COUT; i += 128) {
+      const int t = i / (NPL * COUT), r = i % (NPL * COUT), c8 = r / COUT, co = r % COUT;
+      cp_async_16(sb + (size_t)i * 16, w + ((size_t)t * COUT + co) * CIN + c8 * 8);
+    }
+    for (int i = tid; i < COUT; i += 128) sbias[i] = bias ? bias[i] : 0.f;
+    load_row(0);
+    load_row(1);
+    load_row(2);
   }
-  for (int i = tid; i < COUT; i += 128) sbias[i] = bias ? bias[i] : 0.f;
-  load_row(0);
-  load_row(1);
-  load_row(2);
   cp_async_commit();                                    // group: weights and rows 0..2 (tile 0)
-  if (nt > 1) load_row(3);
+  if (nt > 1 && !mma_warp) load_row(3);
   cp_async_commit();                                    // group: row 3 (tile 1)
   prop_tc::tc_fence_before();
   __syncthreads();
@@ -323,22 +327,27 @@ __global__ void __launch_bounds__(128) k_conv_tc_row(const __nv_bfloat16* __rest
   for (int i = 0; i < nt; ++i) {
     cp_async_wait<1>();                                 // rows i .. i+2 landed (row i+3 may be in flight)
     prop_dev::fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0 && ok) {
-      prop_tc::tc_fence_after();
-      int kk = 0;
+    prop_tc::tc_fence_before();
+    __syncthreads();   // rows visible; accumulator (i & 1) read back by tile i-2's epilogue
+    if (mma_warp) {
+      if (lane == 0) {
+        prop_tc::tc_fence_after();
+        int kk = 0;
 #pragma unroll
-      for (int t = 0; t < 9; ++t)
+        for (int t = 0; t < 9; ++t)
 #pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc, ++kk) {
-          const int r = t / 3, dx = t % 3 - 1;
-          const uint32_t slot = (uint32_t)((i + r) % RING);
-          const uint64_t a = prop_tc::smem_desc(a0 + slot * ROW + (uint32_t)(2 * kc) * H_PLANE + (uint32_t)(dx + 1) * 16,
-                                                H_PLANE, 128);
-          const uint64_t b = prop_tc::smem_desc(b0 + (uint32_t)(t * NPL + 2 * kc) * B_PLANE, B_PLANE, 128);
-          prop_tc::mma_bf16(tmem + (uint32_t)((i & 1) * 32), a, b, idesc, kk > 0);
-        }
-      prop_tc::mma_commit(&bar[i & 1]);
+          for (int kc = 0; kc < CIN / 16; ++kc, ++kk) {
+            const int r = t / 3, dx = t % 3 - 1;
+            const uint32_t slot = (uint32_t)((i + r) % RING);
+            const uint64_t a = prop_tc::smem_desc(a0 + slot * ROW + (uint32_t)(2 * kc) * H_PLANE + (uint32_t)(dx + 1) * 16,
+                                                  H_PLANE, 128);
+            const uint64_t b = prop_tc::smem_desc(b0 + (uint32_t)(t * NPL + 2 * kc) * B_PLANE, B_PLANE, 128);
+            prop_tc::mma_bf16(tmem + (uint32_t)((i & 1) * 32), a, b, idesc, kk > 0);
+          }
+        prop_tc::mma_commit(&bar[i & 1]);
+      }
+      __syncwarp();
+      continue;
     }
     if (i > 0) {   // tile i-1's MMAs done: its accumulator is ready and row slot (i-1) % RING is free
       ok = ok && prop_dev::mbar_wait(&bar[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), &g_cnn_err);
@@ -347,10 +356,8 @@ __global__ void __launch_bounds__(128) k_conv_tc_row(const __nv_bfloat16* __rest
     if (i + 4 < nt + 2) load_row(i + 4);               // the row tile i+2 needs last
     cp_async_commit();
     if (i > 0 && ok) epilogue(i - 1);
-    prop_tc::tc_fence_before();
-    __syncthreads();   // accumulator i-1 read before tile i+1's MMAs overwrite it
   }
-  if (ok) {
+  if (ok && !mma_warp) {
     ok = prop_dev::mbar_wait(&bar[(nt - 1) & 1], (uint32_t)(((nt - 1) >> 1) & 1), &g_cnn_err);
     prop_tc::tc_fence_after();
     if (ok) epilogue(nt - 1);
@@ -497,7 +504,7 @@ int launch_conv(const void* in, const void* w, const float* b, void* out, int N,
               cudaSuccess ||
           cudaFuncSetAttribute(k_conv_tc_row<CIN, COUT, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_conv_tc_row<CIN, COUT, MODE>, 128, sm) !=
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_conv_tc_row<CIN, COUT, MODE>, 160, sm) !=
               cudaSuccess ||
           cudaGetDevice(&dev) != cudaSuccess ||
           cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
@@ -514,7 +521,7 @@ int launch_conv(const void* in, const void* w, const float* b, void* out, int N,
     const long strips = (long)N * (W / 128);
     const long slots = (long)ctas_per_sm * sms;
     const int cps = (int)std::max<long>(1, std::min<long>(H, slots / strips));
-    k_conv_tc_row<CIN, COUT, MODE><<<(unsigned)(strips * cps), 128, sm, st>>>(
+    k_conv_tc_row<CIN, COUT, MODE><<<(unsigned)(strips * cps), 160, sm, st>>>(
         (const __nv_bfloat16*)in, (const __nv_bfloat16*)w, b, out, N, H, W, cps, active, astride, want);
     return cudaGetLastError() == cudaSuccess ? 0 : PROP_CNN_E_CUDA;
   }
