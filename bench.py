@@ -271,6 +271,16 @@ def _peak():
     return (pk, "measured") if pk else (6800.0, "fallback")
 
 
+def _tensor_peak():
+    """Sustained dense BF16 tensor throughput of this GPU (TFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f).get("bf16_tflops_sustained")
+    except OSError:
+        pk = None
+    return (pk, "measured (sustained)") if pk else (1700.0, "fallback (sustained)")
+
+
 def roofline_of(name: str, prof: dict) -> dict:
     """HBM roofline of the kernel kind with the largest device time in the timed region:
     summed algorithmic bytes / summed CUDA-event durations of its launches."""
@@ -435,6 +445,15 @@ class Runner:
                          for k, v in prof.items() if v["launches"]}}
         if guess == "learned":
             d["guess_net_ms"] = round(prof["guess_net"]["total_ms"], 3)
+            # tensor-pipe view of the network: its 3x3 convolutions' FLOPs (the stored,
+            # 16-padded channel counts the kernels compute) over every system's points,
+            # against the sustained BF16 peak (the network runs inside a long step)
+            ch = [int(c) for c in self.load_net()["channels"]]
+            flop = 2 * 9 * sum(a * b for a, b in zip(ch[:-1], ch[1:])) * self.W.points * self.W.npoles * self.args.steps
+            tf = flop / (prof["guess_net"]["total_ms"] / 1e3) / 1e12 if prof["guess_net"]["total_ms"] > 0 else 0.0
+            tpk, tsrc = _tensor_peak()
+            d["guess_net_tensor"] = {"bound": "tensor", "achieved": tf, "peak": tpk, "unit": "TFLOP/s",
+                                     "frac": tf / tpk, "peak_source": tsrc, "flop_per_step": flop / self.args.steps}
             d["net"] = {k: v for k, v in self.load_net()["meta"].items()
                         if k in ("family", "n", "train_media_seeds", "solves", "adam_iterations")}
         self._last = (pr, r)
